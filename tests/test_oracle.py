@@ -1,0 +1,352 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself:
+  * the closed-form travelling wave of Eq. (2) (band width eta = pi a / sqrt(2 w),
+    speed v = mu e eta / (2 pi)), approached at second order under refinement;
+  * mass conservation of pure diffusion under the scaled operator (m_v = d_v lbar^2 / 4);
+  * the point-reflection symmetry of the torus grid about the seed;
+  * the naive full-scan mode (every vertex updated, every vertex scanned) -- bit-exact;
+  * Sec. 3.1 event sequences (torus: split then merge, P. Fig. 2/4), #handles = #tunnels =
+    g = (2 - chi)/2 and Reeb cycle rank g (Sec. 5), genus-0 surfaces give a tree;
+  * Z2 homology of every loop by two independent methods (tree-cotree classes and cut
+    2-colouring), the checker itself pinned on known cycles and by brute-force GF(2) rank.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+from topology import Topo, gf2_rank
+
+OK = 0
+
+
+# ------------------------------------------------------------------ fixtures
+@pytest.fixture(scope="module")
+def torus():
+    return meshgen.torus(64, 32, 2.0, 0.7)
+
+
+@pytest.fixture(scope="module")
+def torus_run(torus):
+    return oracle.detect(torus, meshgen.seed_vertex(0, torus.nv), record_steps=1)
+
+
+@pytest.fixture(scope="module")
+def chain2():
+    return meshgen.tube_chain(2, 64)
+
+
+@pytest.fixture(scope="module")
+def chain3():
+    return meshgen.tube_chain(3, 80)
+
+
+# ------------------------------------------------------------------ constants
+def test_constants_match_closed_forms():
+    c = oracle.constants()
+    a, w, mu = 1 / 25, (1 / 25) / 5, 0.25
+    eta = math.pi * a / math.sqrt(2 * w)
+    assert c["eta"] == pytest.approx(eta, rel=1e-15)
+    assert c["lbar"] == pytest.approx(eta / 4, rel=1e-15)
+    D = mu * a * a / 2
+    # dt * D * s = c (the explicit-Euler max-norm stability fraction of the diffusion part)
+    assert c["dt"] * D * c["s"] == pytest.approx(0.5, rel=1e-14)
+
+
+# ------------------------------------------------------------------ mesh validation
+def test_mesh_validation_statuses(torus):
+    s = 0
+    # open mesh: drop one face
+    r = oracle.detect(meshgen.Mesh(torus.X, torus.F[1:]), s)
+    assert r.status_name == "ENOTMANIFOLD"
+    # flipped face: a directed half-edge appears twice
+    F = torus.F.copy()
+    F[0] = F[0][::-1]
+    assert oracle.detect(meshgen.Mesh(torus.X, F), s).status_name == "ENONORIENTABLE"
+    # two disjoint tori
+    F2 = np.concatenate([torus.F, torus.F + torus.nv])
+    X2 = np.concatenate([torus.X, torus.X + 10.0])
+    assert oracle.detect(meshgen.Mesh(X2, F2), s).status_name == "EDISCONNECTED"
+    # index out of range
+    F = torus.F.copy()
+    F[3, 1] = torus.nv
+    assert oracle.detect(meshgen.Mesh(torus.X, F), s).status_name == "EINVAL"
+    # seed out of range
+    assert oracle.detect(torus, torus.nv).status_name == "EINVAL"
+
+
+@pytest.mark.parametrize("mk,g", [(lambda: meshgen.torus(16, 8), 1), (lambda: meshgen.tube_chain(2, 48), 2),
+                                  (lambda: meshgen.sphere(24), 0)])
+def test_genus_from_euler_characteristic(mk, g):
+    m = mk()
+    assert m.genus() == g  # independent count in numpy
+    r = oracle.detect(m, 0, max_steps=1, tunnels=0)
+    assert r.genus == g
+
+
+# ------------------------------------------------------------------ diffusion pins
+def test_pure_diffusion_conserves_mass(torus):
+    """e = w = 0 and no snapping: Eq. (2) reduces to phi_t = D L phi (D = mu a^2 / 2).
+    With m_v = d_v lbar^2 / 4 the operator satisfies sum_v m_v (L phi)_v = 0, so the
+    explicit step conserves sum_v d_v phi_v.  A row-scale or sign mistake breaks it."""
+    m = meshgen.tube_chain(2, 48)  # irregular degrees
+    seed = meshgen.seed_vertex(3, m.nv)
+    lbar = oracle.constants()["lbar"]  # w = 0 has no band width: keep the default length scale
+    o = oracle.default_options(e=0.0, w=0.0, eps0=0.0, tunnels=0, max_steps=60, lbar=lbar)
+    r = oracle.detect(m, seed, o)
+    assert r.status_name == "EMAXSTEPS"
+    deg = np.bincount(m.F.ravel(), minlength=m.nv)  # closed manifold: degree = incident faces
+    ring = set([seed])
+    for f in m.F:
+        if seed in f:
+            ring.update(int(x) for x in f)
+    mass0 = sum(deg[v] for v in ring)
+    mass = float(np.dot(deg, r.phi))
+    assert (r.phi > 0).sum() > 5 * len(ring)  # it did spread
+    assert mass == pytest.approx(mass0, rel=1e-12)
+
+
+def _front_pos(phi, nu, nv, level):
+    P = phi.reshape(nu, nv).mean(axis=1)
+    p = P[: nu // 2]
+    idx = np.nonzero((p[:-1] >= level) & (p[1:] < level))[0]
+    i = idx[-1]
+    return i + (p[i] - level) / (p[i] - p[i + 1])
+
+
+def _wave(div):
+    eta = oracle.constants()["eta"]
+    o = oracle.default_options(tunnels=0)
+    o.lbar = eta / div
+    c = oracle.constants(o)
+    line = c["lbar"] * math.sqrt(3) / 2  # lattice line spacing of the triangulated grid
+    nu, nv = 200 * div // 4 + 400, 8
+    m = meshgen.torus(nu, nv, 50.0, 1.0)
+    t1, t2 = 120 * div, 300 * div
+    o.max_steps = t1
+    r1 = oracle.detect(m, 0, o)
+    o.max_steps = t2
+    r2 = oracle.detect(m, 0, o)
+    v = (_front_pos(r2.phi, nu, nv, 0.5) - _front_pos(r1.phi, nu, nv, 0.5)) * line / ((t2 - t1) * c["dt"])
+    width = (_front_pos(r2.phi, nu, nv, 0.1) - _front_pos(r2.phi, nu, nv, 0.9)) * line
+    return v, width
+
+
+def test_travelling_wave_closed_form():
+    """Eq. (2) with one front (n = 2) is phi_t = (mu/2)[a^2 phi'' + w(2 phi - 1) + e sqrt(phi(1-phi))].
+    Its travelling wave is phi = (1 + cos(pi x / eta))/2 on [0, eta] with eta = pi a / sqrt(2 w)
+    and speed v = mu e eta / (2 pi).  The 0.1-0.9 width of that profile is
+    eta (1 - 2 acos(0.8)/pi).  The lattice front converges to both at second order."""
+    a, w, mu, e = 1 / 25, 1 / 125, 0.25, 1 / 30
+    eta = math.pi * a / math.sqrt(2 * w)
+    v_th = mu * e * eta / (2 * math.pi)
+    w_th = eta * (1 - 2 * math.acos(0.8) / math.pi)
+    (v8, w8), (v16, w16) = _wave(8), _wave(16)
+    ev8, ev16 = abs(v8 / v_th - 1), abs(v16 / v_th - 1)
+    ew8, ew16 = abs(w8 / w_th - 1), abs(w16 / w_th - 1)
+    assert ev16 < 0.03 and ew16 < 0.02
+    assert ev8 / ev16 > 2.5 and ew8 / ew16 > 2.5  # ~4x per halving: second order
+    v_rich = v16 + (v16 - v8) / 3.0                 # Richardson, order 2
+    assert abs(v_rich / v_th - 1) < 0.01
+
+
+def test_single_vertex_seed_dies_out(torus):
+    """A one-vertex nucleus is sub-critical for Eq. (2) at these constants; the closed
+    1-ring grows.  This is why the seed region is the closed 1-ring."""
+    r = oracle.detect(torus, 5, seed_ring=0, tunnels=0)
+    assert (r.cover >= 0).sum() < 20 and r.status_name != "OK"
+    r1 = oracle.detect(torus, 5, seed_ring=1, tunnels=0)
+    assert r1.status_name == "OK" and (r1.cover >= 0).all()
+
+
+def test_point_reflection_symmetry():
+    """(i, j) -> (-i, -j) is an automorphism of the grid torus fixing the seed (0, 0)."""
+    nu, nv = 48, 24
+    m = meshgen.torus(nu, nv, 2.0, 0.7)
+    for steps in (40, 160):
+        r = oracle.detect(m, 0, max_steps=steps, tunnels=0)
+        phi = r.phi.reshape(nu, nv)
+        refl = phi[(-np.arange(nu)) % nu][:, (-np.arange(nv)) % nv]
+        assert np.abs(phi - refl).max() <= 1e-12
+        assert np.array_equal(phi > 0, refl > 0)
+
+
+# ------------------------------------------------------------------ frontier restriction
+@pytest.mark.parametrize("name", ["torus", "chain2", "caps"])
+def test_naive_mode_bit_exact(name, torus, chain2):
+    m = {"torus": torus, "chain2": chain2, "caps": None}[name]
+    if m is None:
+        m = meshgen.capsules(4, 56)
+    s = meshgen.seed_vertex(1, m.nv)
+    a = oracle.detect(m, s, record_steps=1)
+    b = oracle.detect(m, s, record_steps=1, naive=1)
+    assert a.status == b.status == OK
+    assert np.array_equal(a.records, b.records)
+    assert np.array_equal(a.phi, b.phi) and np.array_equal(a.layer, b.layer)
+    assert np.array_equal(a.cover, b.cover)
+    assert np.array_equal(a.nodes, b.nodes) and np.array_equal(a.node_pos, b.node_pos)
+    assert np.array_equal(a.layers, b.layers)
+    assert len(a.handles) == len(b.handles)
+    for h1, h2, t1, t2 in zip(a.handles, b.handles, a.tunnels, b.tunnels):
+        assert np.array_equal(h1.edges, h2.edges) and np.array_equal(h1.points, h2.points)
+        assert np.array_equal(t1.verts, t2.verts) and t1.stop_step == t2.stop_step
+
+
+def test_naive_mode_bit_exact_mid_run(torus):
+    for steps in (50, 120, 180):
+        a = oracle.detect(torus, 7, max_steps=steps, tunnels=0)
+        b = oracle.detect(torus, 7, max_steps=steps, tunnels=0, naive=1)
+        assert np.array_equal(a.phi, b.phi) and np.array_equal(a.layer, b.layer)
+
+
+# ------------------------------------------------------------------ events and counts
+def test_torus_event_sequence(torus_run):
+    r = torus_run
+    assert r.status == OK and r.genus == 1
+    ev = [k for k, _ in r.events()]
+    assert ev[0] == "SEED" and ev[1] == "SPLIT"
+    assert ev.count("MERGE") == 1 and ev.index("MERGE") > ev.index("SPLIT")
+    assert len(r.handles) == 1 and len(r.tunnels) == 1 and r.tunnels[0].status == OK
+    assert r.reeb_cycle_rank() == 1
+    # every vertex covered, final values all 1 (partition of unity with the base gone)
+    assert (r.cover >= 0).all() and (r.phi == 1.0).all()
+    # SEED node sits at the seed vertex
+    s = meshgen.seed_vertex(0, 2048)
+    assert np.array_equal(r.node_pos[0], torus_run.node_pos[0]) and np.allclose(r.node_pos[0], meshgen.torus().X[s])
+    # steps recorded: frontier size positive, cover never beyond the last step
+    assert len(r.records) == r.steps and (r.records[:, 0] > 0).all() and r.cover.max() <= r.steps
+
+
+def _grid_coords(v, nv):
+    return v // nv, v % nv
+
+
+def test_torus_loop_classes(torus, torus_run):
+    """Handle = meridian class (crosses the longitude once, the meridian never), P. Sec. 2
+    ('handle loop is way shorter'); tunnel winds once around the major circle; the two
+    intersect once."""
+    nu, nv = 64, 32
+    h, t = torus_run.handles[0], torus_run.tunnels[0]
+    topo = Topo(torus.F, torus.nv)
+    lon = topo.vertex_cycle_edges([i * nv for i in range(nu)])     # j = 0 ring (major circle)
+    mer = topo.vertex_cycle_edges([j for j in range(nv)])          # i = 0 ring (minor circle)
+    x = topo.crossing_edges(h.edges)
+    assert int((x & lon).sum()) % 2 == 1 and int((x & mer).sum()) % 2 == 0
+    # tunnel winding numbers from exact grid coordinates
+    I, J = _grid_coords(t.verts.astype(np.int64), nv)
+    di = np.diff(np.concatenate([I, I[:1]]))
+    dj = np.diff(np.concatenate([J, J[:1]]))
+    di = (di + nu // 2) % nu - nu // 2
+    dj = (dj + nv // 2) % nv - nv // 2
+    assert abs(di.sum()) == nu and dj.sum() % nv == 0
+    z = topo.vertex_cycle_edges(t.verts)
+    assert int((z & x).sum()) % 2 == 1
+    # handle (meridian-class isoline) is shorter than the tunnel (major circle)
+    pts = torus.X[t.verts]
+    tlen = np.linalg.norm(np.roll(pts, -1, axis=0) - pts, axis=1).sum()
+    assert h.length < tlen
+
+
+@pytest.mark.parametrize("which", ["chain2", "chain3"])
+def test_counts_and_homology(which, chain2, chain3):
+    m = {"chain2": chain2, "chain3": chain3}[which]
+    topo = Topo(m.F, m.nv)
+    assert topo.g2 == 2 * m.genus()
+    for sd in range(2):
+        r = oracle.detect(m, meshgen.seed_vertex(sd, m.nv))
+        g = r.genus
+        assert r.status == OK and g == m.genus()
+        assert len(r.handles) == g and len(r.tunnels) == g
+        assert r.reeb_cycle_rank() == g
+        merges = [k for k, _ in r.events()].count("MERGE")
+        assert merges <= g
+        classes = []
+        for h, t in zip(r.handles, r.tunnels):
+            assert t.status == OK
+            x = topo.crossing_edges(h.edges)
+            assert topo.is_dual_cycle(x)
+            assert not topo.dual_is_null(x) and topo.cut_connected_dual(x)
+            z = topo.vertex_cycle_edges(t.verts)
+            assert topo.is_primal_cycle(z)
+            assert not topo.primal_is_null(z) and topo.cut_connected_primal(z)
+            cx, cz = topo.class_dual(x), topo.class_primal(z)
+            assert cx.any() and cz.any()
+            # the tunnel crosses its handle loop an odd number of times
+            assert int((x & z).sum()) % 2 == 1
+            classes.append((cx, cz))
+        assert gf2_rank(np.array([c[0] for c in classes])) == g
+        assert gf2_rank(np.array([c[1] for c in classes])) == g
+
+
+def test_genus0_reeb_tree():
+    for m in (meshgen.sphere(28), meshgen.capsules(5, 60)):
+        r = oracle.detect(m, meshgen.seed_vertex(2, m.nv))
+        assert r.status == OK and r.genus == 0
+        assert len(r.handles) == 0 and r.reeb_cycle_rank() == 0
+        ev = [k for k, _ in r.events()]
+        assert "MERGE" not in ev
+        # each c-way split adds c - 1 fronts, each front ends once
+        children = sum(1 for b, _, _ in r.layers if r.nodes[b][0] == 1)
+        assert ev.count("END") == 1 + children - ev.count("SPLIT")
+        # a tree: #arcs = #nodes - 1; every arc goes from an earlier node to a later one
+        assert len(r.layers) == len(r.nodes) - 1
+        for b, d, _ in r.layers:
+            assert r.nodes[b][1] <= r.nodes[d][1]
+
+
+def test_capsules_branching_splits():
+    m = meshgen.capsules(5, 60)
+    r = oracle.detect(m, meshgen.seed_vertex(0, m.nv))
+    ev = [k for k, _ in r.events()]
+    assert ev.count("SPLIT") >= 1 and ev.count("END") >= 3
+
+
+# ------------------------------------------------------------------ checker pins
+def test_homology_checker_on_known_cycles():
+    nu, nv = 12, 6
+    m = meshgen.torus(nu, nv)
+    topo = Topo(m.F, m.nv)
+    assert topo.g2 == 2
+    lon = topo.vertex_cycle_edges([i * nv for i in range(nu)])
+    mer = topo.vertex_cycle_edges(list(range(nv)))
+    tri = topo.vertex_cycle_edges(list(m.F[5]))
+    for z, null in [(lon, False), (mer, False), (tri, True), (lon ^ lon, True), (lon ^ tri, False)]:
+        assert topo.primal_is_null(z) == null
+        assert (not topo.class_primal(z).any()) == null
+    assert gf2_rank(np.array([topo.class_primal(lon), topo.class_primal(mer)])) == 2
+    # dual cycles: the crossing set of a vertex star is a coboundary; a full ring cut is not
+    star = np.zeros(topo.ne, np.uint8)
+    for u, e in topo.adj[7]:
+        star[e] = 1
+    assert topo.dual_is_null(star) and not topo.class_dual(star).any()
+    ring = np.zeros(topo.ne, np.uint8)  # edges between column i=0 and i=1 (and the diagonals)
+    for j in range(nv):
+        for u, e in topo.adj[j]:
+            if u // nv == 1:
+                ring[e] = 1
+    assert topo.is_dual_cycle(ring) and not topo.dual_is_null(ring) and topo.class_dual(ring).any()
+
+
+def test_homology_checker_brute_force_gf2():
+    """Third method on a tiny torus: z is a boundary iff rank[d2 | z] == rank[d2]."""
+    m = meshgen.torus(6, 4)
+    topo = Topo(m.F, m.nv)
+    d2 = np.zeros((topo.nf, topo.ne), np.uint8)
+    for f, tri in enumerate(m.F):
+        for k in range(3):
+            d2[f, topo.eid(int(tri[k]), int(tri[(k + 1) % 3]))] ^= 1
+    r0 = gf2_rank(d2)
+    assert r0 == topo.nf - 1
+    rng = np.random.default_rng(0)
+    for _ in range(12):
+        # random cycle: sum of random faces' boundaries plus a random generator combination
+        z = (rng.integers(0, 2, topo.nf) @ d2) % 2
+        c = rng.integers(0, 2, topo.g2)
+        z = (z + c @ topo.gamma) % 2
+        brute_null = gf2_rank(np.vstack([d2, z[None, :]])) == r0
+        assert brute_null == (not c.any())
+        assert topo.primal_is_null(z.astype(np.uint8)) == brute_null
+        assert (not topo.class_primal(z.astype(np.uint8)).any()) == brute_null
