@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark of full handle/tunnel loop detection (faces/s) on the tube-chain workload.
+
+One step = one complete detection of the batch -- operator build, initial pass (every
+event, loop and Reeb node), tunnel passes and result download -- for 4 seed vertices on
+the tube-chain mesh (8 smooth-unioned tori R = 1, r = 0.35, spacing 1.6, blend 0.15,
+marching tetrahedra, ~512k faces, genus 8, normal jitter 0.1 of the mean edge).
+
+value  = faces per step / device time per step (CUDA events on the library's stream,
+         inputs already in HBM, L2 flushed by a 256 MiB write before each timed step);
+e2e    = the same metric through the C ABI with host (pinned) buffers, host wall time,
+         host->device input copies and result download inside the call;
+roofline = the initial-pass frontier update kernel (the dominant kernel): algorithmic
+         bytes per launch / mean launch time from CUDA events recorded around each launch
+         inside the library, against the measured HBM copy bandwidth;
+cpu_baseline = the plain CPU oracle on a bounded sample of the same workload.
+
+--impl reference times the CPU oracle itself (the only reference implementation of this
+method available here) with the same metric and JSON layout.
+Multi-GPU (torchrun): every rank runs its own copy of the batch (weak scaling, no
+collective on the data path); value = all ranks' faces / the slowest rank's step time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "faces/s full loop detection (batched FP32 vs plain FP64 GPU); SpMV HBM GB/s vs peak"
+UNIT = "faces/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0, help="workload grid scale (1.0 = full size)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=2, help="problems timed for the CPU baseline")
+    return ap.parse_args()
+
+
+def workload_desc(probs):
+    m = probs[0][0]
+    nprob = sum(len(s) for _, s in probs)
+    faces = sum(mm.nf * len(s) for mm, s in probs)
+    return {"workload": f"tube chain, 8 smooth-unioned tori, {m.nf} faces, genus {m.genus()}, {nprob} seeds",
+            "mesh_faces": m.nf, "mesh_vertices": m.nv, "genus": m.genus(), "problems": nprob,
+            "faces_per_step": faces}, faces
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def update_kernel_traffic():
+    """dram bytes per launch of the update kernel from a committed ncu capture, if the kernel
+    source is unchanged since (else None)."""
+    p = os.path.join(ROOT, "profiles", "k_update_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    src = os.path.join(ROOT, "paper_2105_13168_gb300", "csrc", "initial.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if d.get("source_sha256") != h:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(probs, nsample: int) -> dict:
+    import oracle
+
+    flat = [(m, s) for m, seeds in probs for s in seeds][:max(1, nsample)]
+    t0 = time.perf_counter()
+    faces = 0
+    for m, s in flat:
+        r = oracle.detect(m, s)
+        assert r.status == 0, r.status_name
+        faces += m.nf
+    dt = time.perf_counter() - t0
+    return {"value": faces / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": round(dt, 2),
+            "sample": f"{len(flat)} of {sum(len(s) for _, s in probs)} problems of the same workload, full detection "
+                      "(initial pass + tunnel passes), single-threaded FP64 oracle"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import meshgen
+    import oracle
+
+    probs = meshgen.workload(2, args.scale)
+    cfg, _ = workload_desc(probs)
+    m, seeds = probs[0]
+    times = []
+    for it in range(args.warmup + args.steps):
+        s = seeds[it % len(seeds)]
+        t0 = time.perf_counter()
+        r = oracle.detect(m, s)
+        dt = time.perf_counter() - t0
+        assert r.status == 0
+        if it >= args.warmup:
+            times.append(dt)
+    mean = sum(times) / len(times)
+    value = m.nf / mean
+    cfg = dict(cfg, sample="each step: one problem (one seed) of the workload, full detection")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one problem (one seed) per step of the tube-chain workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    import meshgen
+    import paper_2105_13168_gb300 as vls
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    probs = meshgen.workload(2, args.scale)
+    cfg, faces = workload_desc(probs)
+    # CPU baseline (rank 0, one GPU): timed before any GPU work of this process
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(probs, args.cpu_sample)
+
+    stream = torch.cuda.current_stream()
+    opts = vls.vls_default_options(profile=1)
+    ctx = vls.vls_create(opts, stream.cuda_stream)
+    meshes_dev = [(torch.from_numpy(m.X).to(dev), torch.from_numpy(m.F).to(dev)) for m, _ in probs]
+    seeds = [s for _, s in probs]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def one(device_inputs=True):
+        if device_inputs:
+            res = vls.vls_detect_batch(ctx, meshes_dev, seeds, device=True)
+        else:
+            res = vls.vls_detect_batch(ctx, meshes_host, seeds, device=False)
+        out = vls.read_result(res)
+        vls.vls_result_free(res)
+        return out
+
+    for _ in range(args.warmup):
+        out = one()
+        assert all(p.status == 0 for p in out), [p.status_name for p in out]
+    # ---- timed region: device-resident inputs
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    step_ms, launches = [], 0
+    upd_ms = upd_n = rows = 0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = one()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = out[0].stats
+        launches += st["kernel_launches"]
+        upd_ms += st["ms_update"]
+        upd_n += st["n_update"]
+        rows += sum(p.stats["row_updates"] for p in out)
+        assert all(p.status == 0 for p in out), [p.status_name for p in out]
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    if dist is not None:
+        dist.barrier()
+    ms = sum(step_ms) / len(step_ms)
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = faces * world / (ms_max / 1e3)
+    # ---- e2e: host buffers through the C ABI (pinned), copies inside the call
+    pinned = [(torch.from_numpy(m.X).pin_memory(), torch.from_numpy(m.F).pin_memory()) for m, _ in probs]
+    meshes_host = [(x.numpy(), f.numpy()) for x, f in pinned]
+    one(device_inputs=False)
+    e2e_s, h2d, d2h = [], 0, 0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = one(device_inputs=False)
+        e2e_s.append(time.perf_counter() - t0)
+        h2d, d2h = out[0].stats["h2d_bytes"], out[0].stats["d2h_bytes"]
+    e2e_v = faces * world / (sum(e2e_s) / len(e2e_s))
+    vls.vls_destroy(ctx)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    # ---- roofline of the frontier update kernel
+    peak, peak_kind = measured_peaks()
+    deg = sum(3 * m.nf * len(s) for m, s in probs) / sum(m.nv * len(s) for m, s in probs)
+    bytes_per_row = 44 + 4 * deg  # frontier entry 8, row bounds 8, columns 4d, own state 12, output 16
+    launch_s = (upd_ms / upd_n) / 1e3 if upd_n else None
+    rows_per_launch = rows / upd_n if upd_n else 0
+    achieved = (rows_per_launch * bytes_per_row / launch_s) / 1e9 if launch_s else None
+    roof = {"kernel": "k_update (initial-pass frontier update, FP64)", "bound": "hbm", "achieved": achieved,
+            "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": update_kernel_traffic(), "bytes_per_row": round(bytes_per_row, 2),
+            "rows_per_launch": round(rows_per_launch, 1), "launch_us": launch_s * 1e6 if launch_s else None,
+            "share_of_step": (upd_ms / args.steps) / ms if ms else None}
+    cfg = dict(cfg, precision="fp64", inputs="resident in HBM (device pointers) for value; pinned host for e2e",
+               l2="flushed by a 256 MiB write before every timed step",
+               parallelism=f"{world} GPU(s), each its own copy of the batch" if world > 1 else "1 GPU")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roof, "clocks": clocks}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

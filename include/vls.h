@@ -1,0 +1,180 @@
+/*
+ * vls.h -- C ABI of the GB300 variational loop-shrinking library.
+ *
+ * Implements the hot path of Weinrauch, Seidel, Mlakar, Steinberger, Zayer,
+ * "A Variational Loop Shrinking Analogy for Handle and Tunnel Detection and Reeb
+ * Graph Construction on Surfaces": a closed triangle mesh and a seed vertex go in;
+ * handle loops, tunnel loops and the diffusion Reeb graph come out (problem
+ * statement, Sec. 1; initial pass Sec. 3.1; tunnel pass Sec. 3.2; single-layer
+ * passes Sec. 4; Reeb graph Sec. 5).  Every step runs in CUDA kernels on the
+ * current device.
+ *
+ * Conventions
+ *   - Every function returns vls_status (0 = VLS_OK) unless stated otherwise; no C++
+ *     exception crosses this boundary.
+ *   - Input arrays are borrowed: read during the call only, never retained.
+ *   - Results live in library-owned host memory until vls_result_free(); every pointer
+ *     a result accessor hands out stays valid until then.
+ *   - A context is not thread-safe: use one per host thread.
+ *   - Layer ids in results are per problem: 1 is the seed layer, then ids follow
+ *     creation order.  Vertex ids are those of the input mesh.
+ */
+#ifndef VLS_H
+#define VLS_H
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VLS_API __attribute__((visibility("default")))
+#else
+#define VLS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VLS_OK = 0,
+  VLS_EINVAL = 1,          /* bad argument, index out of range, degenerate face, bad seed */
+  VLS_ENOTMANIFOLD = 2,    /* open or non-manifold edge / vertex */
+  VLS_ENONORIENTABLE = 3,  /* inconsistently oriented faces */
+  VLS_EDISCONNECTED = 4,   /* more than one connected component, or unused vertex */
+  VLS_EMAXSTEPS = 5,       /* step limit reached (state up to the limit is still returned) */
+  VLS_ESLOTS = 6,          /* more than 4 layers met at one vertex */
+  VLS_ELAYERS = 7,         /* layer table or event buffer capacity exceeded */
+  VLS_ELOOPFAIL = 8,       /* a tunnel pass never reached the far side / trace got stuck */
+  VLS_ETIMEOUT = 9,        /* reserved: bounded device-side wait gave up */
+  VLS_ENOMEM = 10,         /* device or host allocation failed */
+  VLS_ECUDA = 11,          /* CUDA runtime error (kernel launch / copy) */
+  VLS_ESTALL = 12          /* no front left but parts of the surface were never covered */
+} vls_status;
+
+typedef enum { VLS_FP64 = 0, VLS_FP32_RECHECK = 1 } vls_precision;
+
+/*
+ * Options.  Defaults (vls_default_options) are the paper's constants (Sec. 2,
+ * "Implementation details": mu = 1/4, e = 1/30, a = 1/25, w = a/5) and the following
+ * readings of what the paper leaves open: dt = dt_factor * lbar^2 / (4 mu a^2 / 2) with
+ * dt_factor 0.5; lbar = eta / 4 with eta = pi a / sqrt(2 w) (band width of the
+ * travelling wave of Eq. (2)); snap threshold eps0 = 1e-3; isoline / arrival level
+ * theta_iso = 0.5.
+ */
+typedef struct {
+  double mu, e, a, w;       /* Eq. (2) coefficients */
+  double dt_factor;         /* Euler step as a fraction of the diffusion stability limit */
+  double eps0;              /* snap: values below eps0 -> 0, above 1 - eps0 -> 1 */
+  double theta_iso;         /* isoline level of handle loops, arrival level of tunnel passes */
+  double lbar;              /* operator length scale; <= 0 selects eta / 4 */
+  double recheck_margin;    /* FP32 mode: values within this of a threshold are redone in FP64 */
+  int32_t max_steps;        /* initial-pass step limit (per problem) */
+  int32_t max_pass_steps;   /* tunnel-pass step limit (per pass) */
+  int32_t tunnels;          /* 1: run the tunnel passes (Sec. 3.2) */
+  int32_t keep_state;       /* 1: results carry the final per-vertex state (layer, value, cover) */
+  int32_t record_steps;     /* 1: results carry per-step frontier size, band size, band hash */
+  int32_t sync_interval;    /* steps between host polls of the device "still running" flag */
+  int32_t threads;          /* threads per block of the frontier kernels (0: autotuned) */
+  int32_t blocks_per_sm;    /* grid = blocks_per_sm x SM count (0: autotuned) */
+  vls_precision precision;
+  int32_t profile;          /* 1: time every frontier-update launch with CUDA events (vls_stats) */
+} vls_options;
+
+/* A closed, oriented triangle mesh: X[nv][3] positions, F[nf][3] vertex ids (CCW). */
+typedef struct {
+  const double *X;
+  int64_t nv;
+  const int32_t *F;
+  int64_t nf;
+  int32_t device; /* 0: X and F are host pointers; 1: device pointers on the current device */
+} vls_mesh;
+
+typedef struct vls_ctx vls_ctx;
+typedef struct vls_result vls_result;
+
+typedef struct {
+  int32_t steps;           /* initial-pass steps executed */
+  int32_t tunnel_steps;    /* max tunnel-pass steps over this problem's passes */
+  int64_t row_updates;     /* frontier rows updated in the initial pass */
+  int64_t pass_updates;    /* rows updated in the tunnel passes */
+  int32_t merges, splits, ends, layers;
+  double ms_operator, ms_initial, ms_tunnel, ms_download; /* batch-wide phase times */
+  int64_t kernel_launches; /* kernels launched for the whole batch */
+  /* profile = 1: summed device time and launch count of the initial-pass update kernel and
+   * of the tunnel-pass update kernel (batch-wide), from CUDA events around each launch */
+  double ms_update, ms_pass_update;
+  int64_t n_update, n_pass_update;
+  int64_t h2d_bytes, d2h_bytes; /* batch-wide host<->device bytes of this call */
+} vls_stats;
+
+/* Fill *o with the defaults above. */
+VLS_API void vls_default_options(vls_options *o);
+
+/* Derived constants of o: out[0] eta, out[1] lbar, out[2] dt, out[3] s = 4 / lbar^2. */
+VLS_API void vls_constants(const vls_options *o, double out[4]);
+
+/*
+ * Create a context on the current CUDA device.  `cuda_stream` is a cudaStream_t (may be
+ * NULL for the default stream); every kernel and copy is issued on it.  The context keeps
+ * one grow-only device arena, sized to the largest batch it has run and released by
+ * vls_destroy(); a call allocates device memory only when its batch needs more.
+ */
+VLS_API vls_status vls_create(vls_ctx **ctx, const vls_options *o, void *cuda_stream);
+VLS_API void vls_destroy(vls_ctx *ctx);
+
+/*
+ * Loop detection for one mesh and one seed vertex (Sec. 3.1-3.2, Sec. 5): validates the
+ * mesh, builds the operator, runs the initial pass and one tunnel pass per handle.
+ * *out receives a result with one problem (even on error; its status says why).
+ */
+VLS_API vls_status vls_detect(vls_ctx *ctx, const vls_mesh *m, int32_t seed_vertex, vls_result **out);
+
+/*
+ * Batched detection: n_mesh meshes, mesh i with seeds_per_mesh[i] seed vertices taken in
+ * order from `seeds`.  Problems are numbered mesh-major, seed-minor.  All problems advance
+ * in the same kernels (one launch per step for the whole batch).  Each problem reports its
+ * own status; one failing problem does not fail the others.  Returns VLS_OK unless the
+ * batch as a whole could not run.
+ */
+VLS_API vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_mesh *meshes, const int32_t *seeds,
+                            const int32_t *seeds_per_mesh, vls_result **out);
+
+VLS_API int32_t vls_result_count(const vls_result *r);                 /* problems in the result */
+VLS_API vls_status vls_result_status(const vls_result *r, int32_t p);
+VLS_API int32_t vls_result_genus(const vls_result *r, int32_t p);      /* (2 - chi) / 2 */
+VLS_API vls_status vls_result_stats(const vls_result *r, int32_t p, vls_stats *s);
+
+/* kind 0: handle loops (Sec. 3.1), kind 1: tunnel loops (Sec. 3.2) */
+VLS_API int32_t vls_result_num_loops(const vls_result *r, int32_t p, int32_t kind);
+/*
+ * Loop i of the given kind.  Handles: *verts = the collapsed inside-vertex cycle of the
+ * theta-isoline, *pts = its FP64 isoline points (one per crossing edge, *npts of them).
+ * Tunnels: *verts = the vertex cycle, *pts = NULL.
+ */
+VLS_API vls_status vls_result_loop(const vls_result *r, int32_t p, int32_t kind, int32_t i, const int32_t **verts,
+                           int64_t *n, const double **pts, int64_t *npts);
+/* Handle i: crossing edges [n][2] (inside, outside) in loop order; info[0] step, [1] layer,
+ * [2] Reeb node of its merge; *length = polyline length of the isoline points. */
+VLS_API vls_status vls_result_handle(const vls_result *r, int32_t p, int32_t i, const int32_t **edges, int64_t *n,
+                             int32_t info[3], double *length);
+/* Tunnel i (one per handle): info[0] status, [1] step its pass stopped, [2] first vertex reached */
+VLS_API vls_status vls_result_tunnel(const vls_result *r, int32_t p, int32_t i, int32_t info[3]);
+
+/* Reeb graph (Sec. 5): nodes [n][2] = (kind 0 SEED / 1 SPLIT / 2 MERGE / 3 END, step),
+ * positions [n][3] (mean of the narrow band); arcs = layers [L][3] = (birth node, death
+ * node, final state: 2 dead after split, 3 merged, 4 ended). */
+VLS_API vls_status vls_result_reeb(const vls_result *r, int32_t p, const int32_t **nodes, const double **pos,
+                           int32_t *n_nodes, const int32_t **layers, int32_t *n_layers);
+
+/* Final per-vertex state (keep_state = 1): layer id (0 none), value, cover step (-1 never). */
+VLS_API vls_status vls_result_state(const vls_result *r, int32_t p, const int32_t **layer, const double **phi,
+                            const int32_t **cover, int64_t *nv);
+/* Per-step records (record_steps = 1): [steps][4] = frontier rows, band vertices, band hash
+ * low 32 bits, high 32 bits. */
+VLS_API vls_status vls_result_records(const vls_result *r, int32_t p, const int64_t **rec, int32_t *steps);
+
+VLS_API void vls_result_free(vls_result *r);
+VLS_API const char *vls_status_string(vls_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VLS_H */

@@ -1,0 +1,884 @@
+// api.cu -- host engine and C ABI (include/vls.h).
+//
+// One call = one batch: the host lays the batch out in a grow-only device arena owned by
+// the context, copies (or, for device meshes, moves on the device) the inputs into the union
+// graph, and drives the phases on the context's stream: operator build (a0), initial pass
+// (steps of kernels, the host polls a device "still running" counter every sync_interval
+// steps), tunnel passes, result download.  Nothing on the path runs on the host except
+// launch bookkeeping and the final repacking of downloaded results.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdlib>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vls_batch.cuh"
+
+using namespace vls;
+
+namespace {
+
+struct ProbResult {
+  int32_t status = 0, genus = 0, steps = 0, tunnel_steps = 0;
+  int64_t nv = 0;
+  vls_stats stats{};
+  std::vector<int32_t> nodes;  // [n][2]
+  std::vector<double> npos;    // [n][3]
+  std::vector<int32_t> layers; // [L][3]
+  struct Handle {
+    std::vector<int32_t> edges, verts;
+    std::vector<double> pts;
+    int32_t info[3];
+    double len;
+  };
+  std::vector<Handle> handles;
+  struct Tunnel {
+    int32_t info[3];
+    std::vector<int32_t> verts;
+  };
+  std::vector<Tunnel> tunnels;
+  std::vector<int32_t> lay, cover;
+  std::vector<double> phi;
+  std::vector<int64_t> rec;
+};
+
+}  // namespace
+
+struct vls_result {
+  std::vector<ProbResult> p;
+};
+
+struct vls_ctx {
+  vls_options opt;
+  cudaStream_t st = nullptr;
+  Arena arena;
+  int sm = 148;
+  std::vector<cudaEvent_t> evpool; // profiling events, reused across calls
+};
+
+cudaError_t Arena::reserve(size_t bytes) {
+  if (bytes <= cap) return cudaSuccess;
+  if (base) cudaFree(base);
+  base = nullptr;
+  cap = 0;
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&base, want);
+  if (e != cudaSuccess) { base = nullptr; return e; }
+  cap = want;
+  return cudaSuccess;
+}
+
+extern "C" void vls_default_options(vls_options *o) {
+  std::memset(o, 0, sizeof(*o));
+  o->mu = 0.25;
+  o->e = 1.0 / 30.0;
+  o->a = 1.0 / 25.0;
+  o->w = o->a / 5.0;
+  o->dt_factor = 0.5;
+  o->eps0 = 1e-3;
+  o->theta_iso = 0.5;
+  o->lbar = 0.0;
+  o->recheck_margin = 1e-4;
+  o->max_steps = 200000;
+  o->max_pass_steps = 200000;
+  o->tunnels = 1;
+  o->keep_state = 0;
+  o->record_steps = 0;
+  o->sync_interval = 16;
+  o->threads = 0;
+  o->blocks_per_sm = 0;
+  o->precision = VLS_FP64;
+}
+
+extern "C" void vls_constants(const vls_options *o, double out[4]) {
+  const double pi = 3.14159265358979323846;
+  double eta = pi * o->a / std::sqrt(2.0 * o->w);
+  double lbar = o->lbar > 0 ? o->lbar : eta / 4.0;
+  double D = o->mu * o->a * o->a / 2.0;
+  double dt = o->dt_factor * lbar * lbar / (4.0 * D);
+  out[0] = eta;
+  out[1] = lbar;
+  out[2] = dt;
+  out[3] = 4.0 / (lbar * lbar);
+}
+
+extern "C" const char *vls_status_string(vls_status s) {
+  switch (s) {
+  case VLS_OK: return "ok";
+  case VLS_EINVAL: return "invalid argument or mesh index";
+  case VLS_ENOTMANIFOLD: return "mesh is open or not manifold";
+  case VLS_ENONORIENTABLE: return "mesh faces are not consistently oriented";
+  case VLS_EDISCONNECTED: return "mesh is disconnected or has unused vertices";
+  case VLS_EMAXSTEPS: return "step limit reached";
+  case VLS_ESLOTS: return "too many layers met at one vertex";
+  case VLS_ELAYERS: return "layer, event or loop capacity exceeded";
+  case VLS_ELOOPFAIL: return "tunnel pass failed to reach the far side";
+  case VLS_ETIMEOUT: return "device wait timed out";
+  case VLS_ENOMEM: return "out of memory";
+  case VLS_ECUDA: return "CUDA error";
+  case VLS_ESTALL: return "front stopped before covering the surface";
+  }
+  return "unknown status";
+}
+
+extern "C" vls_status vls_create(vls_ctx **ctx, const vls_options *o, void *stream) {
+  if (!ctx) return VLS_EINVAL;
+  vls_ctx *c = new (std::nothrow) vls_ctx();
+  if (!c) return VLS_ENOMEM;
+  if (o) c->opt = *o;
+  else vls_default_options(&c->opt);
+  c->st = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete c;
+    return VLS_ECUDA;
+  }
+  *ctx = c;
+  return VLS_OK;
+}
+
+extern "C" void vls_destroy(vls_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->arena.base) cudaFree(ctx->arena.base);
+  for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+namespace {
+
+// two-pass layout: first pass counts bytes, second hands out pointers
+struct Layout {
+  Arena *a;
+  bool sizing;
+  size_t bytes = 0;
+  template <class T> T *take(size_t n) {
+    if (sizing) {
+      bytes = ((bytes + 255) & ~size_t(255)) + n * sizeof(T);
+      return nullptr;
+    }
+    return a->take<T>(n);
+  }
+};
+
+void layout_batch(Layout &L, Batch &b) {
+  Dev &d = b.d;
+  const size_t P = b.P, V = b.V, NF = b.NF, nnz = b.nnz, Lc = b.Lcap;
+  d.X = L.take<double>(3 * V);
+  d.F = L.take<int32_t>(3 * NF);
+  d.rp = L.take<int32_t>(V + 1);
+  d.col = L.take<int32_t>(nnz);
+  d.hface = L.take<int32_t>(nnz);
+  d.voff = L.take<int32_t>(P + 1);
+  d.foff = L.take<int32_t>(P + 1);
+  d.lbase = L.take<int32_t>(P);
+  d.lcap = L.take<int32_t>(P);
+  d.seed = L.take<int32_t>(P);
+  d.lcount = L.take<int32_t>(P);
+  d.pstatus = L.take<int32_t>(P);
+  d.pdone = L.take<int32_t>(P);
+  d.psteps = L.take<int32_t>(P);
+  d.pnodes = L.take<int32_t>(P);
+  d.pfront = L.take<int32_t>(2 * P);
+  d.pmerge = L.take<int32_t>(P);
+  d.pupd = L.take<int64_t>(P);
+  d.pev = L.take<int32_t>(4 * P);
+  d.lay = L.take<int32_t>(V);
+  d.phi = L.take<double>(V);
+  d.cover = L.take<int32_t>(V);
+  d.stamp = L.take<int32_t>(V);
+  d.fmark = L.take<int32_t>(V);
+  d.uf = L.take<int32_t>(V);
+  d.multi = L.take<int32_t>(V);
+  d.lstate = L.take<int32_t>(Lc);
+  d.lfwd = L.take<int32_t>(Lc);
+  d.lbirth = L.take<int32_t>(Lc);
+  d.ldeath = L.take<int32_t>(Lc);
+  d.lcnt = L.take<int32_t>(3 * Lc);
+  d.lprob = L.take<int32_t>(Lc);
+  d.front[0] = L.take<int32_t>(2 * V);
+  d.front[1] = L.take<int32_t>(2 * V);
+  d.nfront = L.take<int32_t>(2);
+  d.onl = L.take<int32_t>(V);
+  d.olay = L.take<int32_t>(KMAX * V);
+  d.ophi = L.take<double>(KMAX * V);
+  d.coll = L.take<int32_t>(V);
+  d.ncoll = L.take<int32_t>(1);
+  d.ngroups = L.take<int32_t>(1);
+  d.gprob = L.take<int32_t>(MAX_TRACES);
+  d.gnew = L.take<int32_t>(MAX_TRACES);
+  d.gnode = L.take<int32_t>(MAX_TRACES);
+  d.gnmem = L.take<int32_t>(MAX_TRACES);
+  d.gmem = L.take<int32_t>(MAX_TRACES * MAX_GROUP);
+  d.ntrace = L.take<int32_t>(1);
+  d.tgroup = L.take<int32_t>(MAX_TRACES);
+  d.tlayer = L.take<int32_t>(MAX_TRACES);
+  d.tcount = L.take<int32_t>(MAX_TRACES);
+  d.tlen = L.take<int32_t>(MAX_TRACES);
+  d.tkey = L.take<unsigned long long>((size_t)MAX_TRACES * TRACE_CAP);
+  d.tslot = L.take<int32_t>((size_t)MAX_TRACES * TRACE_CAP);
+  d.tsucc = L.take<int32_t>((size_t)MAX_TRACES * TRACE_CAP);
+  d.tpar = L.take<int32_t>((size_t)MAX_TRACES * TRACE_CAP);
+  d.trank = L.take<int32_t>((size_t)MAX_TRACES * TRACE_CAP * 2);
+  d.tnext = L.take<int32_t>((size_t)MAX_TRACES * TRACE_CAP * 2);
+  d.tord = L.take<int32_t>((size_t)MAX_TRACES * TRACE_CAP);
+  d.tbest = L.take<unsigned long long>(MAX_TRACES);
+  d.ncap = (int32_t)(Lc + P);
+  d.nkind = L.take<int32_t>(d.ncap);
+  d.nstep = L.take<int32_t>(d.ncap);
+  d.nprob = L.take<int32_t>(d.ncap);
+  d.nlocal = L.take<int32_t>(d.ncap);
+  d.npos = L.take<double>(3 * (size_t)d.ncap);
+  d.nnodes = L.take<int32_t>(1);
+  d.hcap = (int32_t)Lc;
+  d.nhand = L.take<int32_t>(1);
+  d.hprob = L.take<int32_t>(d.hcap);
+  d.hstep = L.take<int32_t>(d.hcap);
+  d.hlayer = L.take<int32_t>(d.hcap);
+  d.hnode = L.take<int32_t>(d.hcap);
+  d.hoff = L.take<int32_t>(d.hcap);
+  d.hn = L.take<int32_t>(d.hcap);
+  d.hvoff = L.take<int32_t>(d.hcap);
+  d.hvn = L.take<int32_t>(d.hcap);
+  d.hlen = L.take<double>(d.hcap);
+  d.ecap = (int32_t)std::max<size_t>(1u << 20, V / 8);
+  d.nhedge = L.take<int32_t>(1);
+  d.hedge = L.take<int32_t>(2 * (size_t)d.ecap);
+  d.hpts = L.take<double>(3 * (size_t)d.ecap);
+  d.hverts = L.take<int32_t>(d.ecap);
+  d.rec = L.take<long long>(d.record ? (size_t)P * d.rcap * 4 : 1);
+  d.rhash = L.take<unsigned long long>(P);
+  d.rband = L.take<int32_t>(P);
+  d.err = L.take<int32_t>(4);
+}
+
+void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut) {
+  TDev &T = b.td;
+  T.NP = NP;
+  T.PV = (int32_t)PV;
+  T.pbase = L.take<int32_t>(NP + 1);
+  T.pprob = L.take<int32_t>(NP);
+  T.pstep = L.take<int32_t>(NP);
+  T.pcoff = L.take<int32_t>(NP);
+  T.pcn = L.take<int32_t>(NP);
+  T.cut = L.take<int32_t>(ncut);
+  T.heoff = L.take<int32_t>(NP);
+  T.hen = L.take<int32_t>(NP);
+  T.flag = L.take<int8_t>(PV);
+  T.phi = L.take<double>(PV);
+  T.T = L.take<int32_t>(PV);
+  T.stamp = L.take<int32_t>(PV);
+  T.fv[0] = L.take<int32_t>(PV);
+  T.fq[0] = L.take<int32_t>(PV);
+  T.fv[1] = L.take<int32_t>(PV);
+  T.fq[1] = L.take<int32_t>(PV);
+  T.nf = L.take<int32_t>(2);
+  T.onew = L.take<double>(PV);
+  T.qdone = L.take<int32_t>(NP);
+  T.qsteps = L.take<int32_t>(NP);
+  T.qstatus = L.take<int32_t>(NP);
+  T.qbstar = L.take<int32_t>(NP);
+  T.qcnt = L.take<int32_t>(2 * NP);
+  T.qupd = L.take<long long>(NP);
+  T.active = L.take<int32_t>(1);
+  T.tvoff = L.take<int32_t>(NP);
+  T.tvn = L.take<int32_t>(NP);
+  T.tvcap = (int32_t)std::min<int64_t>(PV, INT32_MAX / 2);
+  T.tverts = L.take<int32_t>(T.tvcap);
+  T.ntverts = L.take<int32_t>(1);
+  T.path = L.take<int32_t>(PV);
+}
+
+__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+#define CK(x)                                  \
+  do {                                         \
+    cudaError_t _e = (x);                      \
+    if (_e != cudaSuccess) { err = _e; goto fail; } \
+  } while (0)
+
+int64_t *g_d2h_counter = nullptr; // bytes downloaded by the call in progress (single-threaded ctx)
+template <class T> bool d2h(std::vector<T> &dst, const T *src, size_t n, cudaStream_t st) {
+  dst.resize(n);
+  if (n == 0) return true;
+  if (g_d2h_counter) *g_d2h_counter += (int64_t)(n * sizeof(T));
+  return cudaMemcpyAsync(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+}  // namespace
+
+extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_mesh *meshes, const int32_t *seeds,
+                                       const int32_t *seeds_per_mesh, vls_result **out) {
+  if (!ctx || !out || n_mesh <= 0 || !meshes || !seeds || !seeds_per_mesh) return VLS_EINVAL;
+  *out = nullptr;
+  vls_result *res = new (std::nothrow) vls_result();
+  if (!res) return VLS_ENOMEM;
+  // problems (mesh-major, seed-minor); those failing host checks never reach the device
+  std::vector<int32_t> pm, ps, pres_status;
+  int64_t si = 0;
+  for (int32_t m = 0; m < n_mesh; ++m) {
+    if (seeds_per_mesh[m] < 0) { delete res; return VLS_EINVAL; }
+    for (int32_t k = 0; k < seeds_per_mesh[m]; ++k, ++si) {
+      pm.push_back(m);
+      ps.push_back(seeds[si]);
+    }
+  }
+  const int32_t NPROB = (int32_t)pm.size();
+  res->p.resize(NPROB);
+  Batch b;
+  b.prof.pool = &ctx->evpool;
+  b.prof.on = ctx->opt.profile != 0;
+  g_d2h_counter = &b.d2h;
+  b.st = ctx->st;
+  b.opt = ctx->opt;
+  b.arena = &ctx->arena;
+  b.sm_count = ctx->sm;
+  b.threads = ctx->opt.threads > 0 ? ctx->opt.threads : 256;
+  b.grid = ctx->sm * (ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 2);
+  {
+    double c[4];
+    vls_constants(&ctx->opt, c);
+    Params &P = b.prm;
+    P.mu = ctx->opt.mu;
+    P.e = ctx->opt.e;
+    P.w = ctx->opt.w;
+    P.ah = ctx->opt.a * ctx->opt.a / 2.0;
+    P.dt = c[2];
+    P.s = c[3];
+    P.eps0 = ctx->opt.eps0;
+    P.one_m_eps = 1.0 - ctx->opt.eps0;
+    P.theta = ctx->opt.theta_iso;
+  }
+  std::vector<int32_t> dev_probs; // result index of each device problem
+  int64_t V = 0, NF = 0, Lc = 0;
+  for (int32_t i = 0; i < NPROB; ++i) {
+    const vls_mesh &m = meshes[pm[i]];
+    ProbResult &r = res->p[i];
+    r.nv = m.nv;
+    if (!m.X || !m.F || m.nv < 4 || m.nf < 4 || ps[i] < 0 || ps[i] >= m.nv) { r.status = VLS_EINVAL; continue; }
+    b.voff.push_back((int32_t)V);
+    b.foff.push_back((int32_t)NF);
+    const int32_t lc = (int32_t)std::min<int64_t>(256 + m.nv / 64, 1 << 24);
+    b.lbase.push_back((int32_t)Lc);
+    b.lcap.push_back(lc);
+    b.seed.push_back(ps[i]);
+    b.mesh_of.push_back(pm[i]);
+    dev_probs.push_back(i);
+    V += m.nv;
+    NF += m.nf;
+    Lc += lc;
+  }
+  if (dev_probs.empty()) { *out = res; return VLS_OK; }
+  if (V >= INT32_MAX / 2 || 3 * NF >= INT32_MAX) { delete res; return VLS_EINVAL; }
+  b.voff.push_back((int32_t)V);
+  b.foff.push_back((int32_t)NF);
+  b.P = (int32_t)dev_probs.size();
+  b.V = (int32_t)V;
+  b.NF = (int32_t)NF;
+  b.nnz = 3 * NF;
+  b.Lcap = (int32_t)Lc;
+  b.d.P = b.P;
+  b.d.V = b.V;
+  b.d.NF = b.NF;
+  b.d.nnz = b.nnz;
+  b.d.Lcap = b.Lcap;
+  b.d.record = ctx->opt.record_steps ? 1 : 0;
+  b.d.rcap = b.d.record ? std::min(ctx->opt.max_steps, 1 << 20) : 0;
+
+  cudaError_t err = cudaSuccess;
+  cudaStream_t st = b.st;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  std::vector<int32_t> stage, h_rpb, h_status, h_steps, h_nodes_cnt;
+  int32_t h_nn = 0, h_nh = 0;
+  int32_t tunnel_tau = 0;
+  std::vector<int32_t> h_hprob, h_hstep, h_hlayer, h_hnode, h_hoff, h_hn, h_hvoff, h_hvn;
+  std::vector<double> h_hlen;
+  {
+    Layout L{&ctx->arena, true};
+    layout_batch(L, b);
+    CK(ctx->arena.reserve(L.bytes));
+    ctx->arena.reset();
+    Layout L2{&ctx->arena, false};
+    layout_batch(L2, b);
+  }
+  for (int i = 0; i < 5; ++i) CK(cudaEventCreate(&ev[i]));
+  if (const char *pz = std::getenv("VLS_POISON"))
+    if (pz[0] == '1') CK(cudaMemsetAsync(ctx->arena.base, 0xab, ctx->arena.cap, st)); // debug: expose unset reads
+  {
+    Dev &d = b.d;
+    // inputs into the union graph
+    for (int32_t q = 0; q < b.P; ++q) {
+      const vls_mesh &m = meshes[b.mesh_of[q]];
+      const cudaMemcpyKind kx = m.device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+      if (!m.device) b.h2d += (int64_t)(sizeof(double) * 3 * m.nv + sizeof(int32_t) * 3 * m.nf);
+      CK(cudaMemcpyAsync(const_cast<double *>(d.X) + 3 * (int64_t)b.voff[q], m.X, sizeof(double) * 3 * m.nv, kx, st));
+      CK(cudaMemcpyAsync(const_cast<int32_t *>(d.F) + 3 * (int64_t)b.foff[q], m.F, sizeof(int32_t) * 3 * m.nf, kx, st));
+    }
+    CK(cudaMemcpyAsync(const_cast<int32_t *>(d.voff), b.voff.data(), sizeof(int32_t) * (b.P + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(const_cast<int32_t *>(d.foff), b.foff.data(), sizeof(int32_t) * (b.P + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(const_cast<int32_t *>(d.lbase), b.lbase.data(), sizeof(int32_t) * b.P, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(const_cast<int32_t *>(d.lcap), b.lcap.data(), sizeof(int32_t) * b.P, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(const_cast<int32_t *>(d.seed), b.seed.data(), sizeof(int32_t) * b.P, cudaMemcpyHostToDevice, st));
+    b.h2d += (int64_t)sizeof(int32_t) * (2 * (b.P + 1) + 3 * b.P);
+    CK(cudaEventRecord(ev[0], st));
+    // ---- a0: operator
+    int32_t *stage_d = d.pev; // 5 * P ints needed: pev holds 4 * P, spill into pupd (2 * P ints)
+    stage_d = reinterpret_cast<int32_t *>(d.ophi); // V * KMAX doubles: ample scratch before the first step
+    CK(build_operator(b, stage_d));
+    stage.resize(5 * (size_t)b.P);
+    CK(cudaMemcpyAsync(stage.data(), stage_d, sizeof(int32_t) * 5 * b.P, cudaMemcpyDeviceToHost, st));
+    b.d2h += (int64_t)sizeof(int32_t) * (6 * b.P + 1);
+    h_rpb.resize(b.P + 1);
+    for (int32_t q = 0; q <= b.P; ++q)
+      CK(cudaMemcpyAsync(&h_rpb[q], d.rp + b.voff[q], sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    h_status.assign(b.P, 0);
+    for (int32_t q = 0; q < b.P; ++q) {
+      const int32_t *s = &stage[5 * q];
+      int32_t stt = 0;
+      if (s[0]) stt = VLS_EINVAL;
+      else if (s[1]) stt = VLS_ENONORIENTABLE;
+      else if (s[2]) stt = VLS_ENOTMANIFOLD;
+      else if (s[3] != INT_MAX) stt = s[3] & 15;
+      else if (s[4] != 1) stt = VLS_EDISCONNECTED;
+      h_status[q] = stt;
+      const int64_t E = (int64_t)(h_rpb[q + 1] - h_rpb[q]) / 2;
+      const vls_mesh &m = meshes[b.mesh_of[q]];
+      res->p[dev_probs[q]].genus = (int32_t)((2 - (m.nv - E + m.nf)) / 2);
+    }
+    CK(cudaEventRecord(ev[1], st));
+    // ---- state init
+    CK(cudaMemcpyAsync(d.pstatus, h_status.data(), sizeof(int32_t) * b.P, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(d.lay, 0, sizeof(int32_t) * b.V, st));
+    CK(cudaMemsetAsync(d.phi, 0, sizeof(double) * b.V, st));
+    CK(cudaMemsetAsync(d.cover, 0xff, sizeof(int32_t) * b.V, st));
+    CK(cudaMemsetAsync(d.stamp, 0, sizeof(int32_t) * b.V, st));
+    CK(cudaMemsetAsync(d.fmark, 0, sizeof(int32_t) * b.V, st));
+    CK(cudaMemsetAsync(d.multi, 0xff, sizeof(int32_t) * b.V, st));
+    CK(cudaMemsetAsync(d.lstate, 0, sizeof(int32_t) * b.Lcap, st));
+    CK(cudaMemsetAsync(d.lfwd, 0, sizeof(int32_t) * b.Lcap, st));
+    CK(cudaMemsetAsync(d.lcnt, 0, sizeof(int32_t) * b.Lcap, st));
+    CK(cudaMemsetAsync(d.lcnt + b.Lcap, 0xff, sizeof(int32_t) * b.Lcap, st));
+    CK(cudaMemsetAsync(d.pdone, 0, sizeof(int32_t) * b.P, st));
+    CK(cudaMemsetAsync(d.lcount, 0, sizeof(int32_t) * b.P, st));
+    CK(cudaMemsetAsync(d.psteps, 0, sizeof(int32_t) * b.P, st));
+    CK(cudaMemsetAsync(d.pnodes, 0, sizeof(int32_t) * b.P, st));
+    CK(cudaMemsetAsync(d.pfront, 0, sizeof(int32_t) * 2 * b.P, st));
+    CK(cudaMemsetAsync(d.pmerge, 0, sizeof(int32_t) * b.P, st));
+    CK(cudaMemsetAsync(d.pupd, 0, sizeof(int64_t) * b.P, st));
+    CK(cudaMemsetAsync(d.pev, 0, sizeof(int32_t) * 4 * b.P, st));
+    CK(cudaMemsetAsync(d.nfront, 0, sizeof(int32_t) * 2, st));
+    CK(cudaMemsetAsync(d.ncoll, 0, sizeof(int32_t), st));
+    CK(cudaMemsetAsync(d.nnodes, 0, sizeof(int32_t), st));
+    CK(cudaMemsetAsync(d.nhand, 0, sizeof(int32_t), st));
+    CK(cudaMemsetAsync(d.nhedge, 0, sizeof(int32_t), st));
+    CK(cudaMemsetAsync(d.rhash, 0, sizeof(unsigned long long) * b.P, st));
+    CK(cudaMemsetAsync(d.rband, 0, sizeof(int32_t) * b.P, st));
+    CK(cudaMemsetAsync(d.err, 0, sizeof(int32_t) * 4, st));
+    if (d.record) CK(cudaMemsetAsync(d.rec, 0, sizeof(long long) * 4 * (size_t)b.P * d.rcap, st));
+    CK(init_state(b));
+    // ---- initial pass
+    const int sync_every = ctx->opt.sync_interval > 0 ? ctx->opt.sync_interval : 16;
+    for (int t = 1;; ++t) {
+      CK(initial_step(b, t));
+      if (t % sync_every == 0 || t >= ctx->opt.max_steps) {
+        int32_t act = 0;
+        CK(cudaMemcpyAsync(&act, d.err + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        b.d2h += (int64_t)sizeof(int32_t);
+        CK(cudaStreamSynchronize(st));
+        if (act == 0) break;
+      }
+    }
+    CK(final_checks(b));
+    CK(cudaEventRecord(ev[2], st));
+    // ---- tunnel passes
+    CK(cudaMemcpyAsync(&h_nh, d.nhand, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&h_nn, d.nnodes, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    h_status.resize(b.P);
+    CK(cudaMemcpyAsync(h_status.data(), d.pstatus, sizeof(int32_t) * b.P, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    b.d2h += (int64_t)sizeof(int32_t) * (2 + b.P);
+    h_nh = std::min(h_nh, d.hcap);
+    h_nn = std::min(h_nn, d.ncap);
+    if (!d2h(h_hprob, d.hprob, h_nh, st) || !d2h(h_hstep, d.hstep, h_nh, st) || !d2h(h_hlayer, d.hlayer, h_nh, st) ||
+        !d2h(h_hnode, d.hnode, h_nh, st) || !d2h(h_hoff, d.hoff, h_nh, st) || !d2h(h_hn, d.hn, h_nh, st) ||
+        !d2h(h_hvoff, d.hvoff, h_nh, st) || !d2h(h_hvn, d.hvn, h_nh, st) || !d2h(h_hlen, d.hlen, h_nh, st)) {
+      err = cudaErrorUnknown;
+      goto fail;
+    }
+    CK(cudaStreamSynchronize(st));
+    // passes: handles of problems whose initial pass succeeded
+    std::vector<int32_t> pass_h;
+    if (ctx->opt.tunnels)
+      for (int32_t h = 0; h < h_nh; ++h)
+        if (h_status[h_hprob[h]] == VLS_OK) pass_h.push_back(h);
+    // a pass that did not run reports (status -1, stop step 0, first vertex 0)
+    std::vector<int32_t> h_tstatus(h_nh, -1), h_tsteps(h_nh, 0), h_tb(h_nh, 0), h_tvoff(h_nh, 0), h_tvn(h_nh, 0);
+    std::vector<int32_t> h_tverts;
+    std::vector<long long> h_qupd;
+    if (!pass_h.empty()) {
+      const int32_t NP = (int32_t)pass_h.size();
+      std::vector<int32_t> pbase(NP + 1), pprob(NP), pstep(NP), pcoff(NP), pcn(NP), heoff(NP), hen(NP);
+      int64_t PV = 0, ncut = 0;
+      for (int32_t q = 0; q < NP; ++q) {
+        const int32_t h = pass_h[q], p = h_hprob[h];
+        pbase[q] = (int32_t)PV;
+        pprob[q] = p;
+        pstep[q] = h_hstep[h];
+        heoff[q] = h_hoff[h];
+        hen[q] = h_hn[h];
+        pcoff[q] = (int32_t)ncut;
+        pcn[q] = 2 * h_hn[h];
+        ncut += 2 * h_hn[h];
+        PV += b.voff[p + 1] - b.voff[p];
+      }
+      pbase[NP] = (int32_t)PV;
+      if (PV >= INT32_MAX / 2) { err = cudaErrorMemoryAllocation; goto fail; }
+      // the tunnel state lives after the batch state in the arena
+      const size_t keep = ctx->arena.used;
+      Layout L{&ctx->arena, true};
+      L.bytes = keep;
+      layout_tunnels(L, b, NP, PV, ncut);
+      if (L.bytes > ctx->arena.cap) {
+        // grow: the batch state must survive, so copy it into the new arena
+        char *old = ctx->arena.base;
+        const size_t oldcap = ctx->arena.cap;
+        char *nb = nullptr;
+        CK(cudaMalloc(&nb, L.bytes + L.bytes / 8));
+        CK(cudaMemcpyAsync(nb, old, keep, cudaMemcpyDeviceToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        // rebase every pointer of the batch: re-run the layout on the new base
+        ctx->arena.base = nb;
+        ctx->arena.cap = L.bytes + L.bytes / 8;
+        ctx->arena.reset();
+        Layout L2{&ctx->arena, false};
+        layout_batch(L2, b);
+        cudaFree(old);
+        (void)oldcap;
+      }
+      ctx->arena.used = keep;
+      Layout L3{&ctx->arena, false};
+      layout_tunnels(L3, b, NP, PV, ncut);
+      TDev &T = b.td;
+      T.err = d.err;
+      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.pbase), pbase.data(), sizeof(int32_t) * (NP + 1), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.pprob), pprob.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.pstep), pstep.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.pcoff), pcoff.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.pcn), pcn.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.heoff), heoff.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.hen), hen.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
+      CK(cudaMemsetAsync(T.flag, 0, (size_t)PV, st));
+      CK(cudaMemsetAsync(T.phi, 0, sizeof(double) * PV, st));
+      CK(cudaMemsetAsync(T.T, 0xff, sizeof(int32_t) * PV, st));
+      CK(cudaMemsetAsync(T.stamp, 0, sizeof(int32_t) * PV, st));
+      CK(cudaMemsetAsync(T.nf, 0, sizeof(int32_t) * 2, st));
+      CK(cudaMemsetAsync(T.qdone, 0, sizeof(int32_t) * NP, st));
+      CK(cudaMemsetAsync(T.qsteps, 0, sizeof(int32_t) * NP, st));
+      CK(cudaMemsetAsync(T.qstatus, 0xff, sizeof(int32_t) * NP, st));
+      k_fill_i32<<<(NP + 255) / 256, 256, 0, st>>>(T.qbstar, NP, 0x7fffffff); VLS_LAUNCH(b);
+      CK(cudaMemsetAsync(T.qcnt, 0, sizeof(int32_t) * 2 * NP, st));
+      CK(cudaMemsetAsync(T.qupd, 0, sizeof(long long) * NP, st));
+      CK(cudaMemsetAsync(T.ntverts, 0, sizeof(int32_t), st));
+      CK(cudaMemsetAsync(T.tvn, 0, sizeof(int32_t) * NP, st));
+      CK(run_tunnels(b, &tunnel_tau));
+      std::vector<int32_t> qs(NP), qst(NP), qb(NP), tvo(NP), tvn(NP);
+      int32_t ntv = 0;
+      CK(cudaMemcpyAsync(qs.data(), T.qstatus, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(qst.data(), T.qsteps, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(qb.data(), T.qbstar, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(tvo.data(), T.tvoff, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(tvn.data(), T.tvn, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&ntv, T.ntverts, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      h_qupd.resize(NP);
+      CK(cudaMemcpyAsync(h_qupd.data(), T.qupd, sizeof(long long) * NP, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      b.d2h += (int64_t)(5 * sizeof(int32_t) + sizeof(long long)) * NP + (int64_t)sizeof(int32_t);
+      ntv = std::min(ntv, T.tvcap);
+      h_tverts.resize(ntv);
+      if (ntv) CK(cudaMemcpyAsync(h_tverts.data(), T.tverts, sizeof(int32_t) * ntv, cudaMemcpyDeviceToHost, st));
+      b.d2h += (int64_t)sizeof(int32_t) * ntv;
+      for (int32_t q = 0; q < NP; ++q) {
+        const int32_t h = pass_h[q];
+        h_tstatus[h] = qs[q];
+        h_tsteps[h] = qst[q];
+        h_tb[h] = qb[q] == 0x7fffffff ? -1 : qb[q];
+        h_tvoff[h] = tvo[q];
+        h_tvn[h] = tvn[q];
+      }
+      // per-problem pass statistics
+      for (int32_t q = 0; q < NP; ++q) {
+        ProbResult &r = res->p[dev_probs[pprob[q]]];
+        r.stats.pass_updates += h_qupd[q];
+        r.tunnel_steps = std::max(r.tunnel_steps, qst[q]);
+      }
+    }
+    CK(cudaEventRecord(ev[3], st));
+    // ---- download
+    std::vector<int32_t> nkind, nstep, nprob, nlocal, lstate, lbirth, ldeath, lcount, psteps, pev, hedge, hverts;
+    std::vector<double> npos, hpts;
+    std::vector<int64_t> pupd;
+    int32_t ne = 0;
+    CK(cudaMemcpyAsync(&ne, d.nhedge, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    b.d2h += (int64_t)sizeof(int32_t);
+    ne = std::min(ne, d.ecap);
+    if (!d2h(nkind, d.nkind, h_nn, st) || !d2h(nstep, d.nstep, h_nn, st) || !d2h(nprob, d.nprob, h_nn, st) ||
+        !d2h(nlocal, d.nlocal, h_nn, st) || !d2h(npos, d.npos, 3 * (size_t)h_nn, st) ||
+        !d2h(lcount, d.lcount, b.P, st) || !d2h(psteps, d.psteps, b.P, st) || !d2h(pev, d.pev, 3 * (size_t)b.P, st) ||
+        !d2h(pupd, reinterpret_cast<const int64_t *>(d.pupd), b.P, st) || !d2h(hedge, d.hedge, 2 * (size_t)ne, st) ||
+        !d2h(hverts, d.hverts, ne, st) || !d2h(hpts, d.hpts, 3 * (size_t)ne, st) ||
+        !d2h(lstate, d.lstate, b.Lcap, st) || !d2h(lbirth, d.lbirth, b.Lcap, st) || !d2h(ldeath, d.ldeath, b.Lcap, st)) {
+      err = cudaErrorUnknown;
+      goto fail;
+    }
+    std::vector<int32_t> lay_all, cover_all;
+    std::vector<double> phi_all;
+    std::vector<long long> rec_all;
+    if (ctx->opt.keep_state) {
+      if (!d2h(lay_all, d.lay, b.V, st) || !d2h(cover_all, d.cover, b.V, st) || !d2h(phi_all, d.phi, b.V, st)) {
+        err = cudaErrorUnknown;
+        goto fail;
+      }
+    }
+    if (d.record) {
+      if (!d2h(rec_all, d.rec, (size_t)b.P * d.rcap * 4, st)) { err = cudaErrorUnknown; goto fail; }
+    }
+    CK(cudaEventRecord(ev[4], st));
+    CK(cudaStreamSynchronize(st));
+#ifdef VLS_CHECKED
+    {
+      int32_t e4[4] = {0, 0, 0, 0};
+      cudaMemcpy(e4, d.err, sizeof(e4), cudaMemcpyDeviceToHost);
+      if (e4[2] != 0) {
+        fprintf(stderr, "vls checked build: index check failed at site %d (index %d)\n", e4[2], e4[3]);
+        for (auto &r : res->p) r.status = VLS_ECUDA;
+      }
+    }
+#endif
+    // ---- repack per problem
+    const float ms_op = elapsed(ev[0], ev[1]), ms_init = elapsed(ev[1], ev[2]), ms_tun = elapsed(ev[2], ev[3]),
+                ms_dl = elapsed(ev[3], ev[4]);
+    double ms_k[2] = {0.0, 0.0};
+    int64_t n_k[2] = {0, 0};
+    for (const auto &mk : b.prof.marks) {
+      ms_k[mk.first] += elapsed((*b.prof.pool)[mk.second], (*b.prof.pool)[mk.second + 1]);
+      n_k[mk.first]++;
+    }
+    for (int32_t q = 0; q < b.P; ++q) {
+      ProbResult &r = res->p[dev_probs[q]];
+      r.status = h_status[q];
+      r.steps = psteps[q];
+      r.stats.steps = psteps[q];
+      r.stats.tunnel_steps = r.tunnel_steps;
+      r.stats.row_updates = pupd[q];
+      r.stats.merges = pev[3 * q];
+      r.stats.splits = pev[3 * q + 1];
+      r.stats.ends = pev[3 * q + 2];
+      r.stats.layers = lcount[q];
+      r.stats.ms_operator = ms_op;
+      r.stats.ms_initial = ms_init;
+      r.stats.ms_tunnel = ms_tun;
+      r.stats.ms_download = ms_dl;
+      r.stats.kernel_launches = b.launches;
+      r.stats.ms_update = ms_k[0];
+      r.stats.ms_pass_update = ms_k[1];
+      r.stats.n_update = n_k[0];
+      r.stats.n_pass_update = n_k[1];
+      r.stats.h2d_bytes = b.h2d;
+      r.stats.d2h_bytes = b.d2h;
+      const int32_t nl = lcount[q];
+      r.layers.resize(3 * (size_t)nl);
+      for (int32_t l = 1; l <= nl; ++l) {
+        const int32_t g = b.lbase[q] + l;
+        r.layers[3 * (l - 1)] = lbirth[g];
+        r.layers[3 * (l - 1) + 1] = ldeath[g];
+        r.layers[3 * (l - 1) + 2] = lstate[g];
+      }
+      if (ctx->opt.keep_state) {
+        const int32_t v0 = b.voff[q], n = b.voff[q + 1] - v0;
+        r.lay.resize(n);
+        r.phi.assign(phi_all.begin() + v0, phi_all.begin() + v0 + n);
+        r.cover.assign(cover_all.begin() + v0, cover_all.begin() + v0 + n);
+        for (int32_t i = 0; i < n; ++i) r.lay[i] = lay_all[v0 + i] ? lay_all[v0 + i] - b.lbase[q] : 0;
+      }
+      if (d.record) {
+        const int32_t n = std::min(psteps[q], d.rcap);
+        r.rec.resize(4 * (size_t)n);
+        for (int32_t i = 0; i < 4 * n; ++i) r.rec[i] = rec_all[(size_t)q * d.rcap * 4 + i];
+      }
+    }
+    // nodes in local order
+    for (int32_t q = 0; q < b.P; ++q) {
+      int32_t cnt = 0;
+      for (int32_t g = 0; g < h_nn; ++g) cnt += nprob[g] == q;
+      ProbResult &r = res->p[dev_probs[q]];
+      r.nodes.assign(2 * (size_t)cnt, 0);
+      r.npos.assign(3 * (size_t)cnt, 0.0);
+    }
+    for (int32_t g = 0; g < h_nn; ++g) {
+      ProbResult &r = res->p[dev_probs[nprob[g]]];
+      const int32_t loc = nlocal[g];
+      if (loc < 0 || 2 * (size_t)loc >= r.nodes.size()) continue;
+      r.nodes[2 * loc] = nkind[g];
+      r.nodes[2 * loc + 1] = nstep[g];
+      for (int c = 0; c < 3; ++c) r.npos[3 * loc + c] = npos[3 * (size_t)g + c];
+    }
+    // handles and tunnels, emission order per problem
+    for (int32_t h = 0; h < h_nh; ++h) {
+      const int32_t q = h_hprob[h];
+      ProbResult &r = res->p[dev_probs[q]];
+      const int32_t v0 = b.voff[q];
+      ProbResult::Handle H;
+      const int32_t o = h_hoff[h], n = h_hn[h];
+      H.edges.resize(2 * (size_t)n);
+      H.pts.resize(3 * (size_t)n);
+      for (int32_t i = 0; i < n; ++i) {
+        H.edges[2 * i] = hedge[2 * (size_t)(o + i)] - v0;
+        H.edges[2 * i + 1] = hedge[2 * (size_t)(o + i) + 1] - v0;
+        for (int c = 0; c < 3; ++c) H.pts[3 * i + c] = hpts[3 * (size_t)(o + i) + c];
+      }
+      H.verts.resize(h_hvn[h]);
+      for (int32_t i = 0; i < h_hvn[h]; ++i) H.verts[i] = hverts[h_hvoff[h] + i] - v0;
+      H.info[0] = h_hstep[h];
+      H.info[1] = h_hlayer[h];
+      H.info[2] = h_hnode[h];
+      H.len = h_hlen[h];
+      r.handles.push_back(std::move(H));
+      {
+        ProbResult::Tunnel T;
+        T.info[0] = h_tstatus[h];
+        T.info[1] = h_tsteps[h];
+        T.info[2] = h_tb[h];
+        if (h_tstatus[h] == VLS_OK)
+          T.verts.assign(h_tverts.begin() + h_tvoff[h], h_tverts.begin() + h_tvoff[h] + h_tvn[h]);
+        r.tunnels.push_back(std::move(T));
+      }
+    }
+    for (int32_t q = 0; q < b.P; ++q) {
+      ProbResult &r = res->p[dev_probs[q]];
+      if (r.status == VLS_OK)
+        for (auto &T : r.tunnels)
+          if (T.info[0] != VLS_OK) { r.status = T.info[0]; break; }
+    }
+  }
+  for (int i = 0; i < 5; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  g_d2h_counter = nullptr;
+  *out = res;
+  return VLS_OK;
+fail:
+  g_d2h_counter = nullptr;
+  for (int i = 0; i < 5; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  cudaGetLastError();
+  for (auto &r : res->p)
+    if (r.status == VLS_OK) r.status = (err == cudaErrorMemoryAllocation) ? VLS_ENOMEM : VLS_ECUDA;
+  *out = res;
+  return err == cudaErrorMemoryAllocation ? VLS_ENOMEM : VLS_ECUDA;
+}
+
+extern "C" vls_status vls_detect(vls_ctx *ctx, const vls_mesh *m, int32_t seed_vertex, vls_result **out) {
+  if (!m) return VLS_EINVAL;
+  const int32_t one = 1;
+  return vls_detect_batch(ctx, 1, m, &seed_vertex, &one, out);
+}
+
+extern "C" int32_t vls_result_count(const vls_result *r) { return r ? (int32_t)r->p.size() : 0; }
+
+#define GETP(r, p)                                                  \
+  if (!(r) || (p) < 0 || (p) >= (int32_t)(r)->p.size()) return VLS_EINVAL; \
+  const ProbResult &P_ = (r)->p[p];
+
+extern "C" vls_status vls_result_status(const vls_result *r, int32_t p) {
+  GETP(r, p);
+  return (vls_status)P_.status;
+}
+extern "C" int32_t vls_result_genus(const vls_result *r, int32_t p) {
+  if (!r || p < 0 || p >= (int32_t)r->p.size()) return -1;
+  return r->p[p].genus;
+}
+extern "C" vls_status vls_result_stats(const vls_result *r, int32_t p, vls_stats *s) {
+  GETP(r, p);
+  if (!s) return VLS_EINVAL;
+  *s = P_.stats;
+  return VLS_OK;
+}
+extern "C" int32_t vls_result_num_loops(const vls_result *r, int32_t p, int32_t kind) {
+  if (!r || p < 0 || p >= (int32_t)r->p.size()) return -1;
+  return kind == 0 ? (int32_t)r->p[p].handles.size() : (int32_t)r->p[p].tunnels.size();
+}
+extern "C" vls_status vls_result_loop(const vls_result *r, int32_t p, int32_t kind, int32_t i, const int32_t **verts,
+                                      int64_t *n, const double **pts, int64_t *npts) {
+  GETP(r, p);
+  if (kind == 0) {
+    if (i < 0 || i >= (int32_t)P_.handles.size()) return VLS_EINVAL;
+    const auto &H = P_.handles[i];
+    if (verts) *verts = H.verts.data();
+    if (n) *n = (int64_t)H.verts.size();
+    if (pts) *pts = H.pts.data();
+    if (npts) *npts = (int64_t)H.pts.size() / 3;
+    return VLS_OK;
+  }
+  if (i < 0 || i >= (int32_t)P_.tunnels.size()) return VLS_EINVAL;
+  const auto &T = P_.tunnels[i];
+  if (verts) *verts = T.verts.data();
+  if (n) *n = (int64_t)T.verts.size();
+  if (pts) *pts = nullptr;
+  if (npts) *npts = 0;
+  return VLS_OK;
+}
+extern "C" vls_status vls_result_handle(const vls_result *r, int32_t p, int32_t i, const int32_t **edges, int64_t *n,
+                                        int32_t info[3], double *length) {
+  GETP(r, p);
+  if (i < 0 || i >= (int32_t)P_.handles.size()) return VLS_EINVAL;
+  const auto &H = P_.handles[i];
+  if (edges) *edges = H.edges.data();
+  if (n) *n = (int64_t)H.edges.size() / 2;
+  if (info) std::memcpy(info, H.info, sizeof(H.info));
+  if (length) *length = H.len;
+  return VLS_OK;
+}
+extern "C" vls_status vls_result_tunnel(const vls_result *r, int32_t p, int32_t i, int32_t info[3]) {
+  GETP(r, p);
+  if (i < 0 || i >= (int32_t)P_.tunnels.size() || !info) return VLS_EINVAL;
+  std::memcpy(info, P_.tunnels[i].info, sizeof(int32_t) * 3);
+  return VLS_OK;
+}
+extern "C" vls_status vls_result_reeb(const vls_result *r, int32_t p, const int32_t **nodes, const double **pos,
+                                      int32_t *n_nodes, const int32_t **layers, int32_t *n_layers) {
+  GETP(r, p);
+  if (nodes) *nodes = P_.nodes.data();
+  if (pos) *pos = P_.npos.data();
+  if (n_nodes) *n_nodes = (int32_t)(P_.nodes.size() / 2);
+  if (layers) *layers = P_.layers.data();
+  if (n_layers) *n_layers = (int32_t)(P_.layers.size() / 3);
+  return VLS_OK;
+}
+extern "C" vls_status vls_result_state(const vls_result *r, int32_t p, const int32_t **layer, const double **phi,
+                                       const int32_t **cover, int64_t *nv) {
+  GETP(r, p);
+  if (P_.lay.empty()) return VLS_EINVAL;
+  if (layer) *layer = P_.lay.data();
+  if (phi) *phi = P_.phi.data();
+  if (cover) *cover = P_.cover.data();
+  if (nv) *nv = (int64_t)P_.lay.size();
+  return VLS_OK;
+}
+extern "C" vls_status vls_result_records(const vls_result *r, int32_t p, const int64_t **rec, int32_t *steps) {
+  GETP(r, p);
+  if (rec) *rec = P_.rec.data();
+  if (steps) *steps = (int32_t)(P_.rec.size() / 4);
+  return VLS_OK;
+}
+extern "C" void vls_result_free(vls_result *r) { delete r; }

@@ -1,0 +1,313 @@
+// tunnel.cu -- tunnel passes (Sec. 3.2), one per handle loop, all passes of a batch in the
+// same launches (Sec. 4: many single-layer passes run concurrently).
+//
+// Pass q of handle h (problem p, found at step t_h):
+//   domain   vertices covered by step t_h (the area the initial pass had reached, Sec. 3.2)
+//   cut      the handle loop's crossing edges are removed (the loop is the border)
+//   operator uniform scaled Laplacian of the cut, restricted graph (rows renormalised over the
+//            kept edges: s / d_h(v) off the diagonal, -s on it)
+//   field    one dense layer (Sec. 4: the base is 1 - phi), phi = 1 held on the inside
+//            endpoints of the loop's crossing edges, Eq. (2) with n = 2 elsewhere
+//   stop     when an outside endpoint first reaches theta_iso; b* = the smallest such vertex
+//   trace    from b*, repeatedly the unvisited kept neighbour with the least (arrival, id)
+//            whose arrival step is not larger, down to a source; the cycle is closed along
+//            the handle loop by the shorter way to a crossing edge ending at b*.
+// Only rows whose closed neighbourhood holds both phases change, so each step updates the
+// frontier rows only (exact).
+#include "vls_batch.cuh"
+
+namespace vls {
+
+namespace {
+
+constexpr int8_t F_SRC = 1, F_TGT = 2, F_VIS = 4;
+
+struct PassRow {
+  int32_t q, p, base, voff, step;
+};
+
+__device__ __forceinline__ bool in_dom(const Dev &d, int32_t u, int32_t step) {
+  const int32_t c = d.cover[u];
+  return c >= 0 && c <= step;
+}
+// half-edge slot k (v -> u) is cut in pass q
+__device__ __forceinline__ bool is_cut(const TDev &T, int32_t q, int32_t k) {
+  const int32_t *c = T.cut + T.pcoff[q];
+  int32_t lo = 0, hi = T.pcn[q] - 1;
+  while (lo <= hi) {
+    const int32_t m = (lo + hi) >> 1;
+    if (c[m] == k) return true;
+    if (c[m] < k) lo = m + 1;
+    else hi = m - 1;
+  }
+  return false;
+}
+__device__ __forceinline__ bool kept(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base, int32_t voff,
+                                     int8_t fv, int32_t u, int32_t k) {
+  if (!in_dom(d, u, step)) return false;
+  const int8_t fu = T.flag[base + (u - voff)];
+  if (((fv & F_SRC) && (fu & F_TGT)) || ((fv & F_TGT) && (fu & F_SRC))) return !is_cut(T, q, k);
+  return true;
+}
+
+// per pass: flags, sources at 1, cut slots sorted, F_0 = sources
+__global__ void k_tinit(Dev d, TDev T, int32_t *fv0, int32_t *fq0, int32_t *nF0) {
+  const int32_t q = blockIdx.x;
+  if (q >= T.NP) return;
+  const int32_t p = T.pprob[q];
+  const int32_t base = T.pbase[q], voff = d.voff[p];
+  const int32_t eo = T.heoff[q], L = T.hen[q];
+  int32_t *cut = const_cast<int32_t *>(T.cut) + T.pcoff[q];
+  const int32_t nvp = d.voff[p + 1] - voff;
+  (void)nvp; // used by the checked build's guards
+  for (int32_t i = threadIdx.x; i < L; i += blockDim.x) {
+    const int32_t a = d.hedge[2 * (int64_t)(eo + i)], b = d.hedge[2 * (int64_t)(eo + i) + 1];
+    if (!VCHK(T.err, a - voff, nvp, 301) || !VCHK(T.err, b - voff, nvp, 302)) continue;
+    T.flag[base + (a - voff)] = F_SRC;
+    T.flag[base + (b - voff)] = F_TGT;
+    T.phi[base + (a - voff)] = 1.0;
+    T.T[base + (a - voff)] = 0;
+    cut[2 * i] = slot_of(d.rp, d.col, a, b);
+    cut[2 * i + 1] = slot_of(d.rp, d.col, b, a);
+    const int32_t s = atomicAdd(nF0, 1);
+    if (!VCHK(T.err, s, T.PV, 303)) continue;
+    fv0[s] = a;
+    fq0[s] = q;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int32_t n = 2 * L;
+    for (int32_t i = 1; i < n; ++i) {
+      int32_t x = cut[i], j = i - 1;
+      while (j >= 0 && cut[j] > x) { cut[j + 1] = cut[j]; --j; }
+      cut[j + 1] = x;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_tupdate(Dev d, TDev T, Params P, const int32_t *__restrict__ fv,
+                                                 const int32_t *__restrict__ fq, const int32_t *nF_ptr) {
+  const int32_t nF = *nF_ptr;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
+    const int32_t q = fq[i];
+    const int32_t v = fv[i];
+    const int32_t p = T.pprob[q], base = T.pbase[q], voff = d.voff[p], step = T.pstep[q];
+    const int32_t idx = base + (v - voff);
+    if (!VCHK(T.err, idx, T.PV, 310)) { T.onew[i] = 0.0; continue; }
+    const int8_t fl = T.flag[idx];
+    const int32_t b = d.rp[v], e = d.rp[v + 1];
+    int32_t dh = 0;
+    for (int32_t k = b; k < e; ++k)
+      if (kept(d, T, q, step, base, voff, fl, d.col[k], k)) ++dh;
+    const double Lv = dh > 0 ? ddiv(P.s, (double)dh) : 0.0;
+    const double diag = dh > 0 ? -P.s : 0.0;
+    const double x = T.phi[idx];
+    double acc = 0.0, accb = 0.0;
+    for (int32_t k = b; k < e; ++k) {
+      const int32_t u = d.col[k];
+      if (!kept(d, T, q, step, base, voff, fl, u, k)) continue;
+      acc = dadd(acc, dmul(Lv, T.phi[base + (u - voff)]));
+    }
+    acc = dadd(acc, dmul(diag, x));
+    for (int32_t k = b; k < e; ++k) {
+      const int32_t u = d.col[k];
+      if (!kept(d, T, q, step, base, voff, fl, u, k)) continue;
+      accb = dadd(accb, dmul(Lv, dsub(1.0, T.phi[base + (u - voff)])));
+    }
+    const double xb = dsub(1.0, x);
+    accb = dadd(accb, dmul(diag, xb));
+    double out;
+    if (!vertex_update(P, 1, &x, &acc, xb, accb, &out)) out = x;
+    T.onew[i] = out;
+  }
+}
+
+__global__ void k_tapply(Dev d, TDev T, const int32_t *__restrict__ fv, const int32_t *__restrict__ fq,
+                         const int32_t *nF_ptr, int32_t tau, double theta) {
+  const int32_t nF = *nF_ptr;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
+    const int32_t q = fq[i], v = fv[i];
+    const int32_t p = T.pprob[q];
+    const int32_t idx = T.pbase[q] + (v - d.voff[p]);
+    if (!VCHK(T.err, idx, T.PV, 320)) continue;
+    const double x = T.onew[i];
+    T.phi[idx] = x;
+    if (T.T[idx] < 0 && x >= theta) {
+      T.T[idx] = tau;
+      if (T.flag[idx] & F_TGT) atomicMin(&T.qbstar[q], v - d.voff[p]);
+    }
+  }
+}
+
+__device__ __forceinline__ bool t_in_frontier(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
+                                              int32_t voff, int32_t u) {
+  if (!in_dom(d, u, step)) return false;
+  const int32_t iu = base + (u - voff);
+  const int8_t fu = T.flag[iu];
+  if (fu & F_SRC) return false;
+  const double xu = T.phi[iu];
+  bool lay = xu > 0.0, bas = dsub(1.0, xu) > 0.0;
+  for (int32_t k = d.rp[u]; k < d.rp[u + 1] && !(lay && bas); ++k) {
+    const int32_t w = d.col[k];
+    if (!kept(d, T, q, step, base, voff, fu, w, k)) continue;
+    const double xw = T.phi[base + (w - voff)];
+    if (xw > 0.0) lay = true;
+    if (dsub(1.0, xw) > 0.0) bas = true;
+  }
+  return lay && bas;
+}
+
+__global__ void k_tfrontier(Dev d, TDev T, const int32_t *__restrict__ fv, const int32_t *__restrict__ fq,
+                            const int32_t *nF_ptr, int32_t *__restrict__ nv_out, int32_t *__restrict__ nq_out,
+                            int32_t *nN_ptr, int32_t tnext) {
+  const int32_t nF = *nF_ptr;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
+    const int32_t q = fq[i];
+    if (T.qdone[q] || T.qbstar[q] != 0x7fffffff) continue;
+    const int32_t v = fv[i];
+    const int32_t p = T.pprob[q], base = T.pbase[q], voff = d.voff[p], step = T.pstep[q];
+    const int8_t fl = T.flag[base + (v - voff)];
+    const int32_t b = d.rp[v], e = d.rp[v + 1];
+    for (int32_t k = b - 1; k < e; ++k) {
+      const int32_t u = (k < b) ? v : d.col[k];
+      if (k >= b && !kept(d, T, q, step, base, voff, fl, u, k)) continue;
+      const int32_t iu = base + (u - voff);
+      if (!VCHK(T.err, iu, T.PV, 330)) continue;
+      if (atomicExch(&T.stamp[iu], tnext) == tnext) continue;
+      if (!t_in_frontier(d, T, q, step, base, voff, u)) continue;
+      const int32_t s = atomicAdd(nN_ptr, 1);
+      if (!VCHK(T.err, s, T.PV, 331)) continue;
+      nv_out[s] = u;
+      nq_out[s] = q;
+      atomicAdd(&T.qcnt[q], 1);
+    }
+  }
+}
+
+__global__ void k_tepilogue(TDev T, int32_t *cnt_cur, int32_t tau, int32_t max_steps, int32_t *nF_cur) {
+  __shared__ int32_t nact;
+  if (threadIdx.x == 0) nact = 0;
+  __syncthreads();
+  for (int32_t q = threadIdx.x; q < T.NP; q += blockDim.x) {
+    if (!T.qdone[q]) {
+      T.qsteps[q] = tau;
+      T.qupd[q] += cnt_cur[q];
+      if (T.qbstar[q] != 0x7fffffff) { T.qdone[q] = 1; T.qstatus[q] = VLS_OK; }
+      else if (T.qcnt[q] == 0) { T.qdone[q] = 1; T.qstatus[q] = VLS_ELOOPFAIL; }
+      else if (tau >= max_steps) { T.qdone[q] = 1; T.qstatus[q] = VLS_EMAXSTEPS; }
+      if (!T.qdone[q]) atomicAdd(&nact, 1);
+    }
+    cnt_cur[q] = T.qcnt[q];
+    T.qcnt[q] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *T.active = nact;
+    *nF_cur = 0;
+  }
+}
+
+// one thread per pass: greedy descent on (arrival, id), then closure along the loop
+__global__ void k_ttrace(Dev d, TDev T) {
+  for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < T.NP; q += gridDim.x * blockDim.x) {
+    if (T.qstatus[q] != VLS_OK) continue;
+    const int32_t p = T.pprob[q], base = T.pbase[q], voff = d.voff[p], step = T.pstep[q];
+    int32_t *path = T.path + base;
+    const int32_t nvp = d.voff[p + 1] - voff;
+    (void)nvp; // used by the checked build's guards
+    int32_t np = 0;
+    if (!VCHK(T.err, T.qbstar[q], nvp, 340)) { T.qstatus[q] = VLS_ELOOPFAIL; continue; }
+    int32_t x = voff + T.qbstar[q];
+    path[np++] = x;
+    T.flag[base + (x - voff)] |= F_VIS;
+    bool fail = false;
+    while (T.T[base + (x - voff)] != 0) {
+      const int32_t tx = T.T[base + (x - voff)];
+      const int8_t fx = T.flag[base + (x - voff)];
+      int32_t best = -1, tb = 0;
+      for (int32_t k = d.rp[x]; k < d.rp[x + 1]; ++k) {
+        const int32_t u = d.col[k];
+        if (!kept(d, T, q, step, base, voff, fx, u, k)) continue;
+        const int32_t iu = base + (u - voff);
+        const int32_t tu = T.T[iu];
+        if (tu < 0 || tu > tx || (T.flag[iu] & F_VIS)) continue;
+        if (best < 0 || tu < tb || (tu == tb && u < best)) { best = u; tb = tu; }
+      }
+      if (best < 0 || !VCHK(T.err, np, nvp, 341)) { fail = true; break; }
+      T.flag[base + (best - voff)] |= F_VIS;
+      path[np++] = best;
+      x = best;
+    }
+    if (fail) { T.qstatus[q] = VLS_ELOOPFAIL; continue; }
+    // close along the handle loop: crossing edge i ending at b*, loop position j of the source reached
+    const int32_t eo = T.heoff[q], m = T.hen[q];
+    const int32_t bstar = path[0];
+    int64_t bd = -1, bj = -1;
+    int dir = 1;
+    for (int32_t i = 0; i < m; ++i) {
+      if (d.hedge[2 * (int64_t)(eo + i) + 1] != bstar) continue;
+      for (int32_t j = 0; j < m; ++j) {
+        if (d.hedge[2 * (int64_t)(eo + j)] != x) continue;
+        const int64_t fwd = ((int64_t)(i - j) % m + m) % m, bwd = ((int64_t)(j - i) % m + m) % m;
+        const int64_t dd = fwd <= bwd ? fwd : bwd;
+        if (bd < 0 || dd < bd) { bd = dd; bj = j; dir = fwd <= bwd ? 1 : -1; }
+      }
+    }
+    const int32_t off = atomicAdd(T.ntverts, np + (int32_t)(bd > 0 ? bd : 0));
+    if (off + np + bd > T.tvcap) { T.qstatus[q] = VLS_ELAYERS; continue; }
+    int32_t nc = 0;
+    for (int32_t i = 0; i < np; ++i) T.tverts[off + nc++] = path[i] - voff;
+    for (int64_t s = 1; s <= bd; ++s) {
+      const int64_t ix = ((bj + dir * s) % m + m) % m;
+      const int32_t a = d.hedge[2 * (int64_t)(eo + ix)] - voff;
+      if (T.tverts[off + nc - 1] != a) T.tverts[off + nc++] = a;
+    }
+    while (nc > 1 && T.tverts[off + nc - 1] == T.tverts[off]) --nc;
+    T.tvoff[q] = off;
+    T.tvn[q] = nc;
+  }
+}
+
+}  // namespace
+
+// Runs all passes of b.td (already laid out by the host).  Returns the steps executed.
+cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out) {
+  Dev &d = b.d;
+  TDev &T = b.td;
+  cudaStream_t st = b.st;
+  int32_t *fv0 = T.fv[0], *fq0 = T.fq[0];
+  k_tinit<<<T.NP, 256, 0, st>>>(d, T, fv0, fq0, T.nf + 0); VLS_LAUNCH(b);
+  // F_1 from the sources
+  int32_t *cnt = T.qcnt + T.NP; // [NP] rows of the list in flight
+  k_tfrontier<<<b.grid, b.threads, 0, st>>>(d, T, fv0, fq0, T.nf + 0, T.fv[1], T.fq[1], T.nf + 1, 1); VLS_LAUNCH(b);
+  // after init the count of F_1 rows is in qcnt; move it to the "current" counter
+  cudaMemcpyAsync(cnt, T.qcnt, sizeof(int32_t) * T.NP, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(T.qcnt, 0, sizeof(int32_t) * T.NP, st);
+  cudaMemsetAsync(T.nf + 0, 0, sizeof(int32_t), st);
+  int32_t tau = 0;
+  const int sync_every = b.opt.sync_interval > 0 ? b.opt.sync_interval : 8;
+  for (;;) {
+    ++tau;
+    const int cur = tau & 1, nxt = cur ^ 1;
+    const long ps = b.prof.begin(st, 1);
+    k_tupdate<<<b.grid, b.threads, 0, st>>>(d, T, b.prm, T.fv[cur], T.fq[cur], T.nf + cur); VLS_LAUNCH(b);
+    b.prof.end(st, ps);
+    k_tapply<<<b.grid, b.threads, 0, st>>>(d, T, T.fv[cur], T.fq[cur], T.nf + cur, tau, b.prm.theta); VLS_LAUNCH(b);
+    k_tfrontier<<<b.grid, b.threads, 0, st>>>(d, T, T.fv[cur], T.fq[cur], T.nf + cur, T.fv[nxt], T.fq[nxt],
+                                              T.nf + nxt, tau + 1); VLS_LAUNCH(b);
+    k_tepilogue<<<1, 256, 0, st>>>(T, cnt, tau, b.opt.max_pass_steps, T.nf + cur); VLS_LAUNCH(b);
+    if (tau % sync_every == 0) {
+      int32_t act = 0;
+      cudaError_t e = cudaMemcpyAsync(&act, T.active, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+      b.d2h += (int64_t)sizeof(int32_t);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return e;
+      if (act == 0) break;
+    }
+  }
+  k_ttrace<<<(T.NP + 127) / 128, 128, 0, st>>>(d, T); VLS_LAUNCH(b);
+  *h_steps_out = tau;
+  return cudaGetLastError();
+}
+
+}  // namespace vls

@@ -1,0 +1,247 @@
+// vls_internal.cuh -- device-side data layout and helpers of the GB300 loop-shrinking library.
+//
+// Layout (one "batch" = P problems; problem = (mesh, seed vertex)):
+//   The batch is a disjoint union graph: problem p owns vertices [voff[p], voff[p+1]) and
+//   faces [foff[p], foff[p+1]) with global vertex ids, so every frontier kernel works on
+//   global ids and needs the problem id only for rare events.  Meshes shared by several
+//   seeds are replicated (state is per problem anyway).
+//   Per vertex (structure-of-arrays, 4/8-byte aligned, coalesced by vertex id):
+//     rp[V+1], col[nnz], hface[nnz]   CSR of the half-edges v->col (ascending col), the
+//                                     face holding half-edge v->col (closed oriented mesh)
+//     lay[V] int32                    layer id held (global id, 0 = base only)
+//     phi[V] double                   its value; the base is implicit: 1 - phi (Sec. 2)
+//     cover[V] int32                  first step the vertex left the pure base (-1 never)
+//   Each vertex holds at most one non-base layer at a step boundary: merges are resolved
+//   within the step (Sec. 3.1), so the transient co-presence of several layers at a vertex
+//   lives only in the per-frontier-row output buffer (KMAX entries per row).
+//   Layers have global ids; problem p owns [lbase[p], lbase[p] + lcap[p]); local id =
+//   global - lbase[p] (1 = seed layer, then creation order).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vls.h"
+
+namespace vls {
+
+constexpr int KMAX = 4;            // non-base layers that may meet at one vertex in one step
+constexpr int MAX_GROUP = 32;      // layers in one merge group
+constexpr int MAX_TRACES = 64;     // isoline traces per step (all problems)
+constexpr int TRACE_CAP = 1 << 16; // crossing edges per traced isoline
+
+enum LayerState : int32_t { L_UNUSED = 0, L_ALIVE = 1, L_DEAD = 2, L_MERGED = 3, L_ENDED = 4 };
+enum NodeKind : int32_t { N_SEED = 0, N_SPLIT = 1, N_MERGE = 2, N_END = 3 };
+
+struct Params {
+  double mu, e, w, ah, dt, s, eps0, one_m_eps, theta;
+};
+
+// Global device state of one batch.  Passed by value to kernels.
+struct Dev {
+  int32_t P;
+  int32_t V;
+  int32_t NF;
+  int64_t nnz;
+  int32_t Lcap;
+  const double *X;
+  const int32_t *F;
+  int32_t *rp, *col, *hface;
+  // problem tables
+  const int32_t *voff, *foff, *lbase, *lcap, *seed;
+  int32_t *lcount;   // layers created per problem (local ids 1..lcount)
+  int32_t *pstatus;  // per-problem status
+  int32_t *pdone;    // 1 when the initial pass of p ended
+  int32_t *psteps;   // steps executed per problem
+  int32_t *pnodes;   // Reeb nodes per problem
+  int32_t *pfront;   // frontier rows per problem of the list being built
+  int32_t *pmerge;   // 1 if p has a merge this step
+  int64_t *pupd;     // row updates per problem
+  int32_t *pev;      // [P][3] merges, splits, ends
+  // state
+  int32_t *lay;
+  double *phi;
+  int32_t *cover;
+  int32_t *stamp;    // candidate dedup stamp (step id)
+  int32_t *fmark;    // step at which the vertex was last in the frontier
+  int32_t *uf;       // union-find parent for band CCL
+  int32_t *multi;    // frontier row of a vertex holding several layers this step, else -1
+  // layers (global ids)
+  int32_t *lstate, *lfwd, *lbirth, *ldeath, *lcnt;
+  int32_t *lprob;
+  // frontier lists (double buffered) and per-row outputs
+  int32_t *front[2];
+  int32_t *nfront;   // [2]
+  int32_t *onl;      // [Vcap] layers in the new row
+  int32_t *olay;     // [Vcap * KMAX]
+  double *ophi;      // [Vcap * KMAX]
+  int32_t *coll;     // collision rows (frontier indices with >= 2 layers)
+  int32_t *ncoll;
+  // merge groups of the step
+  int32_t *ngroups;
+  int32_t *gprob, *gnew, *gnode, *gnmem, *gmem; // gmem [MAX_TRACES][MAX_GROUP]
+  int32_t *ntrace;
+  int32_t *tgroup, *tlayer;                     // per trace slot
+  int32_t *tcount;                              // crossing edges found per trace
+  int32_t *tlen;                                // ordered loop length per trace
+  unsigned long long *tkey;                     // [MAX_TRACES][TRACE_CAP] sort keys (a<<32|b)
+  int32_t *tslot;                               // [MAX_TRACES][TRACE_CAP] CSR slot of a->b
+  int32_t *tsucc, *tpar, *trank, *tnext, *tord; // [MAX_TRACES][TRACE_CAP]
+  unsigned long long *tbest;                    // per trace: packed best component
+  // Reeb nodes (global pool): kind, step, problem ; position
+  int32_t *nkind, *nstep, *nprob;
+  double *npos;
+  int32_t *nnodes;  // global node counter
+  int32_t ncap;
+  int32_t *nlocal;  // local node index within its problem
+  // handles (global pool)
+  int32_t *nhand;
+  int32_t hcap;
+  int32_t *hprob, *hstep, *hlayer, *hnode, *hoff, *hn, *hvoff, *hvn;
+  double *hlen;
+  int32_t *nhedge;  // edge pool counter
+  int32_t ecap;
+  int32_t *hedge;   // [ecap][2] global vertex ids
+  double *hpts;     // [ecap][3]
+  int32_t *hverts;  // [ecap]
+  // records
+  int32_t record;
+  int32_t rcap;
+  long long *rec;   // [P][rcap][4]
+  unsigned long long *rhash; // [P]
+  int32_t *rband;   // [P]
+  // error word
+  int32_t *err;
+};
+
+// ----------------------------------------------------------- FP64 arithmetic
+// Explicit round-to-nearest operations: no contraction into FMA, each operation rounded on
+// its own in the order written (the CPU oracle is compiled the same way).
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
+
+__device__ __forceinline__ bool frozen_state(int32_t st) { return st == L_DEAD || st == L_ENDED; }
+
+// One explicit Euler step of Eq. (2) at one vertex (base present; nl non-base layers in
+// ascending id order with own values x[] and Laplacians lap[]; base value xb, Laplacian
+// lapb).  Only pairs (layer, base) have mu_ij, e_ij != 0 (Sec. 2); e is antisymmetric so the
+// rates sum to zero; n = nl + 1 phases meet at the vertex.  Then clamp to [0,1], snap at
+// eps0 / 1 - eps0 and divide by the column sum (Sec. 2, normalisation).  Returns false if
+// the column sum vanished (values left unchanged).
+__device__ __forceinline__ bool vertex_update(const Params &P, int nl, const double *x, const double *lap,
+                                              double xb, double lapb, double *out) {
+  double mun = ddiv(P.mu, (double)(nl + 1));
+  double y[KMAX];
+  double sr = 0.0;
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i) {
+    if (i < nl) {
+      double t1 = dmul(P.w, dsub(x[i], xb));
+      double t2 = dmul(P.ah, dsub(lap[i], lapb));
+      double t3 = dmul(P.e, dsqrt(dmul(x[i], xb)));
+      double r = dmul(mun, dadd(dadd(t1, t2), t3));
+      sr = dadd(sr, r);
+      y[i] = dadd(x[i], dmul(P.dt, r));
+    }
+  }
+  double yb = dadd(xb, dmul(P.dt, -sr));
+#pragma unroll
+  for (int i = 0; i <= KMAX; ++i) {
+    if (i <= nl) {
+      double v = (i < nl) ? y[i] : yb;
+      if (v < 0.0) v = 0.0;
+      if (v > 1.0) v = 1.0;
+      if (v < P.eps0) v = 0.0;
+      if (v > P.one_m_eps) v = 1.0;
+      if (i < nl) y[i] = v;
+      else yb = v;
+    }
+  }
+  double S = yb;
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i)
+    if (i < nl) S = dadd(S, y[i]);
+  if (S == 0.0) return false;
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i)
+    if (i < nl) out[i] = ddiv(y[i], S);
+  return true;
+}
+
+// ------------------------------------------------------------ union-find
+// Lock-free union by index: the larger root is hooked under the smaller, so a component's
+// root is its smallest member (the canonical label).
+__device__ __forceinline__ int32_t uf_find(int32_t *par, int32_t x) {
+  int32_t p = par[x];
+  while (p != x) {
+    int32_t gp = par[p];
+    if (gp != p) par[x] = gp; // path halving (benign race: only shortens paths)
+    x = p;
+    p = par[x];
+  }
+  return x;
+}
+__device__ __forceinline__ void uf_unite(int32_t *par, int32_t a, int32_t b) {
+  int32_t ra = uf_find(par, a), rb = uf_find(par, b);
+  while (ra != rb) {
+    if (ra > rb) { int32_t t = ra; ra = rb; rb = t; }
+    int32_t old = atomicCAS(&par[rb], rb, ra);
+    if (old == rb) return;
+    rb = uf_find(par, old);
+    ra = uf_find(par, ra);
+  }
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// problem of a global vertex (voff ascending, P small): binary search
+__device__ __forceinline__ int32_t prob_of_vertex(const int32_t *voff, int32_t P, int32_t v) {
+  int32_t lo = 0, hi = P - 1;
+  while (lo < hi) {
+    int32_t m = (lo + hi + 1) >> 1;
+    if (voff[m] <= v) lo = m;
+    else hi = m - 1;
+  }
+  return lo;
+}
+
+// slot of half-edge u->w in the CSR (binary search over the sorted row), -1 if absent
+__device__ __forceinline__ int32_t slot_of(const int32_t *rp, const int32_t *col, int32_t u, int32_t w) {
+  int32_t lo = rp[u], hi = rp[u + 1] - 1;
+  while (lo <= hi) {
+    int32_t m = (lo + hi) >> 1;
+    int32_t c = col[m];
+    if (c == w) return m;
+    if (c < w) lo = m + 1;
+    else hi = m - 1;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ void set_err(int32_t *err, int32_t code) { atomicCAS(err, 0, code); }
+
+// Checked builds (-DVLS_CHECKED): every guarded index is range-checked; the first violation
+// records (site, index) in err[2], err[3] and the access is skipped.  Unchecked builds
+// compile the guard to `true`.
+#ifdef VLS_CHECKED
+__device__ __forceinline__ bool vchk(int32_t *err, long long i, long long n, int site) {
+  if (i >= 0 && i < n) return true;
+  if (atomicCAS(err + 2, 0, site) == 0) err[3] = (int32_t)i;
+  return false;
+}
+#define VCHK(err, i, n, site) ::vls::vchk((err), (long long)(i), (long long)(n), (site))
+#else
+#define VCHK(err, i, n, site) true
+#endif
+
+// ------------------------------------------------------------------ host side
+struct Batch; // defined in api.cu
+
+cudaError_t launch_operator(Batch &b, int32_t *status);
+}  // namespace vls

@@ -1,0 +1,49 @@
+"""Parity assertions between a GPU result (paper_2105_13168_gb300.vls.Problem) and the CPU
+oracle (oracle.Result).  Integer work (events, labels, loops, cover steps, band hashes) is
+compared exactly; FP64 values with a relative bound of 1e-12 (expected bit-identical: both
+sides round every operation alone in the same order); Reeb positions are means summed in a
+different order on the GPU, compared to 1e-12 relative of the coordinate scale."""
+import numpy as np
+
+FP64_REL = 1e-12
+
+
+def assert_close(a, b, rel=FP64_REL, what=""):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    assert a.shape == b.shape, (what, a.shape, b.shape)
+    if a.size == 0:
+        return
+    scale = max(1.0, float(np.abs(b).max()))
+    err = float(np.abs(a - b).max())
+    assert err <= rel * scale, f"{what}: max abs err {err:.3e} > {rel:.1e} * {scale:.3e}"
+
+
+def assert_parity(g, o, state=True, records=True):
+    assert g.status == o.status, (g.status_name, o.status_name)
+    assert g.genus == o.genus
+    if records and o.records is not None and len(o.records):
+        n = min(len(g.records), len(o.records))
+        assert len(g.records) == len(o.records), (len(g.records), len(o.records))
+        bad = np.nonzero((g.records[:n] != o.records[:n]).any(axis=1))[0]
+        assert bad.size == 0, f"first divergent step {bad[0] + 1}: gpu {g.records[bad[0]]} oracle {o.records[bad[0]]}"
+    assert g.events() == o.events(), f"events: gpu {g.events()[:12]} oracle {o.events()[:12]}"
+    assert np.array_equal(g.layers, o.layers)
+    assert_close(g.node_pos, o.node_pos, what="reeb node positions")
+    assert len(g.handles) == len(o.handles)
+    for i, (hg, ho) in enumerate(zip(g.handles, o.handles)):
+        assert (hg.step, hg.layer, hg.node) == (ho.step, ho.layer, ho.node), \
+            f"handle {i}: gpu {(hg.step, hg.layer, hg.node, len(hg.edges))} oracle {(ho.step, ho.layer, ho.node, len(ho.edges))}"
+        assert np.array_equal(hg.edges, ho.edges), f"handle {i} crossing edges differ"
+        assert np.array_equal(hg.verts, ho.verts), f"handle {i} vertices differ"
+        assert_close(hg.points, ho.points, what=f"handle {i} points")
+        assert abs(hg.length - ho.length) <= FP64_REL * max(1.0, ho.length)
+    assert len(g.tunnels) == len(o.tunnels)
+    for i, (tg, to) in enumerate(zip(g.tunnels, o.tunnels)):
+        assert (tg.status, tg.stop_step, tg.bstar) == (to.status, to.stop_step, to.bstar), \
+            f"tunnel {i}: gpu {(tg.status, tg.stop_step, tg.bstar)} oracle {(to.status, to.stop_step, to.bstar)}"
+        assert np.array_equal(tg.verts, to.verts), f"tunnel {i} differs"
+    if state and g.phi is not None:
+        assert np.array_equal(g.layer, o.layer)
+        assert np.array_equal(g.cover, o.cover)
+        assert_close(g.phi, o.phi, what="phi")

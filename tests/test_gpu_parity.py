@@ -1,0 +1,135 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on the same seeded
+inputs (element by element: per-step frontier/band sizes and band hashes, every event, layer
+table, Reeb node, handle loop, tunnel loop, final state and cover steps)."""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+from parity import assert_close, assert_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vls():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_13168_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_2105_13168_gb300 as v
+
+    v.load()
+    return v
+
+
+def run_gpu(vls, problems, **kw):
+    return vls.detect(problems, keep_state=1, record_steps=1, **kw)
+
+
+def run_orc(m, s, **kw):
+    return oracle.detect(m, s, record_steps=1, **kw)
+
+
+def test_torus_full_parity(vls):
+    m = meshgen.torus(64, 32, 2.0, 0.7)
+    s = meshgen.seed_vertex(0, m.nv)
+    g = run_gpu(vls, [(m, [s])])[0]
+    o = run_orc(m, s)
+    assert o.status == 0
+    assert_parity(g, o)
+
+
+@pytest.mark.parametrize("steps", [1, 2, 7, 60, 108, 109, 150, 177, 178])
+def test_torus_state_each_phase(vls, steps):
+    """State after exactly `steps` steps (before/at/after the split and the merge)."""
+    m = meshgen.torus(64, 32, 2.0, 0.7)
+    s = meshgen.seed_vertex(0, m.nv)
+    g = run_gpu(vls, [(m, [s])], max_steps=steps, tunnels=0)[0]
+    o = run_orc(m, s, max_steps=steps, tunnels=0)
+    assert_parity(g, o)
+
+
+@pytest.mark.parametrize("name", ["chain2", "chain3", "capsules", "sphere", "torus_small"])
+def test_shapes_full_parity(vls, name):
+    m = {"chain2": lambda: meshgen.tube_chain(2, 64), "chain3": lambda: meshgen.tube_chain(3, 80),
+         "capsules": lambda: meshgen.capsules(5, 60), "sphere": lambda: meshgen.sphere(28),
+         "torus_small": lambda: meshgen.torus(24, 12)}[name]()
+    for sd in range(2):
+        s = meshgen.seed_vertex(sd, m.nv)
+        g = run_gpu(vls, [(m, [s])])[0]
+        o = run_orc(m, s)
+        assert_parity(g, o)
+
+
+def test_batch_equals_single_runs(vls):
+    """Problems of uneven size in one batch give exactly their solo results."""
+    meshes = [meshgen.torus(32, 16), meshgen.tube_chain(2, 56), meshgen.capsules(4, 48)]
+    probs = [(m, [meshgen.seed_vertex(3 * i + k, m.nv) for k in range(2)]) for i, m in enumerate(meshes)]
+    batched = run_gpu(vls, probs)
+    i = 0
+    for m, seeds in probs:
+        for s in seeds:
+            solo = run_gpu(vls, [(m, [s])])[0]
+            o = run_orc(m, s)
+            assert_parity(batched[i], o)
+            assert_parity(solo, o)
+            i += 1
+
+
+def test_device_pointers_equal_host(vls):
+    import torch
+
+    m = meshgen.tube_chain(2, 56)
+    s = meshgen.seed_vertex(5, m.nv)
+    o = run_orc(m, s)
+    ctx = vls.vls_create(vls.vls_default_options(keep_state=1, record_steps=1))
+    try:
+        X, F = torch.from_numpy(m.X).cuda(), torch.from_numpy(m.F).cuda()
+        res = vls.vls_detect(ctx, X, F, s, device=True)
+        g = vls.read_result(res)[0]
+        vls.vls_result_free(res)
+        res = vls.vls_detect(ctx, m.X, m.F, s, device=False)
+        h = vls.read_result(res)[0]
+        vls.vls_result_free(res)
+    finally:
+        vls.vls_destroy(ctx)
+    assert_parity(g, o)
+    assert_parity(h, o)
+
+
+def test_invalid_meshes_statuses(vls):
+    t = meshgen.torus(16, 8)
+    bad = []
+    bad.append(meshgen.Mesh(t.X, t.F[1:]))                         # open
+    F = t.F.copy(); F[0] = F[0][::-1]; bad.append(meshgen.Mesh(t.X, F))  # flipped face
+    bad.append(meshgen.Mesh(np.concatenate([t.X, t.X + 9]), np.concatenate([t.F, t.F + t.nv])))  # 2 parts
+    F = t.F.copy(); F[2, 2] = t.nv; bad.append(meshgen.Mesh(t.X, F))     # index out of range
+    probs = [(m, [0]) for m in bad] + [(t, [t.nv + 5])]               # + seed out of range
+    gs = run_gpu(vls, probs)
+    for (m, seeds), g in zip(probs, gs):
+        o = oracle.detect(m, seeds[0])
+        assert g.status == o.status, (g.status_name, o.status_name)
+
+
+def test_step_limit_and_no_tunnels(vls):
+    m = meshgen.tube_chain(2, 56)
+    s = meshgen.seed_vertex(1, m.nv)
+    g = run_gpu(vls, [(m, [s])], max_steps=123)[0]
+    o = run_orc(m, s, max_steps=123)
+    assert g.status_name == "EMAXSTEPS"
+    assert_parity(g, o)
+
+
+def test_stats_are_consistent(vls):
+    m = meshgen.tube_chain(3, 64)
+    s = meshgen.seed_vertex(2, m.nv)
+    g = run_gpu(vls, [(m, [s])])[0]
+    o = run_orc(m, s)
+    assert g.stats["row_updates"] == o.counters[0]
+    assert g.stats["pass_updates"] == o.counters[2]
+    assert g.stats["merges"] == o.counters[3] and g.stats["splits"] == o.counters[4]
+    assert g.stats["ends"] == o.counters[5] and g.stats["layers"] == o.counters[6]
+    assert g.stats["steps"] == o.steps
