@@ -49,6 +49,10 @@ def parse_args():
     ap.add_argument("--scale", type=float, default=1.0, help="workload grid scale (1.0 = full size)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=2, help="problems timed for the CPU baseline")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one detection of the workload bounded to --max-steps initial steps (for profilers)")
+    ap.add_argument("--max-steps", type=int, default=400)
+    ap.add_argument("--max-pass-steps", type=int, default=200)
     return ap.parse_args()
 
 
@@ -185,10 +189,37 @@ def run_reference(args):
     return 0
 
 
+def run_profile_case(args):
+    """One detection of the workload with bounded step counts, device inputs, no extra runs."""
+    import torch
+
+    import meshgen
+    import paper_2105_13168_gb300 as vls
+
+    torch.cuda.set_device(0)
+    probs = meshgen.workload(2, args.scale)
+    cfg, faces = workload_desc(probs)
+    dev = torch.device("cuda", 0)
+    meshes_dev = [(torch.from_numpy(m.X).to(dev), torch.from_numpy(m.F).to(dev)) for m, _ in probs]
+    opts = vls.vls_default_options(max_steps=args.max_steps, max_pass_steps=args.max_pass_steps)
+    ctx = vls.vls_create(opts, torch.cuda.current_stream().cuda_stream)
+    res = vls.vls_detect_batch(ctx, meshes_dev, [s for _, s in probs], device=True)
+    out = vls.read_result(res)
+    vls.vls_result_free(res)
+    vls.vls_destroy(ctx)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": cfg, "max_steps": args.max_steps,
+                      "status": [p.status_name for p in out], "launches": out[0].stats["kernel_launches"],
+                      "rows": sum(p.stats["row_updates"] for p in out)}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args)
     import numpy as np
     import torch
 
@@ -216,8 +247,7 @@ def main():
         cpu = cpu_baseline(probs, args.cpu_sample)
 
     stream = torch.cuda.current_stream()
-    opts = vls.vls_default_options(profile=1)
-    ctx = vls.vls_create(opts, stream.cuda_stream)
+    ctx = vls.vls_create(vls.vls_default_options(), stream.cuda_stream)
     meshes_dev = [(torch.from_numpy(m.X).to(dev), torch.from_numpy(m.F).to(dev)) for m, _ in probs]
     seeds = [s for _, s in probs]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -242,7 +272,6 @@ def main():
     if sampler:
         sampler.start()
     step_ms, launches = [], 0
-    upd_ms = upd_n = rows = 0
     for _ in range(args.steps):
         flush.fill_(1)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -252,11 +281,7 @@ def main():
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        st = out[0].stats
-        launches += st["kernel_launches"]
-        upd_ms += st["ms_update"]
-        upd_n += st["n_update"]
-        rows += sum(p.stats["row_updates"] for p in out)
+        launches += out[0].stats["kernel_launches"]
         assert all(p.status == 0 for p in out), [p.status_name for p in out]
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
@@ -283,6 +308,17 @@ def main():
         h2d, d2h = out[0].stats["h2d_bytes"], out[0].stats["d2h_bytes"]
     e2e_v = faces * world / (sum(e2e_s) / len(e2e_s))
     vls.vls_destroy(ctx)
+    # ---- kernel timing pass: the same workload with CUDA events around every launch of the
+    # frontier update kernel (host-driven launches so that each launch can be bracketed)
+    pctx = vls.vls_create(vls.vls_default_options(profile=1), stream.cuda_stream)
+    flush.fill_(1)
+    res = vls.vls_detect_batch(pctx, meshes_dev, seeds, device=True)
+    pout = vls.read_result(res)
+    vls.vls_result_free(res)
+    vls.vls_destroy(pctx)
+    upd_ms, upd_n = pout[0].stats["ms_update"], pout[0].stats["n_update"]
+    rows = sum(p.stats["row_updates"] for p in pout)
+    prof_step_ms = pout[0].stats["ms_operator"] + pout[0].stats["ms_initial"] + pout[0].stats["ms_tunnel"]
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -298,7 +334,9 @@ def main():
             "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
             "traffic": update_kernel_traffic(), "bytes_per_row": round(bytes_per_row, 2),
             "rows_per_launch": round(rows_per_launch, 1), "launch_us": launch_s * 1e6 if launch_s else None,
-            "share_of_step": (upd_ms / args.steps) / ms if ms else None}
+            "launches": upd_n, "share_of_timed_step": (upd_ms / ms) if ms else None,
+            "method": "CUDA events around each launch in a kernel-timing pass of the same workload "
+                      "(host-driven launches); the timed steps run the device-driven graph"}
     cfg = dict(cfg, precision="fp64", inputs="resident in HBM (device pointers) for value; pinned host for e2e",
                l2="flushed by a 256 MiB write before every timed step",
                parallelism=f"{world} GPU(s), each its own copy of the batch" if world > 1 else "1 GPU")

@@ -167,6 +167,10 @@ VLS_API vls_status vls_result_reeb(const vls_result *r, int32_t p, const int32_t
 /* Final per-vertex state (keep_state = 1): layer id (0 none), value, cover step (-1 never). */
 VLS_API vls_status vls_result_state(const vls_result *r, int32_t p, const int32_t **layer, const double **phi,
                             const int32_t **cover, int64_t *nv);
+/* profile = 1: per-kernel device time of the batch from CUDA events around every launch
+ * (host-driven launches).  names[i] (static strings), launches[i], ms[i] for i < *n. */
+VLS_API vls_status vls_result_kernel_times(const vls_result *r, const char *const **names, const int64_t **launches,
+                                           const double **ms, int32_t *n);
 /* Per-step records (record_steps = 1): [steps][4] = frontier rows, band vertices, band hash
  * low 32 bits, high 32 bits. */
 VLS_API vls_status vls_result_records(const vls_result *r, int32_t p, const int64_t **rec, int32_t *steps);

@@ -49,6 +49,8 @@ struct ProbResult {
 
 struct vls_result {
   std::vector<ProbResult> p;
+  std::vector<int64_t> klaunch;
+  std::vector<double> kms;
 };
 
 struct vls_ctx {
@@ -252,6 +254,9 @@ void layout_batch(Layout &L, Batch &b) {
   d.rhash = L.take<unsigned long long>(P);
   d.rband = L.take<int32_t>(P);
   d.err = L.take<int32_t>(4);
+  d.ctl = L.take<int32_t>(CTL_SIZE);
+  d.nalive = L.take<int32_t>(P);
+  d.nbl = L.take<int32_t>(P);
 }
 
 void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut) {
@@ -338,13 +343,25 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
   Batch b;
   b.prof.pool = &ctx->evpool;
   b.prof.on = ctx->opt.profile != 0;
+  {
+    const char *hl = std::getenv("VLS_HOST_LOOP");
+    // kernel timing needs CUDA events around single launches: profiling runs the host loop
+    b.host_loop = ctx->opt.profile != 0 || (hl && hl[0] == '1');
+  }
   g_d2h_counter = &b.d2h;
   b.st = ctx->st;
   b.opt = ctx->opt;
   b.arena = &ctx->arena;
   b.sm_count = ctx->sm;
-  b.threads = ctx->opt.threads > 0 ? ctx->opt.threads : 256;
-  b.grid = ctx->sm * (ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 2);
+  // row kernels (one thread per frontier row): small blocks spread a few thousand rows over
+  // every SM; group kernels (16 lanes per row): 256-thread blocks
+  b.threads = ctx->opt.threads > 0 ? ctx->opt.threads : 128;
+  b.grid = ctx->sm * (ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 16);
+  b.gthreads = 256;
+  b.ggrid = ctx->sm * 4;
+  configure_initial(b);
+  configure_events(b);
+  configure_tunnel(b);
   {
     double c[4];
     vls_constants(&ctx->opt, c);
@@ -358,6 +375,10 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     P.eps0 = ctx->opt.eps0;
     P.one_m_eps = 1.0 - ctx->opt.eps0;
     P.theta = ctx->opt.theta_iso;
+    P.lv[0] = 0.0;
+    for (int k = 1; k <= LV_MAX; ++k) P.lv[k] = P.s / (double)k;
+    P.mun[0] = 0.0;
+    for (int k = 1; k <= KMAX + 1; ++k) P.mun[k] = P.mu / (double)k;
   }
   std::vector<int32_t> dev_probs; // result index of each device problem
   int64_t V = 0, NF = 0, Lc = 0;
@@ -485,19 +506,39 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     CK(cudaMemsetAsync(d.rhash, 0, sizeof(unsigned long long) * b.P, st));
     CK(cudaMemsetAsync(d.rband, 0, sizeof(int32_t) * b.P, st));
     CK(cudaMemsetAsync(d.err, 0, sizeof(int32_t) * 4, st));
+    CK(cudaMemsetAsync(d.nalive, 0, sizeof(int32_t) * b.P, st));
+    CK(cudaMemsetAsync(d.nbl, 0, sizeof(int32_t) * b.P, st));
+    {
+      int32_t ctl[CTL_SIZE] = {};
+      ctl[CTL_LIMIT] = ctx->opt.max_steps;
+      ctl[CTL_TLIMIT] = ctx->opt.max_pass_steps;
+      CK(cudaMemcpyAsync(d.ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, st));
+      b.h2d += (int64_t)sizeof(ctl);
+    }
     if (d.record) CK(cudaMemsetAsync(d.rec, 0, sizeof(long long) * 4 * (size_t)b.P * d.rcap, st));
     CK(init_state(b));
     // ---- initial pass
-    const int sync_every = ctx->opt.sync_interval > 0 ? ctx->opt.sync_interval : 16;
-    for (int t = 1;; ++t) {
-      CK(initial_step(b, t));
-      if (t % sync_every == 0 || t >= ctx->opt.max_steps) {
-        int32_t act = 0;
-        CK(cudaMemcpyAsync(&act, d.err + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        b.d2h += (int64_t)sizeof(int32_t);
-        CK(cudaStreamSynchronize(st));
-        if (act == 0) break;
+    if (b.host_loop) {
+      const int sync_every = ctx->opt.sync_interval > 0 ? ctx->opt.sync_interval : 16;
+      for (int t = 1;; ++t) {
+        CK(initial_step_host(b));
+        if (t % sync_every == 0 || t >= ctx->opt.max_steps) {
+          int32_t act = 0;
+          CK(cudaMemcpyAsync(&act, d.ctl + CTL_ACTIVE, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+          b.d2h += (int64_t)sizeof(int32_t);
+          CK(cudaStreamSynchronize(st));
+          if (act == 0) break;
+        }
       }
+    } else {
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      err = build_initial_graph(b, &g);
+      if (err == cudaSuccess) err = cudaGraphInstantiate(&ge, g, 0);
+      if (err == cudaSuccess) err = cudaGraphLaunch(ge, st);
+      if (ge) cudaGraphExecDestroy(ge);
+      if (g) cudaGraphDestroy(g);
+      if (err != cudaSuccess) goto fail;
     }
     CK(final_checks(b));
     CK(cudaEventRecord(ev[2], st));
@@ -654,8 +695,18 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     if (d.record) {
       if (!d2h(rec_all, d.rec, (size_t)b.P * d.rcap * 4, st)) { err = cudaErrorUnknown; goto fail; }
     }
+    int32_t h_ctl[CTL_SIZE] = {};
+    CK(cudaMemcpyAsync(h_ctl, d.ctl, sizeof(h_ctl), cudaMemcpyDeviceToHost, st));
+    b.d2h += (int64_t)sizeof(h_ctl);
     CK(cudaEventRecord(ev[4], st));
     CK(cudaStreamSynchronize(st));
+    if (!b.host_loop) {
+      // kernels run inside the graphs: 6 per initial step, 4 per merge phase, 1 per split
+      // phase, 4 per tunnel step
+      const int64_t steps = h_ctl[CTL_T] - 1;
+      b.launches += 6 * steps + 4 * (int64_t)h_ctl[CTL_NMERGE] + (int64_t)h_ctl[CTL_NSPLIT];
+      if (tunnel_tau > 0) b.launches += 4 * (int64_t)tunnel_tau;
+    }
 #ifdef VLS_CHECKED
     {
       int32_t e4[4] = {0, 0, 0, 0};
@@ -669,12 +720,14 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     // ---- repack per problem
     const float ms_op = elapsed(ev[0], ev[1]), ms_init = elapsed(ev[1], ev[2]), ms_tun = elapsed(ev[2], ev[3]),
                 ms_dl = elapsed(ev[3], ev[4]);
-    double ms_k[2] = {0.0, 0.0};
-    int64_t n_k[2] = {0, 0};
+    double ms_k[KK_COUNT_KINDS] = {};
+    int64_t n_k[KK_COUNT_KINDS] = {};
     for (const auto &mk : b.prof.marks) {
       ms_k[mk.first] += elapsed((*b.prof.pool)[mk.second], (*b.prof.pool)[mk.second + 1]);
       n_k[mk.first]++;
     }
+    res->klaunch.assign(n_k, n_k + KK_COUNT_KINDS);
+    res->kms.assign(ms_k, ms_k + KK_COUNT_KINDS);
     for (int32_t q = 0; q < b.P; ++q) {
       ProbResult &r = res->p[dev_probs[q]];
       r.status = h_status[q];
@@ -691,10 +744,10 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       r.stats.ms_tunnel = ms_tun;
       r.stats.ms_download = ms_dl;
       r.stats.kernel_launches = b.launches;
-      r.stats.ms_update = ms_k[0];
-      r.stats.ms_pass_update = ms_k[1];
-      r.stats.n_update = n_k[0];
-      r.stats.n_pass_update = n_k[1];
+      r.stats.ms_update = ms_k[KK_UPDATE];
+      r.stats.ms_pass_update = ms_k[KK_TUPDATE];
+      r.stats.n_update = n_k[KK_UPDATE];
+      r.stats.n_pass_update = n_k[KK_TUPDATE];
       r.stats.h2d_bytes = b.h2d;
       r.stats.d2h_bytes = b.d2h;
       const int32_t nl = lcount[q];
@@ -881,4 +934,14 @@ extern "C" vls_status vls_result_records(const vls_result *r, int32_t p, const i
   if (steps) *steps = (int32_t)(P_.rec.size() / 4);
   return VLS_OK;
 }
+extern "C" vls_status vls_result_kernel_times(const vls_result *r, const char *const **names, const int64_t **launches,
+                                              const double **ms, int32_t *n) {
+  if (!r) return VLS_EINVAL;
+  if (names) *names = kKernelNames;
+  if (launches) *launches = r->klaunch.empty() ? nullptr : r->klaunch.data();
+  if (ms) *ms = r->kms.empty() ? nullptr : r->kms.data();
+  if (n) *n = r->klaunch.empty() ? 0 : (int32_t)KK_COUNT_KINDS;
+  return VLS_OK;
+}
+
 extern "C" void vls_result_free(vls_result *r) { delete r; }

@@ -52,8 +52,7 @@ __device__ __forceinline__ bool in_band_of(const Dev &d, int32_t u, int32_t l) {
     return false;
   }
   if (d.lay[u] != l) return false;
-  const double x = d.phi[u];
-  return x > 0.0 && x < 1.0;
+  return val_band(d.phi[u]);
 }
 
 // block-wide FP64 sum of three coordinates and a count
@@ -107,8 +106,9 @@ __device__ int32_t new_layer(Dev &d, int32_t p, int32_t birth_local) {
 // ------------------------------------------------------------------ merge groups
 // One thread: the collision rows of a step are few.  `luf` is a union-find parent array over
 // global layer ids (-1 = untouched), reset to -1 for every layer it touched before returning.
-__global__ void k_merge_groups(Dev d, const int32_t *__restrict__ fv, int32_t t, int32_t *luf, int32_t *touched) {
+__global__ void k_merge_groups(Dev d, int32_t *luf, int32_t *touched) {
   if (threadIdx.x != 0) return;
+  const int32_t t = d.ctl[CTL_T];
   const int32_t nc = *d.ncoll;
   *d.ngroups = 0;
   *d.ntrace = 0;
@@ -179,10 +179,13 @@ __global__ void k_merge_groups(Dev d, const int32_t *__restrict__ fv, int32_t t,
 // Successor of (a, b): the other crossing edge of the face holding half-edge a -> b (the
 // face on its left); components are cycles of the successor map.  The largest component
 // (ties: smallest first edge in (a, b) order) is ordered from its smallest edge.
-__global__ void __launch_bounds__(1024) k_trace(Dev d, Params P, const int32_t *__restrict__ fv,
-                                                const int32_t *__restrict__ fp, const int32_t *nF_ptr, int32_t t) {
+__global__ void __launch_bounds__(1024) k_trace(Dev d, Params P) {
   const int32_t tb = blockIdx.x;
   if (tb >= *d.ntrace) return;
+  const int32_t t = d.ctl[CTL_T], cur = t & 1;
+  const int32_t *__restrict__ fv = d.front[cur];
+  const int32_t *__restrict__ fp = d.front[cur] + d.V;
+  const int32_t *nF_ptr = d.nfront + cur;
   const int32_t g = d.tgroup[tb], l = d.tlayer[tb], p = d.gprob[g];
   const double th = P.theta;
   unsigned long long *key = d.tkey + (int64_t)tb * TRACE_CAP;
@@ -348,11 +351,13 @@ __global__ void __launch_bounds__(1024) k_trace(Dev d, Params P, const int32_t *
 }
 
 // ------------------------------------------------------------------ merge finish
-__global__ void __launch_bounds__(1024) k_merge_finish(Dev d, Params P, const int32_t *__restrict__ fv,
-                                                       const int32_t *__restrict__ fp, const int32_t *nF_ptr,
-                                                       int32_t t) {
+__global__ void __launch_bounds__(1024) k_merge_finish(Dev d, Params P) {
   const int32_t ng = *d.ngroups;
   if (ng == 0) return;
+  const int32_t t = d.ctl[CTL_T], cur = t & 1;
+  const int32_t *__restrict__ fv = d.front[cur];
+  const int32_t *__restrict__ fp = d.front[cur] + d.V;
+  const int32_t *nF_ptr = d.nfront + cur;
   const int32_t nF = *nF_ptr;
   const int32_t ntr = *d.ntrace;
   const double th = P.theta;
@@ -465,6 +470,7 @@ __global__ void __launch_bounds__(1024) k_merge_finish(Dev d, Params P, const in
         d.lfwd[mem[j]] = N;
         d.ldeath[mem[j]] = s_nodeloc;
       }
+      d.nalive[p] += 1 - nm;
     }
     __syncthreads();
     const int32_t N = s_N;
@@ -500,10 +506,13 @@ __global__ void k_relabel(Dev d) {
 }
 
 // ------------------------------------------------------------------ splits / extinctions
-__global__ void __launch_bounds__(256) k_split(Dev d, const int32_t *__restrict__ fv, const int32_t *__restrict__ fp,
-                                               const int32_t *nF_ptr, int32_t t) {
+__global__ void __launch_bounds__(256) k_split(Dev d) {
   const int32_t p = blockIdx.x;
   if (p >= d.P || d.pdone[p]) return;
+  const int32_t t = d.ctl[CTL_T], cur = t & 1;
+  const int32_t *__restrict__ fv = d.front[cur];
+  const int32_t *__restrict__ fp = d.front[cur] + d.V;
+  const int32_t *nF_ptr = d.nfront + cur;
   const int32_t nF = *nF_ptr;
   constexpr int MAXC = 64;
   __shared__ int32_t roots[MAXC], child[MAXC];
@@ -541,6 +550,7 @@ __global__ void __launch_bounds__(256) k_split(Dev d, const int32_t *__restrict_
           d.ldeath[l] = d.nlocal[node];
         }
         d.lstate[l] = L_ENDED;
+        d.nalive[p] -= 1;
         d.pev[3 * p + 2]++;
       }
       __syncthreads();
@@ -576,6 +586,7 @@ __global__ void __launch_bounds__(256) k_split(Dev d, const int32_t *__restrict_
       d.lstate[l] = L_DEAD;
       d.ldeath[l] = s_nodeloc;
       for (int32_t i = 0; i < nr; ++i) child[i] = new_layer(d, p, s_nodeloc);
+      d.nalive[p] += nr - 1;
       s_nroot = nr;
       d.pev[3 * p + 1]++;
     }
@@ -598,23 +609,51 @@ __global__ void __launch_bounds__(256) k_split(Dev d, const int32_t *__restrict_
 
 }  // namespace
 
-cudaError_t merge_phase(Batch &b, int t, int cur) {
+// IF(merge) body: groups -> traces (one block each) -> finish -> relabel
+cudaError_t add_merge_nodes(Batch &b, cudaGraph_t g) {
+  Dev &d = b.d;
+  int32_t *luf = d.lcnt + b.Lcap;                  // [Lcap] layer union-find scratch (init -1)
+  int32_t *touched = d.lcnt + 2 * (size_t)b.Lcap;  // [Lcap]
+  cudaGraphNode_t n0, n1, n2, n3;
+  cudaError_t e = add_kernel(&n0, g, nullptr, 0, k_merge_groups, dim3(1), dim3(32), d, luf, touched);
+  if (e == cudaSuccess) e = add_kernel(&n1, g, &n0, 1, k_trace, dim3(MAX_TRACES), dim3(1024), d, b.prm);
+  if (e == cudaSuccess) e = add_kernel(&n2, g, &n1, 1, k_merge_finish, dim3(1), dim3(1024), d, b.prm);
+  if (e == cudaSuccess) e = add_kernel(&n3, g, &n2, 1, k_relabel, dim3(b.cfg[KK_RELABEL].grid), dim3(b.cfg[KK_RELABEL].threads), d);
+  return e;
+}
+
+// IF(split / extinction) body
+cudaError_t add_split_nodes(Batch &b, cudaGraph_t g) {
+  cudaGraphNode_t n0;
+  return add_kernel(&n0, g, nullptr, 0, k_split, dim3(b.P), dim3(256), b.d);
+}
+
+void configure_events(Batch &b) { b.cfg[KK_RELABEL] = wave_cfg(b, k_relabel, 256); }
+
+cudaError_t merge_phase_host(Batch &b) {
   Dev &d = b.d;
   cudaStream_t st = b.st;
-  int32_t *fv = d.front[cur], *fp = d.front[cur] + b.V, *nF = d.nfront + cur;
-  int32_t *luf = d.lcnt + b.Lcap;            // [Lcap] layer union-find scratch (init -1)
-  int32_t *touched = d.lcnt + 2 * (size_t)b.Lcap; // [Lcap]
-  k_merge_groups<<<1, 32, 0, st>>>(d, fv, t, luf, touched); VLS_LAUNCH(b);
-  k_trace<<<MAX_TRACES, 1024, 0, st>>>(d, b.prm, fv, fp, nF, t); VLS_LAUNCH(b);
-  k_merge_finish<<<1, 1024, 0, st>>>(d, b.prm, fv, fp, nF, t); VLS_LAUNCH(b);
-  k_relabel<<<b.grid, b.threads, 0, st>>>(d); VLS_LAUNCH(b);
+  int32_t *luf = d.lcnt + b.Lcap;
+  int32_t *touched = d.lcnt + 2 * (size_t)b.Lcap;
+  long ps = b.prof.begin(st, KK_MERGE_GROUPS);
+  k_merge_groups<<<1, 32, 0, st>>>(d, luf, touched); VLS_LAUNCH(b);
+  b.prof.end(st, ps);
+  ps = b.prof.begin(st, KK_TRACE);
+  k_trace<<<MAX_TRACES, 1024, 0, st>>>(d, b.prm); VLS_LAUNCH(b);
+  b.prof.end(st, ps);
+  ps = b.prof.begin(st, KK_MERGE_FINISH);
+  k_merge_finish<<<1, 1024, 0, st>>>(d, b.prm); VLS_LAUNCH(b);
+  b.prof.end(st, ps);
+  ps = b.prof.begin(st, KK_RELABEL);
+  k_relabel<<<b.cfg[KK_RELABEL].grid, b.cfg[KK_RELABEL].threads, 0, st>>>(d); VLS_LAUNCH(b);
+  b.prof.end(st, ps);
   return cudaGetLastError();
 }
 
-cudaError_t split_phase(Batch &b, int t, int cur) {
-  Dev &d = b.d;
-  int32_t *fv = d.front[cur], *fp = d.front[cur] + b.V, *nF = d.nfront + cur;
-  k_split<<<b.P, 256, 0, b.st>>>(d, fv, fp, nF, t); VLS_LAUNCH(b);
+cudaError_t split_phase_host(Batch &b) {
+  const long ps = b.prof.begin(b.st, KK_SPLIT);
+  k_split<<<b.P, 256, 0, b.st>>>(b.d); VLS_LAUNCH(b);
+  b.prof.end(b.st, ps);
   return cudaGetLastError();
 }
 

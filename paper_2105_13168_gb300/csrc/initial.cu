@@ -19,9 +19,113 @@ namespace {
 __device__ __forceinline__ int32_t append(int32_t *counter) { return atomicAdd(counter, 1); }
 
 // ------------------------------------------------------------------- update
-__global__ void __launch_bounds__(256) k_update(Dev d, Params P, const int32_t *__restrict__ fv,
-                                                const int32_t *__restrict__ fp, const int32_t *nF_ptr) {
-  const int32_t nF = *nF_ptr;
+// Neighbour states of a row are gathered into registers first (all loads of one level issued
+// together: columns, then layer ids and values, then layer states), so a row costs a few
+// memory latencies instead of one per neighbour and pass.  MAXD bounds the row length
+// handled by one instantiation (16: registers; 64: local memory, rare).
+template <int MAXD>
+__device__ __forceinline__ void update_row(const Dev &d, const Params &P, int32_t i, int32_t p, int32_t v, int32_t b,
+                                           int32_t deg) {
+  // nlay[j]: layer of neighbour j, 0 for the base only, -1 for a frozen plateau
+  int32_t nlay[MAXD];
+  double nx[MAXD];
+  {
+    int32_t nu[MAXD];
+#pragma unroll
+    for (int j = 0; j < MAXD; ++j) nu[j] = (j < deg) ? d.col[b + j] : v;
+#pragma unroll
+    for (int j = 0; j < MAXD; ++j) {
+      nlay[j] = (j < deg) ? d.lay[nu[j]] : 0;
+      nx[j] = (j < deg) ? d.phi[nu[j]] : 0.0;
+    }
+  }
+  const int32_t lv = d.lay[v];
+  const double xv = d.phi[v];
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j)
+    if (j < deg && nlay[j] != 0 && frozen_state(d.lstate[nlay[j]])) nlay[j] = -1;
+  const int32_t sv = lv != 0 ? d.lstate[lv] : 0;
+  const int32_t o = (lv != 0 && sv == L_ALIVE) ? lv : 0;
+  // layers present in the closed neighbourhood (ascending), base presence
+  int32_t ls[KMAX];
+  int nl = 0;
+  bool hb = false, ovf = false;
+  auto see = [&](int32_t lu, double xu, int32_t su) {
+    if (lu == 0) { hb = true; return; }
+    if (frozen_state(su)) return; // a plateau reads as the row's own layer
+    if (val_lt1(xu)) hb = true;
+    bool dup = false;
+    for (int q = 0; q < nl; ++q) dup |= (ls[q] == lu);
+    if (dup) return;
+    if (nl == KMAX) { ovf = true; return; }
+    int q = nl++;
+    while (q > 0 && ls[q - 1] > lu) { ls[q] = ls[q - 1]; --q; }
+    ls[q] = lu;
+  };
+  see(lv, xv, sv);
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j)
+    if (j < deg) see(nlay[j] < 0 ? 1 : nlay[j], nx[j], nlay[j] < 0 ? (int32_t)L_DEAD : (int32_t)L_ALIVE);
+  if (ovf) {
+    atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_ESLOTS);
+    d.onl[i] = -1;
+    return;
+  }
+  if (!hb || nl == 0) { d.onl[i] = -1; return; }
+  const double Lv = P.lv[deg];
+  const double xb = dsub(1.0, lv != 0 ? xv : 0.0);
+  double x[KMAX], lap[KMAX], out[KMAX];
+#pragma unroll 1
+  for (int q = 0; q < nl; ++q) {
+    const int32_t l = ls[q];
+    const double plat = (o != 0 && l == o) ? 1.0 : 0.0; // a plateau reads as the row's layer
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < MAXD; ++j) {
+      if (j < deg) {
+        const double psi = nlay[j] == l ? nx[j] : (nlay[j] < 0 ? plat : 0.0);
+        // terms are >= 0 and acc starts at +0: skipping a zero term leaves acc bit-identical
+        if (val_pos(psi)) acc = dadd(acc, dmul(Lv, psi));
+      }
+    }
+    x[q] = (lv == l) ? xv : 0.0;
+    acc = dadd(acc, dmul(-P.s, x[q]));
+    lap[q] = acc;
+  }
+  double accb = 0.0;
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j)
+    if (j < deg) {
+      if (nlay[j] == 0) accb = dadd(accb, Lv);                               // Lv * 1.0
+      else if (val_lt1(nx[j])) accb = dadd(accb, dmul(Lv, dsub(1.0, nx[j]))); // zero terms skipped
+    }
+  accb = dadd(accb, dmul(-P.s, xb));
+  if (!vertex_update(P, nl, x, lap, xb, accb, out)) {
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q)
+      if (q < nl) out[q] = x[q];
+  }
+  int cnt = 0;
+#pragma unroll
+  for (int q = 0; q < KMAX; ++q)
+    if (q < nl && out[q] > 0.0) {
+      d.olay[(int64_t)i * KMAX + cnt] = ls[q];
+      d.ophi[(int64_t)i * KMAX + cnt] = out[q];
+      ++cnt;
+    }
+  d.onl[i] = cnt;
+}
+
+__device__ __noinline__ void update_row_wide(const Dev &d, const Params &P, int32_t i, int32_t p, int32_t v, int32_t b,
+                                             int32_t deg) {
+  update_row<64>(d, P, i, p, v, b, deg);
+}
+
+__global__ void __launch_bounds__(256) k_update(Dev d, Params P) {
+  const int32_t cur = d.ctl[CTL_T] & 1;
+  const int32_t *__restrict__ fv = d.front[cur];
+  const int32_t *__restrict__ fp = d.front[cur] + d.V;
+  const int32_t nF = d.nfront[cur];
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
     const int32_t p = fp[i];
     if (d.pdone[p]) { d.onl[i] = -1; continue; }
@@ -29,94 +133,26 @@ __global__ void __launch_bounds__(256) k_update(Dev d, Params P, const int32_t *
     if (!VCHK(d.err, v, d.V, 101)) { d.onl[i] = -1; continue; }
     const int32_t b = d.rp[v], e = d.rp[v + 1];
     if (!VCHK(d.err, e, d.nnz + 1, 102) || !VCHK(d.err, b, e + 1, 103)) { d.onl[i] = -1; continue; }
-    const int32_t lv = d.lay[v];
-    if (!VCHK(d.err, lv, d.Lcap, 104)) { d.onl[i] = -1; continue; }
-    const double xv = d.phi[v];
-    int32_t o = 0;
-    if (lv != 0 && d.lstate[lv] == L_ALIVE) o = lv;
-    // layers present in the closed neighbourhood, base presence
-    int32_t ls[KMAX];
-    int nl = 0;
-    bool hb = false, ovf = false;
-    for (int32_t k = b - 1; k < e; ++k) {
-      const int32_t u = (k < b) ? v : d.col[k];
-      if (!VCHK(d.err, u, d.V, 105)) continue;
-      const int32_t lu = d.lay[u];
-      if (lu == 0) { hb = true; continue; }
-      if (!VCHK(d.err, lu, d.Lcap, 106)) continue;
-      if (frozen_state(d.lstate[lu])) continue; // a plateau reads as the row's own layer
-      if (dsub(1.0, d.phi[u]) > 0.0) hb = true;
-      bool dup = false;
-      for (int q = 0; q < nl; ++q) dup |= (ls[q] == lu);
-      if (!dup) {
-        if (nl == KMAX) ovf = true;
-        else {
-          int q = nl++;
-          while (q > 0 && ls[q - 1] > lu) { ls[q] = ls[q - 1]; --q; }
-          ls[q] = lu;
-        }
-      }
-    }
-    if (ovf) {
-      atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_ESLOTS);
-      d.onl[i] = -1;
-      continue;
-    }
-    if (!hb || nl == 0) { d.onl[i] = -1; continue; }
-    const double Lv = ddiv(P.s, (double)(e - b));
-    const double xb = dsub(1.0, lv != 0 ? xv : 0.0);
-    double x[KMAX], lap[KMAX], out[KMAX];
-#pragma unroll
-    for (int q = 0; q < KMAX; ++q) {
-      if (q < nl) {
-        const int32_t l = ls[q];
-        double acc = 0.0;
-        for (int32_t k = b; k < e; ++k) {
-          const int32_t u = d.col[k];
-          const int32_t lu = d.lay[u];
-          double psi = 0.0;
-          if (lu == l) psi = d.phi[u];
-          else if (lu != 0 && frozen_state(d.lstate[lu])) psi = (o != 0 && l == o) ? 1.0 : 0.0;
-          acc = dadd(acc, dmul(Lv, psi));
-        }
-        x[q] = (lv == l) ? xv : 0.0;
-        acc = dadd(acc, dmul(-P.s, x[q]));
-        lap[q] = acc;
-      }
-    }
-    double accb = 0.0;
-    for (int32_t k = b; k < e; ++k) {
-      const int32_t u = d.col[k];
-      const int32_t lu = d.lay[u];
-      const double bu = (lu == 0) ? 1.0 : dsub(1.0, d.phi[u]);
-      accb = dadd(accb, dmul(Lv, bu));
-    }
-    accb = dadd(accb, dmul(-P.s, xb));
-    if (!vertex_update(P, nl, x, lap, xb, accb, out)) {
-#pragma unroll
-      for (int q = 0; q < KMAX; ++q)
-        if (q < nl) out[q] = x[q];
-    }
-    int cnt = 0;
-#pragma unroll
-    for (int q = 0; q < KMAX; ++q)
-      if (q < nl && out[q] > 0.0) {
-        d.olay[(int64_t)i * KMAX + cnt] = ls[q];
-        d.ophi[(int64_t)i * KMAX + cnt] = out[q];
-        ++cnt;
-      }
-    d.onl[i] = cnt;
+    const int32_t deg = e - b;
+    if (deg <= 16) update_row<16>(d, P, i, p, v, b, deg);
+    else if (deg <= 64) update_row_wide(d, P, i, p, v, b, deg);
+    else { atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_EINVAL); d.onl[i] = -1; }
   }
 }
 
 // ------------------------------------------------------------------- apply
-__global__ void k_apply(Dev d, const int32_t *__restrict__ fv, const int32_t *__restrict__ fp,
-                        const int32_t *nF_ptr, int32_t t) {
-  const int32_t nF = *nF_ptr;
+// Also starts the band labelling: every row is its own union-find root (only band rows are
+// ever united).  The last block decides whether the merge phase runs this step.
+__global__ void k_apply(Dev d, Handles H) {
+  const int32_t t = d.ctl[CTL_T], cur = t & 1;
+  const int32_t *__restrict__ fv = d.front[cur];
+  const int32_t *__restrict__ fp = d.front[cur] + d.V;
+  const int32_t nF = d.nfront[cur];
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
+    const int32_t v = fv[i];
+    d.uf[v] = v;
     const int32_t c = d.onl[i];
     if (c < 0) continue;
-    const int32_t v = fv[i];
     if (c == 0) {
       d.lay[v] = 0;
       d.phi[v] = 0.0;
@@ -130,7 +166,14 @@ __global__ void k_apply(Dev d, const int32_t *__restrict__ fv, const int32_t *__
       const int32_t s = append(d.ncoll);
       if (VCHK(d.err, s, d.V, 110)) d.coll[s] = i;
       d.pmerge[fp[i]] = 1;
+      d.ctl[CTL_MERGE] = 1;
     }
+  }
+  if (last_block_done(d.ctl + CTL_DONE_APPLY)) {
+    const int32_t m = __ldcg(d.ctl + CTL_MERGE);
+    if (H.use) cudaGraphSetConditional(H.merge, m ? 1u : 0u);
+    if (m) d.ctl[CTL_NMERGE]++;
+    d.ctl[CTL_MERGE] = 0;
   }
 }
 
@@ -138,105 +181,180 @@ __global__ void k_apply(Dev d, const int32_t *__restrict__ fv, const int32_t *__
 __device__ __forceinline__ bool is_band(const Dev &d, int32_t v, int32_t &l) {
   l = d.lay[v];
   if (l == 0 || d.lstate[l] != L_ALIVE) return false;
-  const double x = d.phi[v];
-  return x > 0.0 && x < 1.0;
+  return val_band(d.phi[v]);
 }
 
-__global__ void k_band_init(Dev d, const int32_t *__restrict__ fv, const int32_t *__restrict__ fp,
-                            const int32_t *nF_ptr) {
-  const int32_t nF = *nF_ptr;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
-    if (d.pdone[fp[i]]) continue;
-    const int32_t v = fv[i];
-    int32_t l;
-    if (is_band(d, v, l)) d.uf[v] = v;
-  }
-}
-
-__global__ void k_band_hook(Dev d, const int32_t *__restrict__ fv, const int32_t *__restrict__ fp,
-                            const int32_t *nF_ptr, int32_t t) {
-  const int32_t nF = *nF_ptr;
+__global__ void k_band_hook(Dev d) {
+  const int32_t t = d.ctl[CTL_T], cur = t & 1;
+  const int32_t *__restrict__ fv = d.front[cur];
+  const int32_t *__restrict__ fp = d.front[cur] + d.V;
+  const int32_t nF = d.nfront[cur];
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
     if (d.pdone[fp[i]]) continue;
     const int32_t v = fv[i];
     int32_t l;
     if (!is_band(d, v, l)) continue;
-    for (int32_t k = d.rp[v]; k < d.rp[v + 1]; ++k) {
-      const int32_t u = d.col[k];
-      if (!VCHK(d.err, u, d.V, 130)) continue;
-      if (u >= v || d.fmark[u] != t) continue; // band vertices are frontier rows of this step
-      int32_t lu;
-      if (is_band(d, u, lu) && lu == l) uf_unite(d.uf, u, v);
+    const int32_t b = d.rp[v], deg = d.rp[v + 1] - b;
+    if (deg <= 16) {
+      // a neighbour joins v's band component iff it is a frontier row of this step (band
+      // vertices are) holding the same live layer strictly between 0 and 1
+      int32_t nu[16], nm[16], nl[16];
+      double nx[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) nu[j] = (j < deg) ? d.col[b + j] : v;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const bool ok = j < deg && nu[j] < v;
+        nm[j] = ok ? d.fmark[nu[j]] : -1;
+        nl[j] = ok ? d.lay[nu[j]] : 0;
+        nx[j] = ok ? d.phi[nu[j]] : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (nm[j] == t && nl[j] == l && val_band(nx[j])) uf_unite(d.uf, nu[j], v);
+    } else {
+      for (int32_t k = b; k < b + deg; ++k) {
+        const int32_t u = d.col[k];
+        if (!VCHK(d.err, u, d.V, 130)) continue;
+        if (u >= v || d.fmark[u] != t) continue;
+        int32_t lu;
+        if (is_band(d, u, lu) && lu == l) uf_unite(d.uf, u, v);
+      }
     }
   }
 }
 
-__global__ void k_band_count(Dev d, const int32_t *__restrict__ fv, const int32_t *__restrict__ fp,
-                             const int32_t *nF_ptr) {
-  const int32_t nF = *nF_ptr;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
-    if (d.pdone[fp[i]]) continue;
-    const int32_t v = fv[i];
-    int32_t l;
-    if (!is_band(d, v, l)) continue;
-    if (uf_find(d.uf, v) == v) atomicAdd(&d.lcnt[l], 1);
-  }
-}
-
-// ------------------------------------------------------------------- next frontier
-__device__ __forceinline__ bool in_frontier(const Dev &d, int32_t u) {
-  const int32_t lu = d.lay[u];
-  if (lu != 0 && frozen_state(d.lstate[lu])) return false;
-  bool hb = false, hl = false;
-  const int32_t b = d.rp[u], e = d.rp[u + 1];
-  for (int32_t k = b - 1; k < e && !(hb && hl); ++k) {
-    const int32_t w = (k < b) ? u : d.col[k];
-    const int32_t lw = d.lay[w];
-    if (lw == 0) { hb = true; continue; }
-    if (frozen_state(d.lstate[lw])) continue;
-    hl = true;
-    if (dsub(1.0, d.phi[w]) > 0.0) hb = true;
-  }
-  return hb && hl;
-}
-
-// F_t (cur) -> F_{t+1} (nxt).  `tnext` is the id of the step the new list belongs to.
-__global__ void k_frontier(Dev d, const int32_t *__restrict__ fv, const int32_t *__restrict__ fp,
-                           const int32_t *nF_ptr, int32_t *__restrict__ nv_out, int32_t *__restrict__ np_out,
-                           int32_t *nN_ptr, int32_t *pcount_next, int32_t tnext, int32_t record) {
-  const int32_t nF = *nF_ptr;
+// Component roots per layer.  A layer reaching two roots, or a problem with a live layer
+// that has no root (no band left), sends the step through the split phase.
+__global__ void k_band_count(Dev d, Handles H) {
+  const int32_t cur = d.ctl[CTL_T] & 1;
+  const int32_t *__restrict__ fv = d.front[cur];
+  const int32_t *__restrict__ fp = d.front[cur] + d.V;
+  const int32_t nF = d.nfront[cur];
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
     const int32_t p = fp[i];
     if (d.pdone[p]) continue;
     const int32_t v = fv[i];
-    if (record) {
+    int32_t l;
+    if (!is_band(d, v, l)) continue;
+    if (uf_find(d.uf, v) == v) {
+      const int32_t old = atomicAdd(&d.lcnt[l], 1);
+      if (old == 0) atomicAdd(&d.nbl[p], 1);
+      else if (old == 1) d.ctl[CTL_SPLIT] = 1;
+    }
+  }
+  if (last_block_done(d.ctl + CTL_DONE_COUNT)) {
+    int32_t s = __ldcg(d.ctl + CTL_SPLIT);
+    for (int32_t p = 0; p < d.P && !s; ++p)
+      if (!d.pdone[p] && __ldcg(d.nbl + p) != d.nalive[p]) s = 1;
+    if (H.use) cudaGraphSetConditional(H.split, s ? 1u : 0u);
+    if (s) d.ctl[CTL_NSPLIT]++;
+    d.ctl[CTL_SPLIT] = 0;
+  }
+}
+
+// ------------------------------------------------------------------- next frontier
+// u joins the frontier iff it is not frozen and its closed neighbourhood holds the base and a
+// live layer.  Neighbour ids, then their states, are loaded before any test.
+template <int MAXD>
+__device__ __forceinline__ bool in_frontier_t(const Dev &d, int32_t u, int32_t b, int32_t deg) {
+  int32_t nlay[MAXD];
+  uint32_t partial = 0; // bit j: neighbour j holds a layer with value < 1 (base present if live)
+  {
+    int32_t nu[MAXD];
+#pragma unroll
+    for (int j = 0; j < MAXD; ++j) nu[j] = (j < deg) ? d.col[b + j] : u;
+#pragma unroll
+    for (int j = 0; j < MAXD; ++j) {
+      nlay[j] = (j < deg) ? d.lay[nu[j]] : 0;
+      const double x = (j < deg) ? d.phi[nu[j]] : 0.0;
+      if (val_lt1(x)) partial |= 1u << j;
+    }
+  }
+  const int32_t lu = d.lay[u];
+  const double xu = d.phi[u];
+  bool hb = false, hl = false;
+  if (lu == 0) hb = true;
+  else {
+    if (frozen_state(d.lstate[lu])) return false;
+    hl = true;
+    if (val_lt1(xu)) hb = true;
+  }
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j) {
+    if (j < deg) {
+      if (nlay[j] == 0) { hb = true; continue; }
+      if (hb && hl) continue;
+      if (frozen_state(d.lstate[nlay[j]])) continue;
+      hl = true;
+      if ((partial >> j) & 1u) hb = true;
+    }
+  }
+  return hb && hl;
+}
+__device__ __noinline__ bool in_frontier_wide(const Dev &d, int32_t u, int32_t b, int32_t deg) {
+  return in_frontier_t<64>(d, u, b, deg < 64 ? deg : 64);
+}
+__device__ __forceinline__ bool in_frontier(const Dev &d, int32_t u) {
+  const int32_t b = d.rp[u], deg = d.rp[u + 1] - b;
+  if (deg <= 16) return in_frontier_t<16>(d, u, b, deg);
+  return in_frontier_wide(d, u, b, deg);
+}
+
+// F_t -> F_{t+1}: a group of 16 lanes per row, lane j takes candidate j of the row's closed
+// neighbourhood (the row itself, then its neighbours; rows longer than 15 loop).  Also clears
+// the per-layer root counts of this step (each band root resets its layer's counter) and
+// accumulates the step record.
+__global__ void __launch_bounds__(256) k_frontier(Dev d) {
+  const int32_t t = d.ctl[CTL_T], cur = t & 1, nxt = cur ^ 1, tnext = t + 1;
+  const int32_t *__restrict__ fv = d.front[cur];
+  const int32_t *__restrict__ fp = d.front[cur] + d.V;
+  const int32_t nF = d.nfront[cur];
+  int32_t *__restrict__ nv_out = d.front[nxt];
+  int32_t *__restrict__ np_out = d.front[nxt] + d.V;
+  int32_t *nN_ptr = d.nfront + nxt;
+  int32_t *pcount_next = d.pfront + (size_t)nxt * d.P;
+  const int32_t lane = threadIdx.x & 15;
+  const int32_t group = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int32_t ngroup = (gridDim.x * blockDim.x) >> 4;
+  for (int32_t i = group; i < nF; i += ngroup) {
+    const int32_t p = fp[i];
+    if (d.pdone[p]) continue;
+    const int32_t v = fv[i];
+    if (lane == 0) {
       int32_t l;
       if (is_band(d, v, l)) {
-        atomicAdd(&d.rband[p], 1);
-        const uint64_t key = ((uint64_t)(uint32_t)(v - d.voff[p]) << 32) | (uint32_t)(l - d.lbase[p]);
-        atomicAdd(&d.rhash[p], (unsigned long long)mix64(key));
+        if (d.uf[v] == v) d.lcnt[l] = 0;
+        if (d.record) {
+          atomicAdd(&d.rband[p], 1);
+          const uint64_t key = ((uint64_t)(uint32_t)(v - d.voff[p]) << 32) | (uint32_t)(l - d.lbase[p]);
+          atomicAdd(&d.rhash[p], (unsigned long long)mix64(key));
+        }
       }
     }
     const int32_t b = d.rp[v], e = d.rp[v + 1];
-    for (int32_t k = b - 1; k < e; ++k) {
+    for (int32_t k = b - 1 + lane; k < e; k += 16) {
       const int32_t u = (k < b) ? v : d.col[k];
       if (!VCHK(d.err, u, d.V, 120)) continue;
       if (atomicExch(&d.stamp[u], tnext) == tnext) continue;
       if (!in_frontier(d, u)) continue;
-      const int32_t s = append(nN_ptr);
+      const int32_t s = warp_append(nN_ptr, pcount_next, p);
       if (!VCHK(d.err, s, d.V, 121)) continue;
       nv_out[s] = u;
       np_out[s] = p;
       d.fmark[u] = tnext;
-      atomicAdd(&pcount_next[p], 1);
     }
   }
 }
 
 // ------------------------------------------------------------------- epilogue
-__global__ void k_epilogue(Dev d, int32_t *pcount_cur, int32_t *pcount_next, int32_t t, int32_t max_steps,
-                           int32_t *active, int32_t *nF_cur) {
+// One block: per-problem bookkeeping, then the step counter advances; the WHILE node stops
+// when no problem is running (or at the hard step bound).
+__global__ void k_epilogue(Dev d, Handles H, int32_t max_steps) {
   __shared__ int32_t nact;
+  const int32_t t = d.ctl[CTL_T], cur = t & 1, nxt = cur ^ 1;
+  int32_t *pcount_cur = d.pfront + (size_t)cur * d.P;
+  int32_t *pcount_next = d.pfront + (size_t)nxt * d.P;
   if (threadIdx.x == 0) nact = 0;
   __syncthreads();
   for (int32_t p = threadIdx.x; p < d.P; p += blockDim.x) {
@@ -260,12 +378,15 @@ __global__ void k_epilogue(Dev d, int32_t *pcount_cur, int32_t *pcount_next, int
     }
     pcount_cur[p] = 0;
     d.pmerge[p] = 0;
+    d.nbl[p] = 0;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    *active = nact;
-    *nF_cur = 0; // the list just consumed is reused two steps later
+    d.ctl[CTL_ACTIVE] = nact;
+    d.nfront[cur] = 0; // the list just consumed is reused two steps later
     *d.ncoll = 0;
+    d.ctl[CTL_T] = t + 1;
+    if (H.use && (nact == 0 || t >= d.ctl[CTL_LIMIT])) cudaGraphSetConditional(H.loop, 0u);
   }
 }
 
@@ -282,6 +403,7 @@ __global__ void k_init(Dev d, int32_t *fv0, int32_t *fp0, int32_t *nF0) {
     d.ldeath[L1] = -1;
     d.lprob[L1] = p;
     d.lcount[p] = 1;
+    d.nalive[p] = 1;
     const int32_t node = atomicAdd(d.nnodes, 1);
     d.nkind[node] = N_SEED;
     d.nstep[node] = 0;
@@ -317,43 +439,114 @@ __global__ void k_final_status(Dev d, const int32_t *pstall) {
     if (d.pstatus[p] == 0 && pstall[p]) d.pstatus[p] = VLS_ESTALL;
 }
 
+__global__ void k_ctl_set(int32_t *ctl, int32_t idx, int32_t v) { ctl[idx] = v; }
+
 }  // namespace
 
-// The frontier list buffers: index 0/1 alternate; list c holds F_t for t % 2 == c.
+// The frontier lists alternate: list (t & 1) holds F_t.  The seed regions form F_0 and the
+// frontier kernel run at t = 0 builds F_1.
 cudaError_t init_state(Batch &b) {
   Dev &d = b.d;
   cudaStream_t st = b.st;
   k_init<<<(b.P + 127) / 128, 128, 0, st>>>(d, d.front[0], d.front[0] + b.V, d.nfront + 0); VLS_LAUNCH(b);
-  // F_1 from the seed regions (treated as the rows of step 0)
-  int32_t *pc = d.pfront;
-  k_frontier<<<b.grid, b.threads, 0, st>>>(d, d.front[0], d.front[0] + b.V, d.nfront + 0, d.front[1],
-                                            d.front[1] + b.V, d.nfront + 1, pc + b.P, 1, 0); VLS_LAUNCH(b);
+  k_frontier<<<b.cfg[KK_FRONTIER].grid, b.cfg[KK_FRONTIER].threads, 0, st>>>(d); VLS_LAUNCH(b);
   cudaMemsetAsync(d.nfront + 0, 0, sizeof(int32_t), st);
+  k_ctl_set<<<1, 1, 0, st>>>(d.ctl, CTL_T, 1); VLS_LAUNCH(b);
   return cudaGetLastError();
 }
 
-cudaError_t initial_step(Batch &b, int t) {
+// The initial pass as one graph: WHILE(problems running) { update; apply; IF(merge) {...};
+// band hook; band count; IF(split / extinction) {...}; next frontier; epilogue }.
+cudaError_t build_initial_graph(Batch &b, cudaGraph_t *out) {
+  cudaGraph_t g = nullptr, body = nullptr, mbody = nullptr, sbody = nullptr;
+  cudaGraphNode_t w, n_upd, n_app, n_if_m, n_hook, n_cnt, n_if_s, n_fr, n_ep;
+  Handles H{};
+  H.use = 1;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  auto G = [&](int k) { return dim3(b.cfg[k].grid); };
+  auto T = [&](int k) { return dim3(b.cfg[k].threads); };
+#define GK(x)                         \
+  do {                                \
+    e = (x);                          \
+    if (e != cudaSuccess) goto fail;  \
+  } while (0)
+  GK(add_conditional(&w, g, nullptr, 0, cudaGraphCondTypeWhile, 1u, &H.loop, &body));
+  GK(cudaGraphConditionalHandleCreate(&H.merge, body, 0u, cudaGraphCondAssignDefault));
+  GK(cudaGraphConditionalHandleCreate(&H.split, body, 0u, cudaGraphCondAssignDefault));
+  GK(add_kernel(&n_upd, body, nullptr, 0, k_update, G(KK_UPDATE), T(KK_UPDATE), b.d, b.prm));
+  GK(add_kernel(&n_app, body, &n_upd, 1, k_apply, G(KK_APPLY), T(KK_APPLY), b.d, H));
+  {
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = H.merge;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    GK(cudaGraphAddNode(&n_if_m, body, &n_app, nullptr, 1, &np));
+    mbody = np.conditional.phGraph_out[0];
+    GK(add_merge_nodes(b, mbody));
+  }
+  GK(add_kernel(&n_hook, body, &n_if_m, 1, k_band_hook, G(KK_HOOK), T(KK_HOOK), b.d));
+  GK(add_kernel(&n_cnt, body, &n_hook, 1, k_band_count, G(KK_COUNT), T(KK_COUNT), b.d, H));
+  {
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = H.split;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    GK(cudaGraphAddNode(&n_if_s, body, &n_cnt, nullptr, 1, &np));
+    sbody = np.conditional.phGraph_out[0];
+    GK(add_split_nodes(b, sbody));
+  }
+  GK(add_kernel(&n_fr, body, &n_if_s, 1, k_frontier, G(KK_FRONTIER), T(KK_FRONTIER), b.d));
+  GK(add_kernel(&n_ep, body, &n_fr, 1, k_epilogue, dim3(1), dim3(256), b.d, H, b.opt.max_steps));
+#undef GK
+  *out = g;
+  return cudaSuccess;
+fail:
+  cudaGraphDestroy(g);
+  return e;
+}
+
+// Debug path: the same kernels launched one step at a time from the host (the event phases
+// run every step; their kernels return at once when nothing happened).
+cudaError_t initial_step_host(Batch &b) {
   Dev &d = b.d;
   cudaStream_t st = b.st;
-  const int cur = t & 1, nxt = cur ^ 1;
-  int32_t *fv = d.front[cur], *fp = d.front[cur] + b.V;
-  int32_t *nF = d.nfront + cur;
-  int32_t *pcur = d.pfront + (size_t)cur * b.P, *pnxt = d.pfront + (size_t)nxt * b.P;
-  const long ps = b.prof.begin(st, 0);
-  k_update<<<b.grid, b.threads, 0, st>>>(d, b.prm, fv, fp, nF); VLS_LAUNCH(b);
+  Handles H{};
+  H.use = 0;
+  long ps = b.prof.begin(st, KK_UPDATE);
+  k_update<<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm); VLS_LAUNCH(b);
   b.prof.end(st, ps);
-  k_apply<<<b.grid, b.threads, 0, st>>>(d, fv, fp, nF, t); VLS_LAUNCH(b);
-  cudaError_t e = merge_phase(b, t, cur);
+  ps = b.prof.begin(st, KK_APPLY);
+  k_apply<<<b.cfg[KK_APPLY].grid, b.cfg[KK_APPLY].threads, 0, st>>>(d, H); VLS_LAUNCH(b);
+  b.prof.end(st, ps);
+  cudaError_t e = merge_phase_host(b);
   if (e != cudaSuccess) return e;
-  k_band_init<<<b.grid, b.threads, 0, st>>>(d, fv, fp, nF); VLS_LAUNCH(b);
-  k_band_hook<<<b.grid, b.threads, 0, st>>>(d, fv, fp, nF, t); VLS_LAUNCH(b);
-  k_band_count<<<b.grid, b.threads, 0, st>>>(d, fv, fp, nF); VLS_LAUNCH(b);
-  e = split_phase(b, t, cur);
+  ps = b.prof.begin(st, KK_HOOK);
+  k_band_hook<<<b.cfg[KK_HOOK].grid, b.cfg[KK_HOOK].threads, 0, st>>>(d); VLS_LAUNCH(b);
+  b.prof.end(st, ps);
+  ps = b.prof.begin(st, KK_COUNT);
+  k_band_count<<<b.cfg[KK_COUNT].grid, b.cfg[KK_COUNT].threads, 0, st>>>(d, H); VLS_LAUNCH(b);
+  b.prof.end(st, ps);
+  e = split_phase_host(b);
   if (e != cudaSuccess) return e;
-  k_frontier<<<b.grid, b.threads, 0, st>>>(d, fv, fp, nF, d.front[nxt], d.front[nxt] + b.V, d.nfront + nxt, pnxt,
-                                            t + 1, d.record); VLS_LAUNCH(b);
-  k_epilogue<<<1, 256, 0, st>>>(d, pcur, pnxt, t, b.opt.max_steps, d.err + 1, nF); VLS_LAUNCH(b);
+  ps = b.prof.begin(st, KK_FRONTIER);
+  k_frontier<<<b.cfg[KK_FRONTIER].grid, b.cfg[KK_FRONTIER].threads, 0, st>>>(d); VLS_LAUNCH(b);
+  b.prof.end(st, ps);
+  ps = b.prof.begin(st, KK_EPILOGUE);
+  k_epilogue<<<1, 256, 0, st>>>(d, H, b.opt.max_steps); VLS_LAUNCH(b);
+  b.prof.end(st, ps);
   return cudaGetLastError();
+}
+
+void configure_initial(Batch &b) {
+  const int rt = b.threads; // row kernels: one thread per frontier row
+  b.cfg[KK_UPDATE] = wave_cfg(b, k_update, rt);
+  b.cfg[KK_APPLY] = wave_cfg(b, k_apply, rt);
+  b.cfg[KK_HOOK] = wave_cfg(b, k_band_hook, rt);
+  b.cfg[KK_COUNT] = wave_cfg(b, k_band_count, rt);
+  b.cfg[KK_FRONTIER] = wave_cfg(b, k_frontier, 256); // 16 lanes per row
 }
 
 cudaError_t final_checks(Batch &b) {

@@ -85,46 +85,82 @@ __global__ void k_tinit(Dev d, TDev T, int32_t *fv0, int32_t *fq0, int32_t *nF0)
   }
 }
 
-__global__ void __launch_bounds__(256) k_tupdate(Dev d, TDev T, Params P, const int32_t *__restrict__ fv,
-                                                 const int32_t *__restrict__ fq, const int32_t *nF_ptr) {
-  const int32_t nF = *nF_ptr;
+// Kept neighbours of a row of pass q, gathered before use: ids, then cover steps, flags and
+// values (MAXD bounds the row length of one instantiation).
+template <int MAXD>
+__device__ __forceinline__ int gather_kept(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
+                                          int32_t voff, int8_t fl, int32_t v, int32_t b, int32_t deg, uint64_t &kp,
+                                          double *nx) {
+  int32_t nu[MAXD];
+  kp = 0;
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j) nu[j] = (j < deg) ? d.col[b + j] : v;
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j) {
+    const int32_t c = (j < deg) ? d.cover[nu[j]] : -1;
+    const int8_t f = (j < deg) ? T.flag[base + (nu[j] - voff)] : (int8_t)0;
+    nx[j] = (j < deg) ? T.phi[base + (nu[j] - voff)] : 0.0;
+    bool k = j < deg && c >= 0 && c <= step;
+    if (k && (((fl & F_SRC) && (f & F_TGT)) || ((fl & F_TGT) && (f & F_SRC)))) k = !is_cut(T, q, b + j);
+    if (k) kp |= 1ull << j;
+  }
+  return __popcll(kp);
+}
+
+template <int MAXD>
+__device__ __forceinline__ void tupdate_row(const Dev &d, const TDev &T, const Params &P, int32_t i, int32_t q,
+                                            int32_t v) {
+  const int32_t p = T.pprob[q], base = T.pbase[q], voff = d.voff[p], step = T.pstep[q];
+  const int32_t idx = base + (v - voff);
+  if (!VCHK(T.err, idx, T.PV, 310)) { T.onew[i] = 0.0; return; }
+  const int8_t fl = T.flag[idx];
+  const int32_t b = d.rp[v], deg = d.rp[v + 1] - b;
+  uint64_t kp;
+  double nx[MAXD];
+  const int dh = gather_kept<MAXD>(d, T, q, step, base, voff, fl, v, b, deg, kp, nx);
+  const double Lv = dh > 0 ? P.lv[dh] : 0.0;
+  const double diag = dh > 0 ? -P.s : 0.0;
+  const double x = T.phi[idx];
+  double acc = 0.0, accb = 0.0;
+  // terms are >= 0 and the sums start at +0: zero terms are skipped (bit-identical)
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j)
+    if (((kp >> j) & 1ull) && val_pos(nx[j])) acc = dadd(acc, dmul(Lv, nx[j]));
+  acc = dadd(acc, dmul(diag, x));
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j)
+    if (((kp >> j) & 1ull) && val_lt1(nx[j])) accb = dadd(accb, dmul(Lv, dsub(1.0, nx[j])));
+  const double xb = dsub(1.0, x);
+  accb = dadd(accb, dmul(diag, xb));
+  double out;
+  if (!vertex_update(P, 1, &x, &acc, xb, accb, &out)) out = x;
+  T.onew[i] = out;
+}
+
+__device__ __noinline__ void tupdate_row_wide(const Dev &d, const TDev &T, const Params &P, int32_t i, int32_t q,
+                                              int32_t v) {
+  tupdate_row<64>(d, T, P, i, q, v);
+}
+
+__global__ void __launch_bounds__(256) k_tupdate(Dev d, TDev T, Params P) {
+  const int32_t cur = d.ctl[CTL_TAU] & 1;
+  const int32_t *__restrict__ fv = T.fv[cur];
+  const int32_t *__restrict__ fq = T.fq[cur];
+  const int32_t nF = T.nf[cur];
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
-    const int32_t q = fq[i];
-    const int32_t v = fv[i];
-    const int32_t p = T.pprob[q], base = T.pbase[q], voff = d.voff[p], step = T.pstep[q];
-    const int32_t idx = base + (v - voff);
-    if (!VCHK(T.err, idx, T.PV, 310)) { T.onew[i] = 0.0; continue; }
-    const int8_t fl = T.flag[idx];
-    const int32_t b = d.rp[v], e = d.rp[v + 1];
-    int32_t dh = 0;
-    for (int32_t k = b; k < e; ++k)
-      if (kept(d, T, q, step, base, voff, fl, d.col[k], k)) ++dh;
-    const double Lv = dh > 0 ? ddiv(P.s, (double)dh) : 0.0;
-    const double diag = dh > 0 ? -P.s : 0.0;
-    const double x = T.phi[idx];
-    double acc = 0.0, accb = 0.0;
-    for (int32_t k = b; k < e; ++k) {
-      const int32_t u = d.col[k];
-      if (!kept(d, T, q, step, base, voff, fl, u, k)) continue;
-      acc = dadd(acc, dmul(Lv, T.phi[base + (u - voff)]));
-    }
-    acc = dadd(acc, dmul(diag, x));
-    for (int32_t k = b; k < e; ++k) {
-      const int32_t u = d.col[k];
-      if (!kept(d, T, q, step, base, voff, fl, u, k)) continue;
-      accb = dadd(accb, dmul(Lv, dsub(1.0, T.phi[base + (u - voff)])));
-    }
-    const double xb = dsub(1.0, x);
-    accb = dadd(accb, dmul(diag, xb));
-    double out;
-    if (!vertex_update(P, 1, &x, &acc, xb, accb, &out)) out = x;
-    T.onew[i] = out;
+    const int32_t v = fv[i], q = fq[i];
+    const int32_t deg = d.rp[v + 1] - d.rp[v];
+    if (deg <= 16) tupdate_row<16>(d, T, P, i, q, v);
+    else if (deg <= 64) tupdate_row_wide(d, T, P, i, q, v);
+    else T.onew[i] = T.phi[T.pbase[q] + (v - d.voff[T.pprob[q]])];
   }
 }
 
-__global__ void k_tapply(Dev d, TDev T, const int32_t *__restrict__ fv, const int32_t *__restrict__ fq,
-                         const int32_t *nF_ptr, int32_t tau, double theta) {
-  const int32_t nF = *nF_ptr;
+__global__ void k_tapply(Dev d, TDev T, double theta) {
+  const int32_t tau = d.ctl[CTL_TAU], cur = tau & 1;
+  const int32_t *__restrict__ fv = T.fv[cur];
+  const int32_t *__restrict__ fq = T.fq[cur];
+  const int32_t nF = T.nf[cur];
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
     const int32_t q = fq[i], v = fv[i];
     const int32_t p = T.pprob[q];
@@ -139,53 +175,82 @@ __global__ void k_tapply(Dev d, TDev T, const int32_t *__restrict__ fv, const in
   }
 }
 
-__device__ __forceinline__ bool t_in_frontier(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
-                                              int32_t voff, int32_t u) {
-  if (!in_dom(d, u, step)) return false;
+// u joins pass q's frontier iff it is in the domain, not a source, and its kept closed
+// neighbourhood holds both phases.
+template <int MAXD>
+__device__ __forceinline__ bool t_in_frontier_t(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
+                                                int32_t voff, int32_t u, int32_t b, int32_t deg) {
   const int32_t iu = base + (u - voff);
   const int8_t fu = T.flag[iu];
   if (fu & F_SRC) return false;
   const double xu = T.phi[iu];
-  bool lay = xu > 0.0, bas = dsub(1.0, xu) > 0.0;
-  for (int32_t k = d.rp[u]; k < d.rp[u + 1] && !(lay && bas); ++k) {
-    const int32_t w = d.col[k];
-    if (!kept(d, T, q, step, base, voff, fu, w, k)) continue;
-    const double xw = T.phi[base + (w - voff)];
-    if (xw > 0.0) lay = true;
-    if (dsub(1.0, xw) > 0.0) bas = true;
-  }
+  bool lay = val_pos(xu), bas = val_lt1(xu);
+  if (lay && bas) return true;
+  uint64_t kp;
+  double nx[MAXD];
+  gather_kept<MAXD>(d, T, q, step, base, voff, fu, u, b, deg, kp, nx);
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j)
+    if ((kp >> j) & 1ull) {
+      if (val_pos(nx[j])) lay = true;
+      if (val_lt1(nx[j])) bas = true;
+    }
   return lay && bas;
 }
+__device__ __noinline__ bool t_in_frontier_wide(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
+                                                int32_t voff, int32_t u, int32_t b, int32_t deg) {
+  return t_in_frontier_t<64>(d, T, q, step, base, voff, u, b, deg < 64 ? deg : 64);
+}
+__device__ __forceinline__ bool t_in_frontier(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
+                                              int32_t voff, int32_t u) {
+  if (!in_dom(d, u, step)) return false;
+  const int32_t b = d.rp[u], deg = d.rp[u + 1] - b;
+  if (deg <= 16) return t_in_frontier_t<16>(d, T, q, step, base, voff, u, b, deg);
+  return t_in_frontier_wide(d, T, q, step, base, voff, u, b, deg);
+}
 
-__global__ void k_tfrontier(Dev d, TDev T, const int32_t *__restrict__ fv, const int32_t *__restrict__ fq,
-                            const int32_t *nF_ptr, int32_t *__restrict__ nv_out, int32_t *__restrict__ nq_out,
-                            int32_t *nN_ptr, int32_t tnext) {
-  const int32_t nF = *nF_ptr;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
+// 16-lane groups per row, one lane per candidate of the row's kept closed neighbourhood.
+__global__ void __launch_bounds__(256) k_tfrontier(Dev d, TDev T) {
+  const int32_t tau = d.ctl[CTL_TAU], cur = tau & 1, nxt = cur ^ 1, tnext = tau + 1;
+  const int32_t *__restrict__ fv = T.fv[cur];
+  const int32_t *__restrict__ fq = T.fq[cur];
+  const int32_t nF = T.nf[cur];
+  int32_t *__restrict__ nv_out = T.fv[nxt];
+  int32_t *__restrict__ nq_out = T.fq[nxt];
+  int32_t *nN_ptr = T.nf + nxt;
+  int32_t *qcnt_next = T.qcnt + (size_t)nxt * T.NP;
+  const int32_t lane = threadIdx.x & 15;
+  const int32_t group = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int32_t ngroup = (gridDim.x * blockDim.x) >> 4;
+  for (int32_t i = group; i < nF; i += ngroup) {
     const int32_t q = fq[i];
     if (T.qdone[q] || T.qbstar[q] != 0x7fffffff) continue;
     const int32_t v = fv[i];
     const int32_t p = T.pprob[q], base = T.pbase[q], voff = d.voff[p], step = T.pstep[q];
     const int8_t fl = T.flag[base + (v - voff)];
     const int32_t b = d.rp[v], e = d.rp[v + 1];
-    for (int32_t k = b - 1; k < e; ++k) {
+    for (int32_t k = b - 1 + lane; k < e; k += 16) {
       const int32_t u = (k < b) ? v : d.col[k];
       if (k >= b && !kept(d, T, q, step, base, voff, fl, u, k)) continue;
       const int32_t iu = base + (u - voff);
       if (!VCHK(T.err, iu, T.PV, 330)) continue;
       if (atomicExch(&T.stamp[iu], tnext) == tnext) continue;
       if (!t_in_frontier(d, T, q, step, base, voff, u)) continue;
-      const int32_t s = atomicAdd(nN_ptr, 1);
+      const int32_t s = warp_append(nN_ptr, qcnt_next, q);
       if (!VCHK(T.err, s, T.PV, 331)) continue;
       nv_out[s] = u;
       nq_out[s] = q;
-      atomicAdd(&T.qcnt[q], 1);
     }
   }
 }
 
-__global__ void k_tepilogue(TDev T, int32_t *cnt_cur, int32_t tau, int32_t max_steps, int32_t *nF_cur) {
+// One block: pass bookkeeping, then the step counter advances; the WHILE node stops when no
+// pass is running (or at the hard step bound).
+__global__ void k_tepilogue(Dev d, TDev T, Handles H, int32_t max_steps) {
   __shared__ int32_t nact;
+  const int32_t tau = d.ctl[CTL_TAU], cur = tau & 1, nxt = cur ^ 1;
+  int32_t *cnt_cur = T.qcnt + (size_t)cur * T.NP;
+  int32_t *cnt_next = T.qcnt + (size_t)nxt * T.NP;
   if (threadIdx.x == 0) nact = 0;
   __syncthreads();
   for (int32_t q = threadIdx.x; q < T.NP; q += blockDim.x) {
@@ -193,17 +258,18 @@ __global__ void k_tepilogue(TDev T, int32_t *cnt_cur, int32_t tau, int32_t max_s
       T.qsteps[q] = tau;
       T.qupd[q] += cnt_cur[q];
       if (T.qbstar[q] != 0x7fffffff) { T.qdone[q] = 1; T.qstatus[q] = VLS_OK; }
-      else if (T.qcnt[q] == 0) { T.qdone[q] = 1; T.qstatus[q] = VLS_ELOOPFAIL; }
+      else if (cnt_next[q] == 0) { T.qdone[q] = 1; T.qstatus[q] = VLS_ELOOPFAIL; }
       else if (tau >= max_steps) { T.qdone[q] = 1; T.qstatus[q] = VLS_EMAXSTEPS; }
       if (!T.qdone[q]) atomicAdd(&nact, 1);
     }
-    cnt_cur[q] = T.qcnt[q];
-    T.qcnt[q] = 0;
+    cnt_cur[q] = 0;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    *T.active = nact;
-    *nF_cur = 0;
+    d.ctl[CTL_TACTIVE] = nact;
+    T.nf[cur] = 0;
+    d.ctl[CTL_TAU] = tau + 1;
+    if (H.use && (nact == 0 || tau >= d.ctl[CTL_TLIMIT])) cudaGraphSetConditional(H.loop, 0u);
   }
 }
 
@@ -268,46 +334,81 @@ __global__ void k_ttrace(Dev d, TDev T) {
   }
 }
 
+__global__ void k_tctl_set(int32_t *ctl, int32_t idx, int32_t v) { ctl[idx] = v; }
+
 }  // namespace
 
-// Runs all passes of b.td (already laid out by the host).  Returns the steps executed.
+void configure_tunnel(Batch &b) {
+  b.cfg[KK_TUPDATE] = wave_cfg(b, k_tupdate, b.threads);
+  b.cfg[KK_TAPPLY] = wave_cfg(b, k_tapply, b.threads);
+  b.cfg[KK_TFRONTIER] = wave_cfg(b, k_tfrontier, 256);
+}
+
+// Runs all passes of b.td (already laid out by the host): init, F_1, then one graph launch
+// WHILE(passes running) { update; apply; next frontier; epilogue }, then the traces.
 cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out) {
   Dev &d = b.d;
   TDev &T = b.td;
   cudaStream_t st = b.st;
-  int32_t *fv0 = T.fv[0], *fq0 = T.fq[0];
-  k_tinit<<<T.NP, 256, 0, st>>>(d, T, fv0, fq0, T.nf + 0); VLS_LAUNCH(b);
-  // F_1 from the sources
-  int32_t *cnt = T.qcnt + T.NP; // [NP] rows of the list in flight
-  k_tfrontier<<<b.grid, b.threads, 0, st>>>(d, T, fv0, fq0, T.nf + 0, T.fv[1], T.fq[1], T.nf + 1, 1); VLS_LAUNCH(b);
-  // after init the count of F_1 rows is in qcnt; move it to the "current" counter
-  cudaMemcpyAsync(cnt, T.qcnt, sizeof(int32_t) * T.NP, cudaMemcpyDeviceToDevice, st);
-  cudaMemsetAsync(T.qcnt, 0, sizeof(int32_t) * T.NP, st);
+  k_tinit<<<T.NP, 256, 0, st>>>(d, T, T.fv[0], T.fq[0], T.nf + 0); VLS_LAUNCH(b);
+  k_tctl_set<<<1, 1, 0, st>>>(d.ctl, CTL_TAU, 0); VLS_LAUNCH(b);
+  k_tfrontier<<<b.cfg[KK_TFRONTIER].grid, b.cfg[KK_TFRONTIER].threads, 0, st>>>(d, T); VLS_LAUNCH(b);
   cudaMemsetAsync(T.nf + 0, 0, sizeof(int32_t), st);
-  int32_t tau = 0;
-  const int sync_every = b.opt.sync_interval > 0 ? b.opt.sync_interval : 8;
-  for (;;) {
-    ++tau;
-    const int cur = tau & 1, nxt = cur ^ 1;
-    const long ps = b.prof.begin(st, 1);
-    k_tupdate<<<b.grid, b.threads, 0, st>>>(d, T, b.prm, T.fv[cur], T.fq[cur], T.nf + cur); VLS_LAUNCH(b);
-    b.prof.end(st, ps);
-    k_tapply<<<b.grid, b.threads, 0, st>>>(d, T, T.fv[cur], T.fq[cur], T.nf + cur, tau, b.prm.theta); VLS_LAUNCH(b);
-    k_tfrontier<<<b.grid, b.threads, 0, st>>>(d, T, T.fv[cur], T.fq[cur], T.nf + cur, T.fv[nxt], T.fq[nxt],
-                                              T.nf + nxt, tau + 1); VLS_LAUNCH(b);
-    k_tepilogue<<<1, 256, 0, st>>>(T, cnt, tau, b.opt.max_pass_steps, T.nf + cur); VLS_LAUNCH(b);
-    if (tau % sync_every == 0) {
-      int32_t act = 0;
-      cudaError_t e = cudaMemcpyAsync(&act, T.active, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-      b.d2h += (int64_t)sizeof(int32_t);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) return e;
-      if (act == 0) break;
+  k_tctl_set<<<1, 1, 0, st>>>(d.ctl, CTL_TAU, 1); VLS_LAUNCH(b);
+  cudaError_t e = cudaSuccess;
+  if (b.host_loop) {
+    Handles H{};
+    H.use = 0;
+    const int sync_every = b.opt.sync_interval > 0 ? b.opt.sync_interval : 16;
+    for (int32_t tau = 1;; ++tau) {
+      long ps = b.prof.begin(st, KK_TUPDATE);
+      k_tupdate<<<b.cfg[KK_TUPDATE].grid, b.cfg[KK_TUPDATE].threads, 0, st>>>(d, T, b.prm); VLS_LAUNCH(b);
+      b.prof.end(st, ps);
+      ps = b.prof.begin(st, KK_TAPPLY);
+      k_tapply<<<b.cfg[KK_TAPPLY].grid, b.cfg[KK_TAPPLY].threads, 0, st>>>(d, T, b.prm.theta); VLS_LAUNCH(b);
+      b.prof.end(st, ps);
+      ps = b.prof.begin(st, KK_TFRONTIER);
+      k_tfrontier<<<b.cfg[KK_TFRONTIER].grid, b.cfg[KK_TFRONTIER].threads, 0, st>>>(d, T); VLS_LAUNCH(b);
+      b.prof.end(st, ps);
+      ps = b.prof.begin(st, KK_TEPILOGUE);
+      k_tepilogue<<<1, 256, 0, st>>>(d, T, H, b.opt.max_pass_steps); VLS_LAUNCH(b);
+      b.prof.end(st, ps);
+      if (tau % sync_every == 0) {
+        int32_t act = 0;
+        e = cudaMemcpyAsync(&act, d.ctl + CTL_TACTIVE, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        b.d2h += (int64_t)sizeof(int32_t);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        if (act == 0) break;
+      }
     }
+  } else {
+    cudaGraph_t g = nullptr, body = nullptr;
+    cudaGraphNode_t w, n0, n1, n2, n3;
+    Handles H{};
+    H.use = 1;
+    e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess) e = add_conditional(&w, g, nullptr, 0, cudaGraphCondTypeWhile, 1u, &H.loop, &body);
+    if (e == cudaSuccess) e = add_kernel(&n0, body, nullptr, 0, k_tupdate, dim3(b.cfg[KK_TUPDATE].grid), dim3(b.cfg[KK_TUPDATE].threads), d, T, b.prm);
+    if (e == cudaSuccess) e = add_kernel(&n1, body, &n0, 1, k_tapply, dim3(b.cfg[KK_TAPPLY].grid), dim3(b.cfg[KK_TAPPLY].threads), d, T, b.prm.theta);
+    if (e == cudaSuccess) e = add_kernel(&n2, body, &n1, 1, k_tfrontier, dim3(b.cfg[KK_TFRONTIER].grid), dim3(b.cfg[KK_TFRONTIER].threads), d, T);
+    if (e == cudaSuccess)
+      e = add_kernel(&n3, body, &n2, 1, k_tepilogue, dim3(1), dim3(256), d, T, H, b.opt.max_pass_steps);
+    cudaGraphExec_t ge = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
   }
   k_ttrace<<<(T.NP + 127) / 128, 128, 0, st>>>(d, T); VLS_LAUNCH(b);
-  *h_steps_out = tau;
-  return cudaGetLastError();
+  int32_t tau_end = 0;
+  e = cudaMemcpyAsync(&tau_end, d.ctl + CTL_TAU, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  b.d2h += (int64_t)sizeof(int32_t);
+  *h_steps_out = tau_end - 1;
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 }  // namespace vls

@@ -53,6 +53,15 @@ struct TDev {
   int32_t *path;         // scratch [pass-vertex] for traces
 };
 
+// Kernel kinds timed in profile mode.
+enum KernelKind : int {
+  KK_UPDATE = 0, KK_TUPDATE, KK_APPLY, KK_HOOK, KK_COUNT, KK_FRONTIER, KK_EPILOGUE, KK_MERGE_GROUPS,
+  KK_TRACE, KK_MERGE_FINISH, KK_RELABEL, KK_SPLIT, KK_TAPPLY, KK_TFRONTIER, KK_TEPILOGUE, KK_COUNT_KINDS
+};
+static const char *const kKernelNames[KK_COUNT_KINDS] = {
+    "k_update", "k_tupdate", "k_apply", "k_band_hook", "k_band_count", "k_frontier", "k_epilogue",
+    "k_merge_groups", "k_trace", "k_merge_finish", "k_relabel", "k_split", "k_tapply", "k_tfrontier", "k_tepilogue"};
+
 // Optional CUDA-event timing of selected launches (pairs drawn from a context-owned pool).
 struct Prof {
   std::vector<cudaEvent_t> *pool = nullptr; // owned by the context, grows on demand
@@ -83,6 +92,7 @@ struct Prof {
 
 struct Batch {
   Prof prof;
+  bool host_loop = false; // debug / profiling: launch each step from the host
   int64_t h2d = 0, d2h = 0;
   cudaStream_t st = nullptr;
   vls_options opt;
@@ -92,7 +102,12 @@ struct Batch {
   int32_t P = 0, V = 0, NF = 0, Lcap = 0;
   int64_t nnz = 0;
   int sm_count = 148;
-  int grid = 0, threads = 256;
+  int grid = 0, threads = 64;     // row kernels
+  int ggrid = 0, gthreads = 256;  // 16-lanes-per-row kernels and vertex scans
+  // per-kernel launch shape: one resident wave (SM count x resident blocks per SM)
+  struct Cfg {
+    int grid = 0, threads = 0;
+  } cfg[KK_COUNT_KINDS];
   long long launches = 0;
   Arena *arena = nullptr;
   // host copies of problem tables
@@ -102,15 +117,65 @@ struct Batch {
 
 #define VLS_LAUNCH(b) ((b).launches++)
 
+// ---------------------------------------------------------------- graph helpers
+template <class T> struct ident { using type = T; };
+
+// Add a kernel node f<<<grid, block>>>(args...) to graph g after deps.
+template <class... K>
+inline cudaError_t add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps,
+                              void (*f)(K...), dim3 grid, dim3 block, typename ident<K>::type... args) {
+  void *params[] = {(void *)&args..., nullptr};
+  cudaKernelNodeParams p = {};
+  p.func = (void *)f;
+  p.gridDim = grid;
+  p.blockDim = block;
+  p.sharedMemBytes = 0;
+  p.kernelParams = params;
+  return cudaGraphAddKernelNode(node, g, deps, ndeps, &p);
+}
+
+// Add a conditional node (IF / WHILE) to g after deps; its handle is created on g with the
+// given default (assigned at every launch of the graph).  *body receives the body graph.
+inline cudaError_t add_conditional(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps,
+                                   cudaGraphConditionalNodeType type, unsigned dflt,
+                                   cudaGraphConditionalHandle *h, cudaGraph_t *body) {
+  cudaError_t e = cudaGraphConditionalHandleCreate(h, g, dflt, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = *h;
+  np.conditional.type = type;
+  np.conditional.size = 1;
+  e = cudaGraphAddNode(node, g, deps, nullptr, ndeps, &np);
+  if (e != cudaSuccess) return e;
+  *body = np.conditional.phGraph_out[0];
+  return cudaSuccess;
+}
+
+// launch shapes (one resident wave per kernel), per translation unit
+void configure_initial(Batch &b);
+void configure_events(Batch &b);
+void configure_tunnel(Batch &b);
+template <class K> inline Batch::Cfg wave_cfg(const Batch &b, K kernel, int threads) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess || nb < 1) nb = 1;
+  Batch::Cfg c;
+  c.grid = b.sm_count * nb;
+  c.threads = threads;
+  return c;
+}
 // operator.cu
 cudaError_t build_operator(Batch &b, int32_t *d_status_stage);
-// initial.cu
+// initial.cu: the initial pass as one graph (WHILE over steps) or, for debugging, a host loop
 cudaError_t init_state(Batch &b);
-cudaError_t initial_step(Batch &b, int t);
+cudaError_t build_initial_graph(Batch &b, cudaGraph_t *graph);
+cudaError_t initial_step_host(Batch &b);
 cudaError_t final_checks(Batch &b);
-// events.cu
-cudaError_t merge_phase(Batch &b, int t, int cur);
-cudaError_t split_phase(Batch &b, int t, int cur);
+// events.cu: bodies of the IF nodes (and their host-loop launches)
+cudaError_t add_merge_nodes(Batch &b, cudaGraph_t body);
+cudaError_t add_split_nodes(Batch &b, cudaGraph_t body);
+cudaError_t merge_phase_host(Batch &b);
+cudaError_t split_phase_host(Batch &b);
 // tunnel.cu
 cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out);
 

@@ -17,6 +17,7 @@
 //   Layers have global ids; problem p owns [lbase[p], lbase[p] + lcap[p]); local id =
 //   global - lbase[p] (1 = seed layer, then creation order).
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,8 +33,12 @@ constexpr int TRACE_CAP = 1 << 16; // crossing edges per traced isoline
 enum LayerState : int32_t { L_UNUSED = 0, L_ALIVE = 1, L_DEAD = 2, L_MERGED = 3, L_ENDED = 4 };
 enum NodeKind : int32_t { N_SEED = 0, N_SPLIT = 1, N_MERGE = 2, N_END = 3 };
 
+constexpr int LV_MAX = 64; // longest row of the register / local-memory row paths
+
 struct Params {
   double mu, e, w, ah, dt, s, eps0, one_m_eps, theta;
+  double lv[LV_MAX + 1];  // s / d: off-diagonal operator entry of a row with d kept neighbours
+  double mun[KMAX + 2];   // mu / n for n phases meeting at a vertex
 };
 
 // Global device state of one batch.  Passed by value to kernels.
@@ -111,7 +116,53 @@ struct Dev {
   int32_t *rband;   // [P]
   // error word
   int32_t *err;
+  // device control block (see CTL_*), per-problem live layers and layers holding a band root
+  int32_t *ctl;
+  int32_t *nalive, *nbl;
 };
+
+// Control block: the step loops run on the device (a CUDA graph WHILE node around the step
+// body), so the step counters live in device memory and every step kernel reads them.
+enum Ctl : int {
+  CTL_T = 0,          // current initial-pass step
+  CTL_ACTIVE = 1,     // problems still running
+  CTL_MERGE = 2,      // a collision row appeared this step
+  CTL_SPLIT = 3,      // a band has != 1 components this step
+  CTL_DONE_APPLY = 4, // last-block counters
+  CTL_DONE_COUNT = 5,
+  CTL_LIMIT = 6,      // hard step bound of the initial pass
+  CTL_TAU = 7,        // current tunnel-pass step
+  CTL_TACTIVE = 8,    // passes still running
+  CTL_TLIMIT = 9,     // hard step bound of the tunnel passes
+  CTL_NMERGE = 10,    // merge phases executed (launch accounting)
+  CTL_NSPLIT = 11,    // split phases executed
+  CTL_SIZE = 16
+};
+
+// Conditional handles of the step graph; `use` = 0 when the kernels run from a host loop.
+struct Handles {
+  cudaGraphConditionalHandle loop, merge, split;
+  int32_t use;
+};
+
+// True in exactly one thread of the grid: thread 0 of the last block to finish.  Every thread
+// of every block must call it (after its share of the work).
+__device__ __forceinline__ bool last_block_done(int32_t *counter) {
+  __shared__ bool last;
+  __threadfence(); // every thread's flag stores become visible before the block reports done
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(counter, 1) == (int32_t)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    *counter = 0;
+    return true;
+  }
+  return false;
+}
 
 // ----------------------------------------------------------- FP64 arithmetic
 // Explicit round-to-nearest operations: no contraction into FMA, each operation rounded on
@@ -124,6 +175,13 @@ __device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
 
 __device__ __forceinline__ bool frozen_state(int32_t st) { return st == L_DEAD || st == L_ENDED; }
 
+// Exact tests on stored values x in [0, 1] (never NaN) done on the bit pattern: for
+// non-negative doubles the order of the bits is the order of the values, and 1 - x > 0 holds
+// exactly when x < 1.  (GB300 has few FP64 units; these keep decisions off them.)
+__device__ __forceinline__ bool val_pos(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool val_lt1(double x) { return __double_as_longlong(x) < 0x3FF0000000000000LL; }
+__device__ __forceinline__ bool val_band(double x) { return val_pos(x) && val_lt1(x); }
+
 // One explicit Euler step of Eq. (2) at one vertex (base present; nl non-base layers in
 // ascending id order with own values x[] and Laplacians lap[]; base value xb, Laplacian
 // lapb).  Only pairs (layer, base) have mu_ij, e_ij != 0 (Sec. 2); e is antisymmetric so the
@@ -132,7 +190,7 @@ __device__ __forceinline__ bool frozen_state(int32_t st) { return st == L_DEAD |
 // the column sum vanished (values left unchanged).
 __device__ __forceinline__ bool vertex_update(const Params &P, int nl, const double *x, const double *lap,
                                               double xb, double lapb, double *out) {
-  double mun = ddiv(P.mu, (double)(nl + 1));
+  const double mun = P.mun[nl + 1]; // = mu / n, rounded once on the host (same IEEE quotient)
   double y[KMAX];
   double sr = 0.0;
 #pragma unroll
@@ -192,6 +250,20 @@ __device__ __forceinline__ void uf_unite(int32_t *par, int32_t a, int32_t b) {
     rb = uf_find(par, old);
     ra = uf_find(par, ra);
   }
+}
+
+// Append to a list shared by the whole grid with one atomic per warp (the lanes that reach this
+// call together), and bump a per-key counter with one atomic per key present in the warp.
+// Returns this lane's slot.  Must be called only by lanes that append.
+__device__ __forceinline__ int32_t warp_append(int32_t *counter, int32_t *key_counts, int32_t key) {
+  namespace cg = cooperative_groups;
+  cg::coalesced_group g = cg::coalesced_threads();
+  int32_t base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(counter, (int32_t)g.size());
+  base = g.shfl(base, 0) + (int32_t)g.thread_rank();
+  cg::coalesced_group kg = cg::labeled_partition(g, key);
+  if (kg.thread_rank() == 0) atomicAdd(&key_counts[key], (int32_t)kg.size());
+  return base;
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {

@@ -48,7 +48,7 @@ class vls_stats(ctypes.Structure):
 EXPORTS = ["vls_default_options", "vls_constants", "vls_create", "vls_destroy", "vls_detect", "vls_detect_batch",
            "vls_result_count", "vls_result_status", "vls_result_genus", "vls_result_stats", "vls_result_num_loops",
            "vls_result_loop", "vls_result_handle", "vls_result_tunnel", "vls_result_reeb", "vls_result_state",
-           "vls_result_records", "vls_result_free", "vls_status_string"]
+           "vls_result_records", "vls_result_kernel_times", "vls_result_free", "vls_status_string"]
 
 _lib = None
 
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH):
     L.vls_result_state.restype = i32
     L.vls_result_records.argtypes = [vp, i32, P(P(i64)), P(i32)]
     L.vls_result_records.restype = i32
+    L.vls_result_kernel_times.argtypes = [vp, P(P(ctypes.c_char_p)), P(P(i64)), P(P(dbl)), P(i32)]
+    L.vls_result_kernel_times.restype = i32
     L.vls_result_free.argtypes = [vp]
     L.vls_result_free.restype = None
     L.vls_status_string.argtypes = [i32]
@@ -232,6 +234,15 @@ def _np(ptr, n, dtype):
     if n <= 0 or not ptr:
         return np.zeros(0, dtype)
     return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dtype, copy=True)
+
+
+def vls_result_kernel_times(res) -> dict:
+    """{kernel name: (launches, total ms)} of a result computed with profile = 1."""
+    L = load()
+    P = ctypes.POINTER
+    names, launches, ms, n = P(ctypes.c_char_p)(), P(ctypes.c_int64)(), P(ctypes.c_double)(), ctypes.c_int32()
+    L.vls_result_kernel_times(res, ctypes.byref(names), ctypes.byref(launches), ctypes.byref(ms), ctypes.byref(n))
+    return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(n.value)}
 
 
 def read_result(res) -> list:
