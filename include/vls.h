@@ -46,7 +46,8 @@ typedef enum {
   VLS_ETIMEOUT = 9,        /* reserved: bounded device-side wait gave up */
   VLS_ENOMEM = 10,         /* device or host allocation failed */
   VLS_ECUDA = 11,          /* CUDA runtime error (kernel launch / copy) */
-  VLS_ESTALL = 12          /* no front left but parts of the surface were never covered */
+  VLS_ESTALL = 12,         /* no front left but parts of the surface were never covered */
+  VLS_ETOOLARGE = 13       /* input above the fixed limits of vls_tunnel_pass_noalloc */
 } vls_status;
 
 typedef enum { VLS_FP64 = 0, VLS_FP32_RECHECK = 1 } vls_precision;
@@ -176,6 +177,30 @@ VLS_API vls_status vls_result_kernel_times(const vls_result *r, const char *cons
 VLS_API vls_status vls_result_records(const vls_result *r, int32_t p, const int64_t **rec, int32_t *steps);
 
 VLS_API void vls_result_free(vls_result *r);
+
+/*
+ * One tunnel pass without any device allocation.  The paper has no counterpart: this is a
+ * convenience for callers that cannot allocate device memory (code that must run inside a
+ * pre-sized memory pool or an allocation-free region, where every device byte is budgeted
+ * up front).  It computes exactly the tunnel loop vls_detect reports for a handle, from:
+ *   F [nf][3]       device, the closed oriented mesh (vertex ids < nv) given to vls_detect
+ *   cover [nv]      device, the cover step of every vertex (vls_result_state)
+ *   handle_step     the step at which the handle was found (vls_result_handle info[0])
+ *   edges [n][2]    device, the handle's crossing edges in loop order (vls_result_handle)
+ * and writes, on the device, out_verts[0..n) (capacity nv) and out_info[4] = status, step the
+ * pass stopped, first vertex reached, n.  Options o may be NULL (defaults).
+ * Limits: nv <= 262144, nf <= 786432, n_edges <= 65536; larger inputs return VLS_ETOOLARGE.
+ * All scratch (about 22 MB) lives in one static device array of the library, which every
+ * device that loads the library holds until the process exits.  The call allocates nothing
+ * and returns after queueing one kernel on cuda_stream (NULL: default stream).  The first
+ * call on a device looks up the array's device address; make that first call before any
+ * stream capture.  Calls share the array: calls that overlap on the GPU (different streams,
+ * different host threads) race and must be serialised by the caller.
+ */
+VLS_API vls_status vls_tunnel_pass_noalloc(const int32_t *F, int64_t nf, int64_t nv, const int32_t *cover,
+                                           int32_t handle_step, const int32_t *edges, int64_t n_edges,
+                                           const vls_options *o, void *cuda_stream, int32_t *out_verts,
+                                           int32_t *out_info);
 VLS_API const char *vls_status_string(vls_status s);
 
 #ifdef __cplusplus

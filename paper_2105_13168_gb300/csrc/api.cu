@@ -122,6 +122,7 @@ extern "C" const char *vls_status_string(vls_status s) {
   case VLS_ENOMEM: return "out of memory";
   case VLS_ECUDA: return "CUDA error";
   case VLS_ESTALL: return "front stopped before covering the surface";
+  case VLS_ETOOLARGE: return "input above the fixed limits of the no-allocation entry point";
   }
   return "unknown status";
 }

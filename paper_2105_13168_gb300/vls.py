@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libvls.so")
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOTMANIFOLD", 3: "ENONORIENTABLE", 4: "EDISCONNECTED",
           5: "EMAXSTEPS", 6: "ESLOTS", 7: "ELAYERS", 8: "ELOOPFAIL", 9: "ETIMEOUT", 10: "ENOMEM",
-          11: "ECUDA", 12: "ESTALL"}
+          11: "ECUDA", 12: "ESTALL", 13: "ETOOLARGE"}
 VLS_FP64, VLS_FP32_RECHECK = 0, 1
 
 
@@ -48,7 +48,8 @@ class vls_stats(ctypes.Structure):
 EXPORTS = ["vls_default_options", "vls_constants", "vls_create", "vls_destroy", "vls_detect", "vls_detect_batch",
            "vls_result_count", "vls_result_status", "vls_result_genus", "vls_result_stats", "vls_result_num_loops",
            "vls_result_loop", "vls_result_handle", "vls_result_tunnel", "vls_result_reeb", "vls_result_state",
-           "vls_result_records", "vls_result_kernel_times", "vls_result_free", "vls_status_string"]
+           "vls_result_records", "vls_result_kernel_times", "vls_result_free", "vls_status_string",
+           "vls_tunnel_pass_noalloc"]
 
 _lib = None
 
@@ -101,6 +102,8 @@ def load(path: str = LIB_PATH):
     L.vls_result_kernel_times.restype = i32
     L.vls_result_free.argtypes = [vp]
     L.vls_result_free.restype = None
+    L.vls_tunnel_pass_noalloc.argtypes = [vp, i64, i64, vp, i32, vp, i64, P(vls_options), vp, vp, vp]
+    L.vls_tunnel_pass_noalloc.restype = i32
     L.vls_status_string.argtypes = [i32]
     L.vls_status_string.restype = ctypes.c_char_p
     _lib = L
@@ -177,6 +180,18 @@ def vls_detect(ctx, X, F, seed: int, device: bool = False) -> ctypes.c_void_p:
     if not out.value:
         raise RuntimeError(f"vls_detect failed: {STATUS.get(st, st)}")
     return out
+
+
+def vls_tunnel_pass_noalloc(F, nv: int, cover, handle_step: int, edges, out_verts, out_info,
+                            opts: vls_options | None = None, stream: int = 0) -> int:
+    """One tunnel pass with no device allocation (all arguments are CUDA tensors: F int32
+    [nf, 3], cover int32 [nv], edges int32 [n, 2], out_verts int32 [nv], out_info int32 [4]).
+    Returns the launch status; the pass status is out_info[0] once the stream has run."""
+    return int(load().vls_tunnel_pass_noalloc(
+        ctypes.c_void_p(F.data_ptr()), int(F.shape[0]), int(nv), ctypes.c_void_p(cover.data_ptr()),
+        int(handle_step), ctypes.c_void_p(edges.data_ptr()), int(edges.shape[0]),
+        ctypes.byref(opts) if opts is not None else None, ctypes.c_void_p(stream) if stream else None,
+        ctypes.c_void_p(out_verts.data_ptr()), ctypes.c_void_p(out_info.data_ptr())))
 
 
 def vls_result_free(res) -> None:
