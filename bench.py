@@ -126,9 +126,9 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def update_kernel_traffic():
-    """dram bytes per launch of the update kernel from a committed ncu capture, if the kernel
-    source is unchanged since (else None)."""
+def update_kernel_traffic(rows_per_launch: float):
+    """DRAM bytes per launch of the update kernel: bytes per row from a committed ncu capture
+    scaled by the mean rows per launch, if the kernel source is unchanged since (else None)."""
     p = os.path.join(ROOT, "profiles", "k_update_traffic.json")
     if not os.path.exists(p):
         return None
@@ -136,9 +136,9 @@ def update_kernel_traffic():
         d = json.load(f)
     src = os.path.join(ROOT, "paper_2105_13168_gb300", "csrc", "initial.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if d.get("source_sha256") != h:
+    if d.get("source_sha256") != h or not d.get("dram_bytes_per_row"):
         return None
-    return d.get("dram_bytes_per_launch")
+    return float(d["dram_bytes_per_row"]) * rows_per_launch
 
 
 def cpu_baseline(probs, nsample: int) -> dict:
@@ -332,7 +332,7 @@ def main():
     achieved = (rows_per_launch * bytes_per_row / launch_s) / 1e9 if launch_s else None
     roof = {"kernel": "k_update (initial-pass frontier update, FP64)", "bound": "hbm", "achieved": achieved,
             "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-            "traffic": update_kernel_traffic(), "bytes_per_row": round(bytes_per_row, 2),
+            "traffic": update_kernel_traffic(rows_per_launch), "bytes_per_row": round(bytes_per_row, 2),
             "rows_per_launch": round(rows_per_launch, 1), "launch_us": launch_s * 1e6 if launch_s else None,
             "launches": upd_n, "share_of_timed_step": (upd_ms / ms) if ms else None,
             "method": "CUDA events around each launch in a kernel-timing pass of the same workload "
