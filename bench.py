@@ -4,16 +4,23 @@
 One step = one complete detection of the batch -- operator build, initial pass (every
 event, loop and Reeb node), tunnel passes and result download -- for 4 seed vertices on
 the tube-chain mesh (8 smooth-unioned tori R = 1, r = 0.35, spacing 1.6, blend 0.15,
-marching tetrahedra, ~512k faces, genus 8, normal jitter 0.1 of the mean edge).
+marching tetrahedra, ~512k faces, genus 8, normal jitter 0.1 of the mean edge), all four
+problems in one batch (one launch per kernel per step, step loops as device-driven graphs).
 
 value  = faces per step / device time per step (CUDA events on the library's stream,
-         inputs already in HBM, L2 flushed by a 256 MiB write before each timed step);
+         inputs already in HBM, L2 flushed by a 256 MiB write before each timed step), in
+         the FP32 form (FP32 values, rows deciding near a threshold redone in FP64) unless
+         --precision fp64;
 e2e    = the same metric through the C ABI with host (pinned) buffers, host wall time,
          host->device input copies and result download inside the call;
-roofline = the initial-pass frontier update kernel (the dominant kernel): algorithmic
+plain_fp64 = the same problems one per call, FP64, kernels launched from the host (no
+         batching, no graph); speedup_vs_plain_fp64 = value / plain_fp64.value;
+roofline = the initial-pass frontier update kernel (the diffusion SpMV): algorithmic
          bytes per launch / mean launch time from CUDA events recorded around each launch
          inside the library, against the measured HBM copy bandwidth;
-cpu_baseline = the plain CPU oracle on a bounded sample of the same workload.
+cpu_baseline = the plain CPU oracle on a bounded sample of the same workload;
+check_vs_oracle = those sampled problems' GPU results against the oracle's: integer
+         results identical, max |phi - phi_oracle|, rows redone in FP64.
 
 --impl reference times the CPU oracle itself (the only reference implementation of this
 method available here) with the same metric and JSON layout.
@@ -53,6 +60,10 @@ def parse_args():
                     help="one detection of the workload bounded to --max-steps initial steps (for profilers)")
     ap.add_argument("--max-steps", type=int, default=400)
     ap.add_argument("--max-pass-steps", type=int, default=200)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="form of the timed batched path (fp32: FP32 values with FP64 near-threshold recheck)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison arm")
+    ap.add_argument("--plain-steps", type=int, default=1, help="timed steps of the plain FP64 arm")
     return ap.parse_args()
 
 
@@ -117,6 +128,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(faces_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job faces/s: every rank detects its own copy of the batch (weak scaling) and the job
+    takes as long as its slowest rank."""
+    return faces_per_rank * world / (ms_max / 1e3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -126,7 +154,7 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def update_kernel_traffic(rows_per_launch: float):
+def update_kernel_traffic(rows_per_launch: float, prec: str):
     """DRAM bytes per launch of the update kernel: bytes per row from a committed ncu capture
     scaled by the mean rows per launch, if the kernel source is unchanged since (else None)."""
     p = os.path.join(ROOT, "profiles", "k_update_traffic.json")
@@ -136,7 +164,7 @@ def update_kernel_traffic(rows_per_launch: float):
         d = json.load(f)
     src = os.path.join(ROOT, "paper_2105_13168_gb300", "csrc", "initial.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if d.get("source_sha256") != h or not d.get("dram_bytes_per_row"):
+    if d.get("source_sha256") != h or d.get("precision", "fp64") != prec or not d.get("dram_bytes_per_row"):
         return None
     return float(d["dram_bytes_per_row"]) * rows_per_launch
 
@@ -147,14 +175,40 @@ def cpu_baseline(probs, nsample: int) -> dict:
     flat = [(m, s) for m, seeds in probs for s in seeds][:max(1, nsample)]
     t0 = time.perf_counter()
     faces = 0
+    results = []
     for m, s in flat:
-        r = oracle.detect(m, s)
+        r = oracle.detect(m, s, record_steps=1)
         assert r.status == 0, r.status_name
         faces += m.nf
+        results.append(r)
     dt = time.perf_counter() - t0
+    # untimed: the same problems stopped at step 400 (front in flight), for the value check
+    midrun = [oracle.detect(m, s, max_steps=400, tunnels=0) for m, s in flat]
     return {"value": faces / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": round(dt, 2),
             "sample": f"{len(flat)} of {sum(len(s) for _, s in probs)} problems of the same workload, full detection "
-                      "(initial pass + tunnel passes), single-threaded FP64 oracle"}
+                      "(initial pass + tunnel passes), single-threaded FP64 oracle"}, results, midrun
+
+
+def compare_with_oracle(g, o) -> dict:
+    """The FP32-form contract against the oracle for one problem: events, layer table, handle
+    and tunnel loops and final layers identical; steps whose band records differ and vertices
+    whose cover step differs counted (a leading-edge decision closer to eps0 than the FP32 drift
+    can go the other way for one step)."""
+    import numpy as np
+
+    same = (g.status == o.status and g.genus == o.genus and g.events() == o.events()
+            and np.array_equal(g.layers, o.layers) and len(g.handles) == len(o.handles)
+            and len(g.tunnels) == len(o.tunnels) and np.array_equal(g.layer, o.layer))
+    if same:
+        for hg, ho in zip(g.handles, o.handles):
+            same &= (hg.step, hg.layer) == (ho.step, ho.layer) and np.array_equal(hg.edges, ho.edges) \
+                and np.array_equal(hg.verts, ho.verts)
+        for tg, to in zip(g.tunnels, o.tunnels):
+            same &= (tg.status, tg.stop_step, tg.bstar) == (to.status, to.stop_step, to.bstar) \
+                and np.array_equal(tg.verts, to.verts)
+    rec = int((g.records != o.records).any(axis=1).sum()) if len(g.records) == len(o.records) else -1
+    return {"identical": bool(same), "record_steps_differing": rec,
+            "cover_steps_differing": int((g.cover != o.cover).sum())}
 
 
 def run_reference(args):
@@ -201,7 +255,8 @@ def run_profile_case(args):
     cfg, faces = workload_desc(probs)
     dev = torch.device("cuda", 0)
     meshes_dev = [(torch.from_numpy(m.X).to(dev), torch.from_numpy(m.F).to(dev)) for m, _ in probs]
-    opts = vls.vls_default_options(max_steps=args.max_steps, max_pass_steps=args.max_pass_steps)
+    opts = vls.vls_default_options(max_steps=args.max_steps, max_pass_steps=args.max_pass_steps,
+                                   precision=args.precision)
     ctx = vls.vls_create(opts, torch.cuda.current_stream().cuda_stream)
     res = vls.vls_detect_batch(ctx, meshes_dev, [s for _, s in probs], device=True)
     out = vls.read_result(res)
@@ -242,12 +297,13 @@ def main():
     probs = meshgen.workload(2, args.scale)
     cfg, faces = workload_desc(probs)
     # CPU baseline (rank 0, one GPU): timed before any GPU work of this process
-    cpu = None
+    cpu, orc_results, orc_midrun = None, [], []
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(probs, args.cpu_sample)
+        cpu, orc_results, orc_midrun = cpu_baseline(probs, args.cpu_sample)
 
     stream = torch.cuda.current_stream()
-    ctx = vls.vls_create(vls.vls_default_options(), stream.cuda_stream)
+    prec = args.precision
+    ctx = vls.vls_create(vls.vls_default_options(precision=prec), stream.cuda_stream)
     meshes_dev = [(torch.from_numpy(m.X).to(dev), torch.from_numpy(m.F).to(dev)) for m, _ in probs]
     seeds = [s for _, s in probs]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -288,12 +344,8 @@ def main():
     if dist is not None:
         dist.barrier()
     ms = sum(step_ms) / len(step_ms)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = faces * world / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, dev)
+    value = whole_job_value(faces, world, ms_max)
     # ---- e2e: host buffers through the C ABI (pinned), copies inside the call
     pinned = [(torch.from_numpy(m.X).pin_memory(), torch.from_numpy(m.F).pin_memory()) for m, _ in probs]
     meshes_host = [(x.numpy(), f.numpy()) for x, f in pinned]
@@ -310,7 +362,7 @@ def main():
     vls.vls_destroy(ctx)
     # ---- kernel timing pass: the same workload with CUDA events around every launch of the
     # frontier update kernel (host-driven launches so that each launch can be bracketed)
-    pctx = vls.vls_create(vls.vls_default_options(profile=1), stream.cuda_stream)
+    pctx = vls.vls_create(vls.vls_default_options(profile=1, precision=prec), stream.cuda_stream)
     flush.fill_(1)
     res = vls.vls_detect_batch(pctx, meshes_dev, seeds, device=True)
     pout = vls.read_result(res)
@@ -318,7 +370,66 @@ def main():
     vls.vls_destroy(pctx)
     upd_ms, upd_n = pout[0].stats["ms_update"], pout[0].stats["n_update"]
     rows = sum(p.stats["row_updates"] for p in pout)
-    prof_step_ms = pout[0].stats["ms_operator"] + pout[0].stats["ms_initial"] + pout[0].stats["ms_tunnel"]
+    # ---- the same batch once more with the final state kept: rechecks, and the check of the
+    # problems the CPU baseline ran against the oracle (integer results, max value error)
+    cctx = vls.vls_create(vls.vls_default_options(precision=prec, keep_state=1, record_steps=1), stream.cuda_stream)
+    res = vls.vls_detect_batch(cctx, meshes_dev, seeds, device=True)
+    cout = vls.read_result(res)
+    vls.vls_result_free(res)
+    vls.vls_destroy(cctx)
+    check = {"problems_checked": len(orc_results), "rechecks": cout[0].stats["rechecks"],
+             "pass_rechecks": cout[0].stats["pass_rechecks"], "row_updates": rows,
+             "pass_updates": sum(p.stats["pass_updates"] for p in cout)}
+    if orc_results:
+        cmp = [compare_with_oracle(g, o) for g, o in zip(cout, orc_results)]
+        check["events_loops_layers_identical"] = all(c["identical"] for c in cmp)
+        check["record_steps_differing"] = [c["record_steps_differing"] for c in cmp]
+        check["cover_steps_differing"] = [c["cover_steps_differing"] for c in cmp]
+        # values mid-run (front in flight; at the end every value is 0 or 1)
+        mctx = vls.vls_create(vls.vls_default_options(precision=prec, keep_state=1, max_steps=400, tunnels=0),
+                              stream.cuda_stream)
+        nchk = len(orc_results)
+        flat = [(x, f, s) for (x, f), ss in zip(meshes_dev, seeds) for s in ss][:nchk]
+        errs = []
+        for (x, f, s), om in zip(flat, orc_midrun):
+            r = vls.vls_detect(mctx, x, f, s, device=True)
+            gm = vls.read_result(r)[0]
+            vls.vls_result_free(r)
+            errs.append(float(np.abs(gm.phi - om.phi).max()))
+        vls.vls_destroy(mctx)
+        check["max_abs_err_phi_at_step_400"] = max(errs)
+    # ---- plain FP64 arm: the same problems one at a time (no batching), FP64, kernels launched
+    # from the host (no graph)
+    plain = None
+    if not args.no_plain:
+        qctx = vls.vls_create(vls.vls_default_options(precision="fp64", host_loop=1), stream.cuda_stream)
+        flat = [(x, f, s) for (x, f), ss in zip(meshes_dev, seeds) for s in ss]
+
+        def plain_step():
+            outs = []
+            for x, f, s in flat:
+                r = vls.vls_detect(qctx, x, f, s, device=True)
+                outs.extend(vls.read_result(r))
+                vls.vls_result_free(r)
+            return outs
+
+        x0, f0, s0 = flat[0]
+        vls.vls_result_free(vls.vls_detect(qctx, x0, f0, s0, device=True))  # warm-up
+        pms = []
+        for _ in range(max(1, args.plain_steps)):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pouts = plain_step()
+            e1.record(stream)
+            e1.synchronize()
+            pms.append(e0.elapsed_time(e1))
+            assert all(p.status == 0 for p in pouts)
+        vls.vls_destroy(qctx)
+        pm = sum(pms) / len(pms)
+        plain = {"value": faces / (pm / 1e3), "unit": UNIT, "ms_per_step": pm, "steps": len(pms),
+                 "form": "FP64, one problem per call (no batching), step kernels launched from the host (no graph)"}
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -326,25 +437,29 @@ def main():
     # ---- roofline of the frontier update kernel
     peak, peak_kind = measured_peaks()
     deg = sum(3 * m.nf * len(s) for m, s in probs) / sum(m.nv * len(s) for m, s in probs)
-    bytes_per_row = 44 + 4 * deg  # frontier entry 8, row bounds 8, columns 4d, own state 12, output 16
+    # frontier entry 8, row bounds 8, columns 4d, own state (layer 4 + value 8 or 4), output 16
+    bytes_per_row = (44 if prec == "fp64" else 40) + 4 * deg
     launch_s = (upd_ms / upd_n) / 1e3 if upd_n else None
     rows_per_launch = rows / upd_n if upd_n else 0
     achieved = (rows_per_launch * bytes_per_row / launch_s) / 1e9 if launch_s else None
-    roof = {"kernel": "k_update (initial-pass frontier update, FP64)", "bound": "hbm", "achieved": achieved,
+    roof = {"kernel": f"k_update (initial-pass frontier update, {prec.upper()})", "bound": "hbm", "achieved": achieved,
             "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-            "traffic": update_kernel_traffic(rows_per_launch), "bytes_per_row": round(bytes_per_row, 2),
+            "traffic": update_kernel_traffic(rows_per_launch, prec), "bytes_per_row": round(bytes_per_row, 2),
             "rows_per_launch": round(rows_per_launch, 1), "launch_us": launch_s * 1e6 if launch_s else None,
             "launches": upd_n, "share_of_timed_step": (upd_ms / ms) if ms else None,
             "method": "CUDA events around each launch in a kernel-timing pass of the same workload "
                       "(host-driven launches); the timed steps run the device-driven graph"}
-    cfg = dict(cfg, precision="fp64", inputs="resident in HBM (device pointers) for value; pinned host for e2e",
+    cfg = dict(cfg, precision=("fp32 values, fp64 near-threshold recheck" if prec == "fp32" else "fp64"), inputs="resident in HBM (device pointers) for value; pinned host for e2e",
                l2="flushed by a 256 MiB write before every timed step",
                parallelism=f"{world} GPU(s), each its own copy of the batch" if world > 1 else "1 GPU")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic", "config": cfg,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "roofline": roof, "clocks": clocks}
+            "gpu_launches": launches, "roofline": roof, "clocks": clocks, "check_vs_oracle": check}
+    if plain is not None:
+        line["plain_fp64"] = plain
+        line["speedup_vs_plain_fp64"] = value / world / plain["value"]
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

@@ -50,6 +50,17 @@ typedef enum {
   VLS_ETOOLARGE = 13       /* input above the fixed limits of vls_tunnel_pass_noalloc */
 } vls_status;
 
+/*
+ * Precision of the layer values (the paper does not state one):
+ *   VLS_FP64          values stored and updated in FP64, every operation rounded on its own in
+ *                     a fixed order (results are bit-reproducible).
+ *   VLS_FP32_RECHECK  values stored as float; the Eq. (2) step of a frontier row runs in FP32.
+ *                     A row whose step takes a decision within recheck_margin of its threshold
+ *                     (snap at eps0 or 1 - eps0, the level theta_iso) or where several layers
+ *                     meet is recomputed in FP64 from the same stored inputs, and its values are
+ *                     rounded to float without crossing any threshold.  FP64 is used for nothing
+ *                     else on the step path.
+ */
 typedef enum { VLS_FP64 = 0, VLS_FP32_RECHECK = 1 } vls_precision;
 
 /*
@@ -66,7 +77,7 @@ typedef struct {
   double eps0;              /* snap: values below eps0 -> 0, above 1 - eps0 -> 1 */
   double theta_iso;         /* isoline level of handle loops, arrival level of tunnel passes */
   double lbar;              /* operator length scale; <= 0 selects eta / 4 */
-  double recheck_margin;    /* FP32 mode: values within this of a threshold are redone in FP64 */
+  double recheck_margin;    /* FP32 form: rows deciding within this of a threshold are redone in FP64; (0, 0.25) */
   int32_t max_steps;        /* initial-pass step limit (per problem) */
   int32_t max_pass_steps;   /* tunnel-pass step limit (per pass) */
   int32_t tunnels;          /* 1: run the tunnel passes (Sec. 3.2) */
@@ -77,6 +88,8 @@ typedef struct {
   int32_t blocks_per_sm;    /* grid = blocks_per_sm x SM count (0: autotuned) */
   vls_precision precision;
   int32_t profile;          /* 1: time every frontier-update launch with CUDA events (vls_stats) */
+  int32_t host_loop;        /* 1: launch each step's kernels from the host instead of running the
+                               step loops as device-driven CUDA graphs (same results) */
 } vls_options;
 
 /* A closed, oriented triangle mesh: X[nv][3] positions, F[nf][3] vertex ids (CCW). */
@@ -104,6 +117,10 @@ typedef struct {
   double ms_update, ms_pass_update;
   int64_t n_update, n_pass_update;
   int64_t h2d_bytes, d2h_bytes; /* batch-wide host<->device bytes of this call */
+  /* precision = VLS_FP32_RECHECK: rows of the initial pass / tunnel passes whose FP32 step had
+   * a decision within recheck_margin of its threshold (or several layers) and was redone in
+   * FP64 (batch-wide); 0 in the FP64 form */
+  int64_t rechecks, pass_rechecks;
 } vls_stats;
 
 /* Fill *o with the defaults above. */
@@ -188,7 +205,8 @@ VLS_API void vls_result_free(vls_result *r);
  *   handle_step     the step at which the handle was found (vls_result_handle info[0])
  *   edges [n][2]    device, the handle's crossing edges in loop order (vls_result_handle)
  * and writes, on the device, out_verts[0..n) (capacity nv) and out_info[4] = status, step the
- * pass stopped, first vertex reached, n.  Options o may be NULL (defaults).
+ * pass stopped, first vertex reached, n.  Options o may be NULL (defaults); the pass always runs
+ * in FP64 (o->precision is not used), so it matches the FP64 form of vls_detect.
  * Limits: nv <= 262144, nf <= 786432, n_edges <= 65536; larger inputs return VLS_ETOOLARGE.
  * All scratch (about 22 MB) lives in one static device array of the library, which every
  * device that loads the library holds until the process exits.  The call allocates nothing

@@ -93,6 +93,8 @@ extern "C" void vls_default_options(vls_options *o) {
   o->threads = 0;
   o->blocks_per_sm = 0;
   o->precision = VLS_FP64;
+  o->profile = 0;
+  o->host_loop = 0;
 }
 
 extern "C" void vls_constants(const vls_options *o, double out[4]) {
@@ -133,6 +135,11 @@ extern "C" vls_status vls_create(vls_ctx **ctx, const vls_options *o, void *stre
   if (!c) return VLS_ENOMEM;
   if (o) c->opt = *o;
   else vls_default_options(&c->opt);
+  if ((c->opt.precision != VLS_FP64 && c->opt.precision != VLS_FP32_RECHECK) ||
+      (c->opt.precision == VLS_FP32_RECHECK && !(c->opt.recheck_margin > 0.0 && c->opt.recheck_margin < 0.25))) {
+    delete c;
+    return VLS_EINVAL;
+  }
   c->st = (cudaStream_t)stream;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -189,7 +196,10 @@ void layout_batch(Layout &L, Batch &b) {
   d.pupd = L.take<int64_t>(P);
   d.pev = L.take<int32_t>(4 * P);
   d.lay = L.take<int32_t>(V);
-  d.phi = L.take<double>(V);
+  const bool f32 = b.opt.precision == VLS_FP32_RECHECK;
+  d.phi = f32 ? nullptr : L.take<double>(V);
+  d.phif = f32 ? L.take<float>(V) : nullptr;
+  d.nrecheck = L.take<unsigned long long>(2);
   d.cover = L.take<int32_t>(V);
   d.stamp = L.take<int32_t>(V);
   d.fmark = L.take<int32_t>(V);
@@ -273,7 +283,9 @@ void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut) {
   T.heoff = L.take<int32_t>(NP);
   T.hen = L.take<int32_t>(NP);
   T.flag = L.take<int8_t>(PV);
-  T.phi = L.take<double>(PV);
+  const bool f32 = b.opt.precision == VLS_FP32_RECHECK;
+  T.phi = f32 ? nullptr : L.take<double>(PV);
+  T.phif = f32 ? L.take<float>(PV) : nullptr;
   T.T = L.take<int32_t>(PV);
   T.stamp = L.take<int32_t>(PV);
   T.fv[0] = L.take<int32_t>(PV);
@@ -347,7 +359,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
   {
     const char *hl = std::getenv("VLS_HOST_LOOP");
     // kernel timing needs CUDA events around single launches: profiling runs the host loop
-    b.host_loop = ctx->opt.profile != 0 || (hl && hl[0] == '1');
+    b.host_loop = ctx->opt.profile != 0 || ctx->opt.host_loop != 0 || (hl && hl[0] == '1');
   }
   g_d2h_counter = &b.d2h;
   b.st = ctx->st;
@@ -380,6 +392,18 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     for (int k = 1; k <= LV_MAX; ++k) P.lv[k] = P.s / (double)k;
     P.mun[0] = 0.0;
     for (int k = 1; k <= KMAX + 1; ++k) P.mun[k] = P.mu / (double)k;
+    P.margin = ctx->opt.recheck_margin;
+    P.f_e = (float)P.e;
+    P.f_w = (float)P.w;
+    P.f_ah = (float)P.ah;
+    P.f_dt = (float)P.dt;
+    P.f_s = (float)P.s;
+    P.f_eps0 = (float)P.eps0;
+    P.f_one_m_eps = (float)P.one_m_eps;
+    P.f_theta = (float)P.theta;
+    P.f_margin = (float)P.margin;
+    for (int k = 0; k <= LV_MAX; ++k) P.f_lv[k] = (float)P.lv[k];
+    for (int k = 0; k <= KMAX + 1; ++k) P.f_mun[k] = (float)P.mun[k];
   }
   std::vector<int32_t> dev_probs; // result index of each device problem
   int64_t V = 0, NF = 0, Lc = 0;
@@ -482,7 +506,9 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     // ---- state init
     CK(cudaMemcpyAsync(d.pstatus, h_status.data(), sizeof(int32_t) * b.P, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(d.lay, 0, sizeof(int32_t) * b.V, st));
-    CK(cudaMemsetAsync(d.phi, 0, sizeof(double) * b.V, st));
+    if (d.phif) CK(cudaMemsetAsync(d.phif, 0, sizeof(float) * b.V, st));
+    else CK(cudaMemsetAsync(d.phi, 0, sizeof(double) * b.V, st));
+    CK(cudaMemsetAsync(d.nrecheck, 0, sizeof(unsigned long long) * 2, st));
     CK(cudaMemsetAsync(d.cover, 0xff, sizeof(int32_t) * b.V, st));
     CK(cudaMemsetAsync(d.stamp, 0, sizeof(int32_t) * b.V, st));
     CK(cudaMemsetAsync(d.fmark, 0, sizeof(int32_t) * b.V, st));
@@ -621,7 +647,8 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       CK(cudaMemcpyAsync(const_cast<int32_t *>(T.heoff), heoff.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
       CK(cudaMemcpyAsync(const_cast<int32_t *>(T.hen), hen.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
       CK(cudaMemsetAsync(T.flag, 0, (size_t)PV, st));
-      CK(cudaMemsetAsync(T.phi, 0, sizeof(double) * PV, st));
+      if (T.phif) CK(cudaMemsetAsync(T.phif, 0, sizeof(float) * PV, st));
+      else CK(cudaMemsetAsync(T.phi, 0, sizeof(double) * PV, st));
       CK(cudaMemsetAsync(T.T, 0xff, sizeof(int32_t) * PV, st));
       CK(cudaMemsetAsync(T.stamp, 0, sizeof(int32_t) * PV, st));
       CK(cudaMemsetAsync(T.nf, 0, sizeof(int32_t) * 2, st));
@@ -688,7 +715,19 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     std::vector<double> phi_all;
     std::vector<long long> rec_all;
     if (ctx->opt.keep_state) {
-      if (!d2h(lay_all, d.lay, b.V, st) || !d2h(cover_all, d.cover, b.V, st) || !d2h(phi_all, d.phi, b.V, st)) {
+      if (!d2h(lay_all, d.lay, b.V, st) || !d2h(cover_all, d.cover, b.V, st)) {
+        err = cudaErrorUnknown;
+        goto fail;
+      }
+      if (d.phif) {
+        std::vector<float> phif_all;
+        if (!d2h(phif_all, d.phif, b.V, st)) {
+          err = cudaErrorUnknown;
+          goto fail;
+        }
+        CK(cudaStreamSynchronize(st));
+        phi_all.assign(phif_all.begin(), phif_all.end());
+      } else if (!d2h(phi_all, d.phi, b.V, st)) {
         err = cudaErrorUnknown;
         goto fail;
       }
@@ -699,6 +738,9 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     int32_t h_ctl[CTL_SIZE] = {};
     CK(cudaMemcpyAsync(h_ctl, d.ctl, sizeof(h_ctl), cudaMemcpyDeviceToHost, st));
     b.d2h += (int64_t)sizeof(h_ctl);
+    unsigned long long h_rechk[2] = {0ull, 0ull};
+    CK(cudaMemcpyAsync(h_rechk, d.nrecheck, sizeof(h_rechk), cudaMemcpyDeviceToHost, st));
+    b.d2h += (int64_t)sizeof(h_rechk);
     CK(cudaEventRecord(ev[4], st));
     CK(cudaStreamSynchronize(st));
     if (!b.host_loop) {
@@ -751,6 +793,8 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       r.stats.n_pass_update = n_k[KK_TUPDATE];
       r.stats.h2d_bytes = b.h2d;
       r.stats.d2h_bytes = b.d2h;
+      r.stats.rechecks = (int64_t)h_rechk[0];
+      r.stats.pass_rechecks = (int64_t)h_rechk[1];
       const int32_t nl = lcount[q];
       r.layers.resize(3 * (size_t)nl);
       for (int32_t l = 1; l <= nl; ++l) {

@@ -28,7 +28,7 @@ __device__ __forceinline__ double psi_iso(const Dev &d, int32_t u, int32_t l) {
   const int32_t lu = d.lay[u];
   if (lu == 0) return 0.0;
   if (frozen_state(d.lstate[lu])) return 1.0;
-  return lu == l ? d.phi[u] : 0.0;
+  return lu == l ? ph_ld(d, u) : 0.0;
 }
 __device__ __forceinline__ bool holds(const Dev &d, int32_t u, int32_t l) {
   const int32_t m = d.multi[u];
@@ -52,7 +52,7 @@ __device__ __forceinline__ bool in_band_of(const Dev &d, int32_t u, int32_t l) {
     return false;
   }
   if (d.lay[u] != l) return false;
-  return val_band(d.phi[u]);
+  return ph_band(d, u);
 }
 
 // block-wide FP64 sum of three coordinates and a count
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(1024) k_merge_finish(Dev d, Params P) {
       for (int q = 0; q < d.onl[row]; ++q) acc = dadd(acc, d.ophi[(int64_t)row * KMAX + q]);
       const int32_t v = fv[row];
       d.lay[v] = N;
-      d.phi[v] = acc;
+      ph_st_round(d, P, v, acc);
     }
     __syncthreads();
   }
@@ -561,8 +561,7 @@ __global__ void __launch_bounds__(256) k_split(Dev d) {
       if (fp[i] != p) continue;
       const int32_t v = fv[i];
       if (d.lay[v] != l) continue;
-      const double x = d.phi[v];
-      if (!(x > 0.0 && x < 1.0)) continue;
+      if (!ph_band(d, v)) continue;
       for (int q = 0; q < 3; ++q) acc[q] += d.X[3 * (int64_t)v + q];
       ++cnt;
       if (VCHK(d.err, d.uf[v], d.V, 221) && d.uf[v] == v) {
@@ -596,8 +595,7 @@ __global__ void __launch_bounds__(256) k_split(Dev d) {
       if (fp[i] != p) continue;
       const int32_t v = fv[i];
       if (d.lay[v] != l) continue;
-      const double x = d.phi[v];
-      if (!(x > 0.0 && x < 1.0)) continue;
+      if (!ph_band(d, v)) continue;
       const int32_t r = uf_find(d.uf, v);
       if (!VCHK(d.err, r, d.V, 220)) continue;
       for (int32_t k = 0; k < nr; ++k)

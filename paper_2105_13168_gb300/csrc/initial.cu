@@ -22,13 +22,82 @@ __device__ __forceinline__ int32_t append(int32_t *counter) { return atomicAdd(c
 // Neighbour states of a row are gathered into registers first (all loads of one level issued
 // together: columns, then layer ids and values, then layer states), so a row costs a few
 // memory latencies instead of one per neighbour and pass.  MAXD bounds the row length
-// handled by one instantiation (16: registers; 64: local memory, rare).
+// handled by one instantiation (16: registers; 64: local memory, rare).  TV is the stored
+// value type: double (FP64 form) or float (FP32 form).
+
+// FP64 row: Laplacian of every present layer and of the base, then Eq. (2).  Values of the
+// FP32 form are widened exactly, so the row is the FP64 step from the stored inputs.
+template <int MAXD, class TV>
+__device__ __forceinline__ void row_f64(const Params &P, int nl, const int32_t *ls, int32_t lv, int32_t o, TV xv,
+                                        const int32_t *nlay, const TV *nx, int32_t deg, double *out) {
+  const double Lv = P.lv[deg];
+  const double xvd = (double)xv;
+  const double xb = dsub(1.0, lv != 0 ? xvd : 0.0);
+  double x[KMAX], lap[KMAX];
+#pragma unroll 1
+  for (int q = 0; q < nl; ++q) {
+    const int32_t l = ls[q];
+    const double plat = (o != 0 && l == o) ? 1.0 : 0.0; // a plateau reads as the row's layer
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < MAXD; ++j) {
+      if (j < deg) {
+        const double psi = nlay[j] == l ? (double)nx[j] : (nlay[j] < 0 ? plat : 0.0);
+        // terms are >= 0 and acc starts at +0: skipping a zero term leaves acc bit-identical
+        if (val_pos(psi)) acc = dadd(acc, dmul(Lv, psi));
+      }
+    }
+    x[q] = (lv == l) ? xvd : 0.0;
+    acc = dadd(acc, dmul(-P.s, x[q]));
+    lap[q] = acc;
+  }
+  double accb = 0.0;
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j)
+    if (j < deg) {
+      if (nlay[j] == 0) accb = dadd(accb, Lv);                                         // Lv * 1.0
+      else if (val_lt1(nx[j])) accb = dadd(accb, dmul(Lv, dsub(1.0, (double)nx[j]))); // zero terms skipped
+    }
+  accb = dadd(accb, dmul(-P.s, xb));
+  if (!vertex_update(P, nl, x, lap, xb, accb, out)) {
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q)
+      if (q < nl) out[q] = x[q];
+  }
+}
+
+// FP32 row of the common case (one layer l and the base, Eq. (2) with n = 2).  Returns false
+// when a decision of the step lies within the recheck margin (the row is then redone in FP64).
 template <int MAXD>
-__device__ __forceinline__ void update_row(const Dev &d, const Params &P, int32_t i, int32_t p, int32_t v, int32_t b,
+__device__ __forceinline__ bool row_f32(const Params &P, int32_t l, int32_t lv, int32_t o, float xv,
+                                        const int32_t *nlay, const float *nx, int32_t deg, double &out) {
+  const float Lv = P.f_lv[deg];
+  const float plat = (o != 0 && l == o) ? 1.f : 0.f;
+  float acc = 0.f, accb = 0.f;
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j)
+    if (j < deg) {
+      const float psi = nlay[j] == l ? nx[j] : (nlay[j] < 0 ? plat : 0.f);
+      acc = fmaf(Lv, psi, acc);
+      accb = fmaf(Lv, nlay[j] == 0 ? 1.f : 1.f - nx[j], accb);
+    }
+  const float x = (lv == l) ? xv : 0.f;
+  const float xb = 1.f - (lv != 0 ? xv : 0.f);
+  const float lap = fmaf(-P.f_s, x, acc);
+  const float lapb = fmaf(-P.f_s, xb, accb);
+  float y;
+  if (!vertex_update_f32(P, x, lap, xb, lapb, y)) return false;
+  out = (double)y;
+  return true;
+}
+
+template <int MAXD, class TV>
+__device__ __forceinline__ bool update_row(const Dev &d, const Params &P, int32_t i, int32_t p, int32_t v, int32_t b,
                                            int32_t deg) {
+  const TV *__restrict__ ph = ph_arr<TV>(d);
   // nlay[j]: layer of neighbour j, 0 for the base only, -1 for a frozen plateau
   int32_t nlay[MAXD];
-  double nx[MAXD];
+  TV nx[MAXD];
   {
     int32_t nu[MAXD];
 #pragma unroll
@@ -36,11 +105,11 @@ __device__ __forceinline__ void update_row(const Dev &d, const Params &P, int32_
 #pragma unroll
     for (int j = 0; j < MAXD; ++j) {
       nlay[j] = (j < deg) ? d.lay[nu[j]] : 0;
-      nx[j] = (j < deg) ? d.phi[nu[j]] : 0.0;
+      nx[j] = (j < deg) ? ph[nu[j]] : (TV)0;
     }
   }
   const int32_t lv = d.lay[v];
-  const double xv = d.phi[v];
+  const TV xv = ph[v];
 #pragma unroll
   for (int j = 0; j < MAXD; ++j)
     if (j < deg && nlay[j] != 0 && frozen_state(d.lstate[nlay[j]])) nlay[j] = -1;
@@ -50,7 +119,7 @@ __device__ __forceinline__ void update_row(const Dev &d, const Params &P, int32_
   int32_t ls[KMAX];
   int nl = 0;
   bool hb = false, ovf = false;
-  auto see = [&](int32_t lu, double xu, int32_t su) {
+  auto see = [&](int32_t lu, TV xu, int32_t su) {
     if (lu == 0) { hb = true; return; }
     if (frozen_state(su)) return; // a plateau reads as the row's own layer
     if (val_lt1(xu)) hb = true;
@@ -69,41 +138,23 @@ __device__ __forceinline__ void update_row(const Dev &d, const Params &P, int32_
   if (ovf) {
     atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_ESLOTS);
     d.onl[i] = -1;
-    return;
+    return false;
   }
-  if (!hb || nl == 0) { d.onl[i] = -1; return; }
-  const double Lv = P.lv[deg];
-  const double xb = dsub(1.0, lv != 0 ? xv : 0.0);
-  double x[KMAX], lap[KMAX], out[KMAX];
-#pragma unroll 1
-  for (int q = 0; q < nl; ++q) {
-    const int32_t l = ls[q];
-    const double plat = (o != 0 && l == o) ? 1.0 : 0.0; // a plateau reads as the row's layer
-    double acc = 0.0;
+  if (!hb || nl == 0) { d.onl[i] = -1; return false; }
+  double out[KMAX];
+  bool redo = false;
+  if constexpr (sizeof(TV) == sizeof(float)) {
+    // FP32 form: one layer in FP32; several layers (a collision: merge arithmetic follows)
+    // and rows near a decision are computed in FP64 and rounded keeping their side
+    if (nl != 1 || !row_f32<MAXD>(P, ls[0], lv, o, xv, nlay, nx, deg, out[0])) {
+      row_f64<MAXD, TV>(P, nl, ls, lv, o, xv, nlay, nx, deg, out);
 #pragma unroll
-    for (int j = 0; j < MAXD; ++j) {
-      if (j < deg) {
-        const double psi = nlay[j] == l ? nx[j] : (nlay[j] < 0 ? plat : 0.0);
-        // terms are >= 0 and acc starts at +0: skipping a zero term leaves acc bit-identical
-        if (val_pos(psi)) acc = dadd(acc, dmul(Lv, psi));
-      }
+      for (int q = 0; q < KMAX; ++q)
+        if (q < nl) out[q] = (double)f32_keep_side(out[q], P.theta);
+      redo = true;
     }
-    x[q] = (lv == l) ? xv : 0.0;
-    acc = dadd(acc, dmul(-P.s, x[q]));
-    lap[q] = acc;
-  }
-  double accb = 0.0;
-#pragma unroll
-  for (int j = 0; j < MAXD; ++j)
-    if (j < deg) {
-      if (nlay[j] == 0) accb = dadd(accb, Lv);                               // Lv * 1.0
-      else if (val_lt1(nx[j])) accb = dadd(accb, dmul(Lv, dsub(1.0, nx[j]))); // zero terms skipped
-    }
-  accb = dadd(accb, dmul(-P.s, xb));
-  if (!vertex_update(P, nl, x, lap, xb, accb, out)) {
-#pragma unroll
-    for (int q = 0; q < KMAX; ++q)
-      if (q < nl) out[q] = x[q];
+  } else {
+    row_f64<MAXD, TV>(P, nl, ls, lv, o, xv, nlay, nx, deg, out);
   }
   int cnt = 0;
 #pragma unroll
@@ -114,18 +165,22 @@ __device__ __forceinline__ void update_row(const Dev &d, const Params &P, int32_
       ++cnt;
     }
   d.onl[i] = cnt;
+  return redo;
 }
 
-__device__ __noinline__ void update_row_wide(const Dev &d, const Params &P, int32_t i, int32_t p, int32_t v, int32_t b,
+template <class TV>
+__device__ __noinline__ bool update_row_wide(const Dev &d, const Params &P, int32_t i, int32_t p, int32_t v, int32_t b,
                                              int32_t deg) {
-  update_row<64>(d, P, i, p, v, b, deg);
+  return update_row<64, TV>(d, P, i, p, v, b, deg);
 }
 
-__global__ void __launch_bounds__(256) k_update(Dev d, Params P) {
+template <class TV>
+__device__ __forceinline__ void update_rows(const Dev &d, const Params &P) {
   const int32_t cur = d.ctl[CTL_T] & 1;
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
   const int32_t nF = d.nfront[cur];
+  uint32_t redo = 0;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
     const int32_t p = fp[i];
     if (d.pdone[p]) { d.onl[i] = -1; continue; }
@@ -134,10 +189,19 @@ __global__ void __launch_bounds__(256) k_update(Dev d, Params P) {
     const int32_t b = d.rp[v], e = d.rp[v + 1];
     if (!VCHK(d.err, e, d.nnz + 1, 102) || !VCHK(d.err, b, e + 1, 103)) { d.onl[i] = -1; continue; }
     const int32_t deg = e - b;
-    if (deg <= 16) update_row<16>(d, P, i, p, v, b, deg);
-    else if (deg <= 64) update_row_wide(d, P, i, p, v, b, deg);
+    if (deg <= 16) redo += update_row<16, TV>(d, P, i, p, v, b, deg);
+    else if (deg <= 64) redo += update_row_wide<TV>(d, P, i, p, v, b, deg);
     else { atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_EINVAL); d.onl[i] = -1; }
   }
+  if constexpr (sizeof(TV) == sizeof(float)) {
+    redo = __reduce_add_sync(0xffffffffu, redo);
+    if ((threadIdx.x & 31) == 0 && redo) atomicAdd(&d.nrecheck[0], (unsigned long long)redo);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_update(Dev d, Params P) {
+  if (d.phif) update_rows<float>(d, P);
+  else update_rows<double>(d, P);
 }
 
 // ------------------------------------------------------------------- apply
@@ -155,10 +219,10 @@ __global__ void k_apply(Dev d, Handles H) {
     if (c < 0) continue;
     if (c == 0) {
       d.lay[v] = 0;
-      d.phi[v] = 0.0;
+      ph_st(d, v, 0.0);
     } else {
       d.lay[v] = d.olay[(int64_t)i * KMAX];
-      d.phi[v] = d.ophi[(int64_t)i * KMAX];
+      ph_st(d, v, d.ophi[(int64_t)i * KMAX]);
       if (d.cover[v] < 0) d.cover[v] = t;
     }
     if (c >= 2) {
@@ -181,7 +245,7 @@ __global__ void k_apply(Dev d, Handles H) {
 __device__ __forceinline__ bool is_band(const Dev &d, int32_t v, int32_t &l) {
   l = d.lay[v];
   if (l == 0 || d.lstate[l] != L_ALIVE) return false;
-  return val_band(d.phi[v]);
+  return ph_band(d, v);
 }
 
 __global__ void k_band_hook(Dev d) {
@@ -199,7 +263,7 @@ __global__ void k_band_hook(Dev d) {
       // a neighbour joins v's band component iff it is a frontier row of this step (band
       // vertices are) holding the same live layer strictly between 0 and 1
       int32_t nu[16], nm[16], nl[16];
-      double nx[16];
+      bool nb[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) nu[j] = (j < deg) ? d.col[b + j] : v;
 #pragma unroll
@@ -207,11 +271,11 @@ __global__ void k_band_hook(Dev d) {
         const bool ok = j < deg && nu[j] < v;
         nm[j] = ok ? d.fmark[nu[j]] : -1;
         nl[j] = ok ? d.lay[nu[j]] : 0;
-        nx[j] = ok ? d.phi[nu[j]] : 0.0;
+        nb[j] = ok && ph_band(d, nu[j]);
       }
 #pragma unroll
       for (int j = 0; j < 16; ++j)
-        if (nm[j] == t && nl[j] == l && val_band(nx[j])) uf_unite(d.uf, nu[j], v);
+        if (nm[j] == t && nl[j] == l && nb[j]) uf_unite(d.uf, nu[j], v);
     } else {
       for (int32_t k = b; k < b + deg; ++k) {
         const int32_t u = d.col[k];
@@ -267,18 +331,16 @@ __device__ __forceinline__ bool in_frontier_t(const Dev &d, int32_t u, int32_t b
 #pragma unroll
     for (int j = 0; j < MAXD; ++j) {
       nlay[j] = (j < deg) ? d.lay[nu[j]] : 0;
-      const double x = (j < deg) ? d.phi[nu[j]] : 0.0;
-      if (val_lt1(x)) partial |= 1u << j;
+      if (j < deg && ph_lt1(d, nu[j])) partial |= 1u << j;
     }
   }
   const int32_t lu = d.lay[u];
-  const double xu = d.phi[u];
   bool hb = false, hl = false;
   if (lu == 0) hb = true;
   else {
     if (frozen_state(d.lstate[lu])) return false;
     hl = true;
-    if (val_lt1(xu)) hb = true;
+    if (ph_lt1(d, u)) hb = true;
   }
 #pragma unroll
   for (int j = 0; j < MAXD; ++j) {
@@ -415,7 +477,7 @@ __global__ void k_init(Dev d, int32_t *fv0, int32_t *fp0, int32_t *nF0) {
       const int32_t u = (k < d.rp[s]) ? s : d.col[k];
       if (!VCHK(d.err, u, d.V, 140)) continue;
       d.lay[u] = L1;
-      d.phi[u] = 1.0;
+      ph_st(d, u, 1.0);
       d.cover[u] = 0;
       const int32_t q = atomicAdd(nF0, 1);
       fv0[q] = u;
@@ -427,7 +489,7 @@ __global__ void k_init(Dev d, int32_t *fv0, int32_t *fp0, int32_t *nF0) {
 // A finished problem must have covered everything with value 1 and have no live layer.
 __global__ void k_final_vertices(Dev d, int32_t *pstall) {
   for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < d.V; v += gridDim.x * blockDim.x)
-    if (d.lay[v] == 0 || dsub(1.0, d.phi[v]) > 0.0) pstall[prob_of_vertex(d.voff, d.P, v)] = 1;
+    if (d.lay[v] == 0 || ph_lt1(d, v)) pstall[prob_of_vertex(d.voff, d.P, v)] = 1;
 }
 __global__ void k_final_layers(Dev d, int32_t *pstall) {
   for (int32_t p = blockIdx.x; p < d.P; p += gridDim.x)

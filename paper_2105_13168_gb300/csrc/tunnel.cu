@@ -50,6 +50,16 @@ __device__ __forceinline__ bool kept(const Dev &d, const TDev &T, int32_t q, int
   return true;
 }
 
+template <class TV> __device__ __forceinline__ const TV *tph_arr(const TDev &T);
+template <> __device__ __forceinline__ const double *tph_arr<double>(const TDev &T) { return T.phi; }
+template <> __device__ __forceinline__ const float *tph_arr<float>(const TDev &T) { return T.phif; }
+__device__ __forceinline__ double tph_ld(const TDev &T, int32_t i) { return T.phif ? (double)T.phif[i] : T.phi[i]; }
+// a row output (exactly representable in float in the FP32 form) into the pass state
+__device__ __forceinline__ void tph_st(const TDev &T, int32_t i, double x) {
+  if (T.phif) T.phif[i] = (float)x;
+  else T.phi[i] = x;
+}
+
 // per pass: flags, sources at 1, cut slots sorted, F_0 = sources
 __global__ void k_tinit(Dev d, TDev T, int32_t *fv0, int32_t *fq0, int32_t *nF0) {
   const int32_t q = blockIdx.x;
@@ -65,7 +75,7 @@ __global__ void k_tinit(Dev d, TDev T, int32_t *fv0, int32_t *fq0, int32_t *nF0)
     if (!VCHK(T.err, a - voff, nvp, 301) || !VCHK(T.err, b - voff, nvp, 302)) continue;
     T.flag[base + (a - voff)] = F_SRC;
     T.flag[base + (b - voff)] = F_TGT;
-    T.phi[base + (a - voff)] = 1.0;
+    tph_st(T, base + (a - voff), 1.0);
     T.T[base + (a - voff)] = 0;
     cut[2 * i] = slot_of(d.rp, d.col, a, b);
     cut[2 * i + 1] = slot_of(d.rp, d.col, b, a);
@@ -87,10 +97,11 @@ __global__ void k_tinit(Dev d, TDev T, int32_t *fv0, int32_t *fq0, int32_t *nF0)
 
 // Kept neighbours of a row of pass q, gathered before use: ids, then cover steps, flags and
 // values (MAXD bounds the row length of one instantiation).
-template <int MAXD>
+template <int MAXD, class TV>
 __device__ __forceinline__ int gather_kept(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
                                           int32_t voff, int8_t fl, int32_t v, int32_t b, int32_t deg, uint64_t &kp,
-                                          double *nx) {
+                                          TV *nx) {
+  const TV *__restrict__ ph = tph_arr<TV>(T);
   int32_t nu[MAXD];
   kp = 0;
 #pragma unroll
@@ -99,7 +110,7 @@ __device__ __forceinline__ int gather_kept(const Dev &d, const TDev &T, int32_t 
   for (int j = 0; j < MAXD; ++j) {
     const int32_t c = (j < deg) ? d.cover[nu[j]] : -1;
     const int8_t f = (j < deg) ? T.flag[base + (nu[j] - voff)] : (int8_t)0;
-    nx[j] = (j < deg) ? T.phi[base + (nu[j] - voff)] : 0.0;
+    nx[j] = (j < deg) ? ph[base + (nu[j] - voff)] : (TV)0;
     bool k = j < deg && c >= 0 && c <= step;
     if (k && (((fl & F_SRC) && (f & F_TGT)) || ((fl & F_TGT) && (f & F_SRC)))) k = !is_cut(T, q, b + j);
     if (k) kp |= 1ull << j;
@@ -107,53 +118,103 @@ __device__ __forceinline__ int gather_kept(const Dev &d, const TDev &T, int32_t 
   return __popcll(kp);
 }
 
-template <int MAXD>
-__device__ __forceinline__ void tupdate_row(const Dev &d, const TDev &T, const Params &P, int32_t i, int32_t q,
-                                            int32_t v) {
-  const int32_t p = T.pprob[q], base = T.pbase[q], voff = d.voff[p], step = T.pstep[q];
-  const int32_t idx = base + (v - voff);
-  if (!VCHK(T.err, idx, T.PV, 310)) { T.onew[i] = 0.0; return; }
-  const int8_t fl = T.flag[idx];
-  const int32_t b = d.rp[v], deg = d.rp[v + 1] - b;
-  uint64_t kp;
-  double nx[MAXD];
-  const int dh = gather_kept<MAXD>(d, T, q, step, base, voff, fl, v, b, deg, kp, nx);
+// FP64 pass row (Eq. (2) with n = 2: the pass layer and its base) from the stored inputs
+// (FP32 values are widened exactly).
+template <int MAXD, class TV>
+__device__ __forceinline__ double trow_f64(const Params &P, uint64_t kp, int dh, const TV *nx, TV xs) {
   const double Lv = dh > 0 ? P.lv[dh] : 0.0;
   const double diag = dh > 0 ? -P.s : 0.0;
-  const double x = T.phi[idx];
+  const double x = (double)xs;
   double acc = 0.0, accb = 0.0;
   // terms are >= 0 and the sums start at +0: zero terms are skipped (bit-identical)
 #pragma unroll
   for (int j = 0; j < MAXD; ++j)
-    if (((kp >> j) & 1ull) && val_pos(nx[j])) acc = dadd(acc, dmul(Lv, nx[j]));
+    if (((kp >> j) & 1ull) && val_pos(nx[j])) acc = dadd(acc, dmul(Lv, (double)nx[j]));
   acc = dadd(acc, dmul(diag, x));
 #pragma unroll
   for (int j = 0; j < MAXD; ++j)
-    if (((kp >> j) & 1ull) && val_lt1(nx[j])) accb = dadd(accb, dmul(Lv, dsub(1.0, nx[j])));
+    if (((kp >> j) & 1ull) && val_lt1(nx[j])) accb = dadd(accb, dmul(Lv, dsub(1.0, (double)nx[j])));
   const double xb = dsub(1.0, x);
   accb = dadd(accb, dmul(diag, xb));
   double out;
   if (!vertex_update(P, 1, &x, &acc, xb, accb, &out)) out = x;
+  return out;
+}
+
+// FP32 pass row; false when a decision lies within the recheck margin.
+template <int MAXD>
+__device__ __forceinline__ bool trow_f32(const Params &P, uint64_t kp, int dh, const float *nx, float x, double &out) {
+  if (dh == 0) return false;
+  const float Lv = P.f_lv[dh];
+  float acc = 0.f, accb = 0.f;
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j)
+    if ((kp >> j) & 1ull) {
+      acc = fmaf(Lv, nx[j], acc);
+      accb = fmaf(Lv, 1.f - nx[j], accb);
+    }
+  const float xb = 1.f - x;
+  float y;
+  if (!vertex_update_f32(P, x, fmaf(-P.f_s, x, acc), xb, fmaf(-P.f_s, xb, accb), y)) return false;
+  out = (double)y;
+  return true;
+}
+
+template <int MAXD, class TV>
+__device__ __forceinline__ bool tupdate_row(const Dev &d, const TDev &T, const Params &P, int32_t i, int32_t q,
+                                            int32_t v) {
+  const int32_t p = T.pprob[q], base = T.pbase[q], voff = d.voff[p], step = T.pstep[q];
+  const int32_t idx = base + (v - voff);
+  if (!VCHK(T.err, idx, T.PV, 310)) { T.onew[i] = 0.0; return false; }
+  const int8_t fl = T.flag[idx];
+  const int32_t b = d.rp[v], deg = d.rp[v + 1] - b;
+  uint64_t kp;
+  TV nx[MAXD];
+  const int dh = gather_kept<MAXD, TV>(d, T, q, step, base, voff, fl, v, b, deg, kp, nx);
+  const TV x = tph_arr<TV>(T)[idx];
+  double out;
+  bool redo = false;
+  if constexpr (sizeof(TV) == sizeof(float)) {
+    if (!trow_f32<MAXD>(P, kp, dh, nx, x, out)) {
+      out = (double)f32_keep_side(trow_f64<MAXD, TV>(P, kp, dh, nx, x), P.theta);
+      redo = true;
+    }
+  } else {
+    out = trow_f64<MAXD, TV>(P, kp, dh, nx, x);
+  }
   T.onew[i] = out;
+  return redo;
 }
 
-__device__ __noinline__ void tupdate_row_wide(const Dev &d, const TDev &T, const Params &P, int32_t i, int32_t q,
+template <class TV>
+__device__ __noinline__ bool tupdate_row_wide(const Dev &d, const TDev &T, const Params &P, int32_t i, int32_t q,
                                               int32_t v) {
-  tupdate_row<64>(d, T, P, i, q, v);
+  return tupdate_row<64, TV>(d, T, P, i, q, v);
 }
 
-__global__ void __launch_bounds__(256) k_tupdate(Dev d, TDev T, Params P) {
+template <class TV>
+__device__ __forceinline__ void tupdate_rows(const Dev &d, const TDev &T, const Params &P) {
   const int32_t cur = d.ctl[CTL_TAU] & 1;
   const int32_t *__restrict__ fv = T.fv[cur];
   const int32_t *__restrict__ fq = T.fq[cur];
   const int32_t nF = T.nf[cur];
+  uint32_t redo = 0;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
     const int32_t v = fv[i], q = fq[i];
     const int32_t deg = d.rp[v + 1] - d.rp[v];
-    if (deg <= 16) tupdate_row<16>(d, T, P, i, q, v);
-    else if (deg <= 64) tupdate_row_wide(d, T, P, i, q, v);
-    else T.onew[i] = T.phi[T.pbase[q] + (v - d.voff[T.pprob[q]])];
+    if (deg <= 16) redo += tupdate_row<16, TV>(d, T, P, i, q, v);
+    else if (deg <= 64) redo += tupdate_row_wide<TV>(d, T, P, i, q, v);
+    else T.onew[i] = tph_ld(T, T.pbase[q] + (v - d.voff[T.pprob[q]]));
   }
+  if constexpr (sizeof(TV) == sizeof(float)) {
+    redo = __reduce_add_sync(0xffffffffu, redo);
+    if ((threadIdx.x & 31) == 0 && redo) atomicAdd(&d.nrecheck[1], (unsigned long long)redo);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_tupdate(Dev d, TDev T, Params P) {
+  if (T.phif) tupdate_rows<float>(d, T, P);
+  else tupdate_rows<double>(d, T, P);
 }
 
 __global__ void k_tapply(Dev d, TDev T, double theta) {
@@ -167,7 +228,7 @@ __global__ void k_tapply(Dev d, TDev T, double theta) {
     const int32_t idx = T.pbase[q] + (v - d.voff[p]);
     if (!VCHK(T.err, idx, T.PV, 320)) continue;
     const double x = T.onew[i];
-    T.phi[idx] = x;
+    tph_st(T, idx, x);
     if (T.T[idx] < 0 && x >= theta) {
       T.T[idx] = tau;
       if (T.flag[idx] & F_TGT) atomicMin(&T.qbstar[q], v - d.voff[p]);
@@ -177,18 +238,18 @@ __global__ void k_tapply(Dev d, TDev T, double theta) {
 
 // u joins pass q's frontier iff it is in the domain, not a source, and its kept closed
 // neighbourhood holds both phases.
-template <int MAXD>
+template <int MAXD, class TV>
 __device__ __forceinline__ bool t_in_frontier_t(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
                                                 int32_t voff, int32_t u, int32_t b, int32_t deg) {
   const int32_t iu = base + (u - voff);
   const int8_t fu = T.flag[iu];
   if (fu & F_SRC) return false;
-  const double xu = T.phi[iu];
+  const TV xu = tph_arr<TV>(T)[iu];
   bool lay = val_pos(xu), bas = val_lt1(xu);
   if (lay && bas) return true;
   uint64_t kp;
-  double nx[MAXD];
-  gather_kept<MAXD>(d, T, q, step, base, voff, fu, u, b, deg, kp, nx);
+  TV nx[MAXD];
+  gather_kept<MAXD, TV>(d, T, q, step, base, voff, fu, u, b, deg, kp, nx);
 #pragma unroll
   for (int j = 0; j < MAXD; ++j)
     if ((kp >> j) & 1ull) {
@@ -197,16 +258,21 @@ __device__ __forceinline__ bool t_in_frontier_t(const Dev &d, const TDev &T, int
     }
   return lay && bas;
 }
+template <class TV>
 __device__ __noinline__ bool t_in_frontier_wide(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
                                                 int32_t voff, int32_t u, int32_t b, int32_t deg) {
-  return t_in_frontier_t<64>(d, T, q, step, base, voff, u, b, deg < 64 ? deg : 64);
+  return t_in_frontier_t<64, TV>(d, T, q, step, base, voff, u, b, deg < 64 ? deg : 64);
 }
 __device__ __forceinline__ bool t_in_frontier(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
                                               int32_t voff, int32_t u) {
   if (!in_dom(d, u, step)) return false;
   const int32_t b = d.rp[u], deg = d.rp[u + 1] - b;
-  if (deg <= 16) return t_in_frontier_t<16>(d, T, q, step, base, voff, u, b, deg);
-  return t_in_frontier_wide(d, T, q, step, base, voff, u, b, deg);
+  if (T.phif) {
+    if (deg <= 16) return t_in_frontier_t<16, float>(d, T, q, step, base, voff, u, b, deg);
+    return t_in_frontier_wide<float>(d, T, q, step, base, voff, u, b, deg);
+  }
+  if (deg <= 16) return t_in_frontier_t<16, double>(d, T, q, step, base, voff, u, b, deg);
+  return t_in_frontier_wide<double>(d, T, q, step, base, voff, u, b, deg);
 }
 
 // 16-lane groups per row, one lane per candidate of the row's kept closed neighbourhood.

@@ -35,7 +35,8 @@ struct TDev {
   const int32_t *cut;          // global CSR slots of the loop's half-edges, both directions
   const int32_t *heoff, *hen;  // [NP] the handle's crossing edges in the global pool
   int8_t *flag;        // [pass-vertex] bit0 source, bit1 target
-  double *phi;         // [pass-vertex]
+  double *phi;         // [pass-vertex] FP64 form
+  float *phif;         // [pass-vertex] FP32 form (non-null selects it; phi unused)
   int32_t *T;          // [pass-vertex] arrival step (-1 unreached)
   int32_t *stamp;      // [pass-vertex]
   int32_t *fv[2], *fq[2];  // frontier (vertex, pass)

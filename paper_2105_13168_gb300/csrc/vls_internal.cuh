@@ -39,6 +39,11 @@ struct Params {
   double mu, e, w, ah, dt, s, eps0, one_m_eps, theta;
   double lv[LV_MAX + 1];  // s / d: off-diagonal operator entry of a row with d kept neighbours
   double mun[KMAX + 2];   // mu / n for n phases meeting at a vertex
+  // FP32 form: the same constants rounded to float, and the recheck margin
+  double margin;
+  float f_e, f_w, f_ah, f_dt, f_s, f_eps0, f_one_m_eps, f_theta, f_margin;
+  float f_lv[LV_MAX + 1];
+  float f_mun[KMAX + 2];
 };
 
 // Global device state of one batch.  Passed by value to kernels.
@@ -64,7 +69,9 @@ struct Dev {
   int32_t *pev;      // [P][3] merges, splits, ends
   // state
   int32_t *lay;
-  double *phi;
+  double *phi;       // FP64 form: layer values
+  float *phif;       // FP32 form: layer values (non-null selects the FP32 form; phi unused)
+  unsigned long long *nrecheck; // [2] rows redone in FP64: initial pass, tunnel passes
   int32_t *cover;
   int32_t *stamp;    // candidate dedup stamp (step id)
   int32_t *fmark;    // step at which the vertex was last in the frontier
@@ -181,6 +188,45 @@ __device__ __forceinline__ bool frozen_state(int32_t st) { return st == L_DEAD |
 __device__ __forceinline__ bool val_pos(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool val_lt1(double x) { return __double_as_longlong(x) < 0x3FF0000000000000LL; }
 __device__ __forceinline__ bool val_band(double x) { return val_pos(x) && val_lt1(x); }
+__device__ __forceinline__ bool val_pos(float x) { return __float_as_int(x) > 0; }
+__device__ __forceinline__ bool val_lt1(float x) { return __float_as_int(x) < 0x3F800000; }
+__device__ __forceinline__ bool val_band(float x) { return val_pos(x) && val_lt1(x); }
+
+// ------------------------------------------------------------ stored values
+// The layer value of a vertex is stored as double (FP64 form) or float (FP32 form, d.phif
+// non-null).  Readers that only test a value use the bit tests above on the stored type.
+__device__ __forceinline__ double ph_ld(const Dev &d, int32_t v) { return d.phif ? (double)d.phif[v] : d.phi[v]; }
+__device__ __forceinline__ bool ph_lt1(const Dev &d, int32_t v) { return d.phif ? val_lt1(d.phif[v]) : val_lt1(d.phi[v]); }
+__device__ __forceinline__ bool ph_band(const Dev &d, int32_t v) {
+  return d.phif ? val_band(d.phif[v]) : val_band(d.phi[v]);
+}
+template <class TV> __device__ __forceinline__ const TV *ph_arr(const Dev &d);
+template <> __device__ __forceinline__ const double *ph_arr<double>(const Dev &d) { return d.phi; }
+template <> __device__ __forceinline__ const float *ph_arr<float>(const Dev &d) { return d.phif; }
+
+// FP32 storage of an FP64 value without moving it across any threshold that later steps test
+// on stored values: 0 < x, x < 1 and x >= theta keep their truth value (x in [0, 1]).  Only
+// one ulp separates a rounded value from x, so one step towards x's side suffices.
+__device__ __forceinline__ float f32_keep_side(double x, double theta) {
+  float f = __double2float_rn(x);
+  const double fd = (double)f;
+  int32_t bits = __float_as_int(f);
+  if (x > 0.0 && !(fd > 0.0)) bits = 1;                   // smallest positive float
+  else if (x < 1.0 && !(fd < 1.0)) bits = 0x3F7FFFFF;     // largest float below 1
+  else if (x < theta && fd >= theta) bits -= 1;
+  else if (x >= theta && fd < theta) bits += 1;
+  return __int_as_float(bits);
+}
+// a value of a row output (exactly representable in float in the FP32 form) into the state
+__device__ __forceinline__ void ph_st(const Dev &d, int32_t v, double x) {
+  if (d.phif) d.phif[v] = (float)x;
+  else d.phi[v] = x;
+}
+// any FP64 value into the state (FP32 form: rounded keeping its side of every threshold)
+__device__ __forceinline__ void ph_st_round(const Dev &d, const Params &P, int32_t v, double x) {
+  if (d.phif) d.phif[v] = f32_keep_side(x, P.theta);
+  else d.phi[v] = x;
+}
 
 // One explicit Euler step of Eq. (2) at one vertex (base present; nl non-base layers in
 // ascending id order with own values x[] and Laplacians lap[]; base value xb, Laplacian
@@ -226,6 +272,34 @@ __device__ __forceinline__ bool vertex_update(const Params &P, int nl, const dou
   for (int i = 0; i < KMAX; ++i)
     if (i < nl) out[i] = ddiv(y[i], S);
   return true;
+}
+
+// FP32 form of vertex_update for one layer and the base (n = 2), the common case.  Returns
+// false when any decision of the step lies within the recheck margin: a clamped value near
+// eps0 or 1 - eps0 (snap), a new value near theta (isoline, arrival), or a vanishing column
+// sum; the caller then redoes the row in FP64.
+__device__ __forceinline__ bool vertex_update_f32(const Params &P, float x, float lap, float xb, float lapb,
+                                                  float &out) {
+  const float t1 = P.f_w * (x - xb);
+  const float t2 = P.f_ah * (lap - lapb);
+  const float t3 = P.f_e * sqrtf(x * xb);
+  const float r = P.f_mun[2] * (t1 + t2 + t3);
+  float y = x + P.f_dt * r;
+  float yb = xb - P.f_dt * r;
+  y = fminf(fmaxf(y, 0.f), 1.f);
+  yb = fminf(fmaxf(yb, 0.f), 1.f);
+  const float m = P.f_margin;
+  bool near = fabsf(y - P.f_eps0) < m || fabsf(y - P.f_one_m_eps) < m || fabsf(yb - P.f_eps0) < m ||
+              fabsf(yb - P.f_one_m_eps) < m;
+  if (y < P.f_eps0) y = 0.f;
+  if (y > P.f_one_m_eps) y = 1.f;
+  if (yb < P.f_eps0) yb = 0.f;
+  if (yb > P.f_one_m_eps) yb = 1.f;
+  const float S = y + yb;
+  if (S == 0.f) return false;
+  out = y / S;
+  near |= fabsf(out - P.f_theta) < m;
+  return !near;
 }
 
 // ------------------------------------------------------------ union-find

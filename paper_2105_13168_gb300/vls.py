@@ -27,7 +27,7 @@ class vls_options(ctypes.Structure):
                 ("max_steps", ctypes.c_int32), ("max_pass_steps", ctypes.c_int32), ("tunnels", ctypes.c_int32),
                 ("keep_state", ctypes.c_int32), ("record_steps", ctypes.c_int32), ("sync_interval", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("profile", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("host_loop", ctypes.c_int32)]
 
 
 class vls_mesh(ctypes.Structure):
@@ -42,7 +42,7 @@ class vls_stats(ctypes.Structure):
                 ("ms_initial", ctypes.c_double), ("ms_tunnel", ctypes.c_double), ("ms_download", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("ms_update", ctypes.c_double), ("ms_pass_update", ctypes.c_double),
                 ("n_update", ctypes.c_int64), ("n_pass_update", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64),
-                ("d2h_bytes", ctypes.c_int64)]
+                ("d2h_bytes", ctypes.c_int64), ("rechecks", ctypes.c_int64), ("pass_rechecks", ctypes.c_int64)]
 
 
 EXPORTS = ["vls_default_options", "vls_constants", "vls_create", "vls_destroy", "vls_detect", "vls_detect_batch",
@@ -111,10 +111,18 @@ def load(path: str = LIB_PATH):
 
 
 # ----------------------------------------------------------------- C-named wrappers
+VLS_FP64, VLS_FP32_RECHECK = 0, 1
+PRECISION = {"fp64": VLS_FP64, "fp32": VLS_FP32_RECHECK}
+
+
 def vls_default_options(**overrides) -> vls_options:
+    """Defaults of the library with fields overridden by keyword; precision may be given as
+    "fp64" / "fp32" (VLS_FP32_RECHECK) or as the enum value."""
     o = vls_options()
     load().vls_default_options(ctypes.byref(o))
     for k, v in overrides.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
         setattr(o, k, v)
     return o
 

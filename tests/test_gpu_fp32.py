@@ -1,0 +1,178 @@
+"""GPU parity of the FP32 form (values stored and stepped in FP32; rows that decide within the
+recheck margin of a threshold, or where several layers meet, redone in FP64) against the FP64
+CPU oracle on the same seeded inputs.
+
+The recheck removes the rounding of the step being taken, not the drift of the FP32 inputs
+(about 1e-7, at most about 6e-7 measured).  A threshold decision whose FP64 value lies closer
+to its threshold than that drift can still go the other way.  In practice this is a leading-edge
+vertex crossing eps0 one step early or late: its cover step and the band size of that step
+differ, and the next steps heal it.  The bar is therefore:
+  - exact: status, genus, every event and the layer table (Reeb graph topology), handle loops
+    (crossing edges and vertex sequences), tunnel loops, final layers;
+  - reported, and bounded here: steps whose band records differ (< 2 % of steps) and vertices
+    whose cover step differs (< 0.1 %);
+  - values: |phi_fp32 - phi_oracle| <= 2e-6 while no decision has differed (records equal up
+    to the compared step); loop points within 1e-4 of the coordinate scale; Reeb positions
+    within 1e-4, or 1e-2 when a step's band differs by a vertex (a position is a band mean).
+"""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 2e-6
+GEOM_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def vls():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_13168_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_2105_13168_gb300 as v
+
+    v.load()
+    return v
+
+
+def close(a, b, rel, what):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    assert a.shape == b.shape, (what, a.shape, b.shape)
+    if a.size == 0:
+        return 0.0
+    scale = max(1.0, float(np.abs(b).max()))
+    err = float(np.abs(a - b).max())
+    assert err <= rel * scale, f"{what}: max abs err {err:.3e} > {rel:.1e} * {scale:.3e}"
+    return err
+
+
+def assert_fp32_parity(g, o):
+    """Exact integer results, bounded record / cover differences, values within FP32_TOL while
+    no decision differed.  Returns (max value error or None, differing record steps, differing
+    cover steps)."""
+    assert g.status == o.status, (g.status_name, o.status_name)
+    assert g.genus == o.genus
+    assert g.events() == o.events()
+    assert np.array_equal(g.layers, o.layers)
+    assert len(g.records) == len(o.records), (len(g.records), len(o.records))
+    rec_bad = int((g.records != o.records).any(axis=1).sum())
+    # a node position is the mean of an event step's band: one vertex more or less in that band
+    # (a differing record) moves it by about the band's extent over its size
+    close(g.node_pos, o.node_pos, GEOM_TOL if rec_bad == 0 else 1e-2, "reeb node positions")
+    assert len(g.handles) == len(o.handles)
+    for i, (hg, ho) in enumerate(zip(g.handles, o.handles)):
+        assert (hg.step, hg.layer, hg.node) == (ho.step, ho.layer, ho.node), f"handle {i}"
+        assert np.array_equal(hg.edges, ho.edges), f"handle {i} crossing edges differ"
+        assert np.array_equal(hg.verts, ho.verts), f"handle {i} vertices differ"
+        close(hg.points, ho.points, GEOM_TOL, f"handle {i} points")
+        assert abs(hg.length - ho.length) <= GEOM_TOL * max(1.0, ho.length) * 10
+    assert len(g.tunnels) == len(o.tunnels)
+    for i, (tg, to) in enumerate(zip(g.tunnels, o.tunnels)):
+        assert (tg.status, tg.stop_step, tg.bstar) == (to.status, to.stop_step, to.bstar), f"tunnel {i}"
+        assert np.array_equal(tg.verts, to.verts), f"tunnel {i} differs"
+    assert np.array_equal(g.layer, o.layer)
+    cov_bad = int((g.cover != o.cover).sum())
+    assert rec_bad <= 0.02 * max(1, len(o.records)), f"{rec_bad} of {len(o.records)} step records differ"
+    assert cov_bad <= 1e-3 * g.cover.size, f"{cov_bad} cover steps differ"
+    err = None
+    if rec_bad == 0:
+        err = float(np.abs(g.phi - o.phi).max()) if g.phi.size else 0.0
+        assert err <= FP32_TOL, f"phi max abs err {err:.3e} > {FP32_TOL:.1e}"
+    return err, rec_bad, cov_bad
+
+
+def run_pair(vls, problems, gpu_kw=None, **kw):
+    gpu = vls.detect(problems, keep_state=1, record_steps=1, precision="fp32", **(gpu_kw or {}), **kw)
+    orc = [oracle.detect(m, s, record_steps=1, **kw) for m, seeds in problems for s in seeds]
+    return gpu, orc
+
+
+def test_torus_fp32_parity(vls):
+    m = meshgen.torus(64, 32, 2.0, 0.7)
+    s = meshgen.seed_vertex(0, m.nv)
+    (g,), (o,) = run_pair(vls, [(m, [s])])
+    assert o.status == 0
+    err, _, _ = assert_fp32_parity(g, o)
+    assert g.stats["rechecks"] > 0
+    assert g.stats["rechecks"] < g.stats["row_updates"]
+    print(f"torus fp32: max |phi - oracle| = {err}, rechecks {g.stats['rechecks']} of "
+          f"{g.stats['row_updates']} rows, pass rechecks {g.stats['pass_rechecks']}")
+
+
+@pytest.mark.parametrize("steps", [1, 7, 60, 109, 178])
+def test_torus_fp32_state_each_phase(vls, steps):
+    m = meshgen.torus(64, 32, 2.0, 0.7)
+    s = meshgen.seed_vertex(0, m.nv)
+    (g,), (o,) = run_pair(vls, [(m, [s])], max_steps=steps, tunnels=0)
+    assert_fp32_parity(g, o)
+
+
+@pytest.mark.parametrize("name", ["chain2", "chain3", "capsules", "sphere", "torus_small"])
+def test_shapes_fp32_parity(vls, name):
+    m = {"chain2": lambda: meshgen.tube_chain(2, 64), "chain3": lambda: meshgen.tube_chain(3, 80),
+         "capsules": lambda: meshgen.capsules(5, 60), "sphere": lambda: meshgen.sphere(28),
+         "torus_small": lambda: meshgen.torus(24, 12)}[name]()
+    seeds = [meshgen.seed_vertex(sd, m.nv) for sd in range(2)]
+    gpu, orc = run_pair(vls, [(m, seeds)])
+    for g, o in zip(gpu, orc):
+        assert_fp32_parity(g, o)
+
+
+def test_tube_chain_small_fp32_batch(vls):
+    """The tube-chain workload at grid scale 0.35 (8 tori, ~63k faces), 4 seeds in one batch."""
+    probs = meshgen.workload(2, 0.35)
+    gpu, orc = run_pair(vls, probs)
+    out = [assert_fp32_parity(g, o) for g, o in zip(gpu, orc)]
+    rows = sum(g.stats["row_updates"] for g in gpu)
+    print(f"tube chain 0.35 fp32: record steps differing {[r for _, r, _ in out]}, cover steps differing "
+          f"{[c for _, _, c in out]}, rechecks {gpu[0].stats['rechecks']} of {rows} rows")
+
+
+@pytest.mark.parametrize("steps", [100, 300])
+def test_tube_chain_small_fp32_values_mid_run(vls, steps):
+    """Values mid-run (front in flight) within the FP32 tolerance of the FP64 oracle."""
+    m, seeds = meshgen.workload(2, 0.35)[0]
+    gpu, orc = run_pair(vls, [(m, seeds)], max_steps=steps, tunnels=0)
+    for g, o in zip(gpu, orc):
+        err, rec_bad, _ = assert_fp32_parity(g, o)
+        if rec_bad == 0:
+            assert err <= FP32_TOL
+
+
+def test_fp32_equals_fp64_form_on_integer_results(vls):
+    """Both GPU forms agree on events, loops and final layers of a mixed batch (records and cover
+    steps within the bounds above)."""
+    meshes = [meshgen.torus(32, 16), meshgen.tube_chain(2, 56), meshgen.capsules(4, 48)]
+    probs = [(m, [meshgen.seed_vertex(5 * i + k, m.nv) for k in range(2)]) for i, m in enumerate(meshes)]
+    a = vls.detect(probs, keep_state=1, record_steps=1, precision="fp32")
+    b = vls.detect(probs, keep_state=1, record_steps=1, precision="fp64")
+    for ga, gb in zip(a, b):
+        assert ga.status == gb.status and ga.events() == gb.events()
+        assert len(ga.records) == len(gb.records)
+        assert (ga.records != gb.records).any(axis=1).sum() <= 0.02 * len(gb.records)
+        assert np.array_equal(ga.layer, gb.layer) and (ga.cover != gb.cover).sum() <= 1e-3 * gb.cover.size
+        assert [h.verts.tolist() for h in ga.handles] == [h.verts.tolist() for h in gb.handles]
+        assert [t.verts.tolist() for t in ga.tunnels] == [t.verts.tolist() for t in gb.tunnels]
+        assert gb.stats["rechecks"] == 0 and gb.stats["pass_rechecks"] == 0
+
+
+def test_fp32_margin_option(vls):
+    """A wide margin sends every row through the FP64 recheck and keeps parity; a bad margin is
+    refused at context creation."""
+    m = meshgen.torus(24, 12)
+    s = meshgen.seed_vertex(0, m.nv)
+    (g,), (o,) = run_pair(vls, [(m, [s])], gpu_kw={"recheck_margin": 0.2})
+    assert_fp32_parity(g, o)
+    assert g.stats["rechecks"] >= 0.5 * g.stats["row_updates"]
+    for bad in (0.0, -1.0, 0.5):
+        with pytest.raises(RuntimeError):
+            vls.vls_create(vls.vls_default_options(precision="fp32", recheck_margin=bad))
+    with pytest.raises(RuntimeError):
+        vls.vls_create(vls.vls_default_options(precision=7))
