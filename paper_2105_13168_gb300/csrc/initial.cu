@@ -176,14 +176,14 @@ __device__ __noinline__ bool update_row_wide(const Dev &d, const Params &P, int3
 
 template <class TV>
 __device__ __forceinline__ void update_rows(const Dev &d, const Params &P) {
-  const int32_t cur = d.ctl[CTL_T] & 1;
+  const int32_t cur = __ldcg(d.ctl + CTL_T) & 1;
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
-  const int32_t nF = d.nfront[cur];
+  const int32_t nF = __ldcg(d.nfront + cur);
   uint32_t redo = 0;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
+  FOR_ROWS(i, nF) {
     const int32_t p = fp[i];
-    if (d.pdone[p]) { d.onl[i] = -1; continue; }
+    if (__ldcg(d.pdone + p)) { d.onl[i] = -1; continue; }
     const int32_t v = fv[i];
     if (!VCHK(d.err, v, d.V, 101)) { d.onl[i] = -1; continue; }
     const int32_t b = d.rp[v], e = d.rp[v + 1];
@@ -199,20 +199,21 @@ __device__ __forceinline__ void update_rows(const Dev &d, const Params &P) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_update(Dev d, Params P) {
+__device__ __forceinline__ void update_phase(const Dev &d, const Params &P) {
   if (d.phif) update_rows<float>(d, P);
   else update_rows<double>(d, P);
 }
+__global__ void __launch_bounds__(256) k_update(Dev d, Params P) { update_phase(d, P); }
 
 // ------------------------------------------------------------------- apply
 // Also starts the band labelling: every row is its own union-find root (only band rows are
-// ever united).  The last block decides whether the merge phase runs this step.
-__global__ void k_apply(Dev d, Handles H) {
-  const int32_t t = d.ctl[CTL_T], cur = t & 1;
+// ever united), and flags the step for the merge phase when a row holds several layers.
+__device__ __forceinline__ void apply_phase(const Dev &d) {
+  const int32_t t = __ldcg(d.ctl + CTL_T), cur = t & 1;
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
-  const int32_t nF = d.nfront[cur];
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
+  const int32_t nF = __ldcg(d.nfront + cur);
+  FOR_ROWS(i, nF) {
     const int32_t v = fv[i];
     d.uf[v] = v;
     const int32_t c = d.onl[i];
@@ -233,6 +234,10 @@ __global__ void k_apply(Dev d, Handles H) {
       d.ctl[CTL_MERGE] = 1;
     }
   }
+}
+// The last block decides whether the merge phase runs this step.
+__global__ void k_apply(Dev d, Handles H) {
+  apply_phase(d);
   if (last_block_done(d.ctl + CTL_DONE_APPLY)) {
     const int32_t m = __ldcg(d.ctl + CTL_MERGE);
     if (H.use) cudaGraphSetConditional(H.merge, m ? 1u : 0u);
@@ -248,13 +253,13 @@ __device__ __forceinline__ bool is_band(const Dev &d, int32_t v, int32_t &l) {
   return ph_band(d, v);
 }
 
-__global__ void k_band_hook(Dev d) {
-  const int32_t t = d.ctl[CTL_T], cur = t & 1;
+__device__ __forceinline__ void hook_phase(const Dev &d) {
+  const int32_t t = __ldcg(d.ctl + CTL_T), cur = t & 1;
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
-  const int32_t nF = d.nfront[cur];
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
-    if (d.pdone[fp[i]]) continue;
+  const int32_t nF = __ldcg(d.nfront + cur);
+  FOR_ROWS(i, nF) {
+    if (__ldcg(d.pdone + fp[i])) continue;
     const int32_t v = fv[i];
     int32_t l;
     if (!is_band(d, v, l)) continue;
@@ -287,17 +292,18 @@ __global__ void k_band_hook(Dev d) {
     }
   }
 }
+__global__ void k_band_hook(Dev d) { hook_phase(d); }
 
 // Component roots per layer.  A layer reaching two roots, or a problem with a live layer
 // that has no root (no band left), sends the step through the split phase.
-__global__ void k_band_count(Dev d, Handles H) {
-  const int32_t cur = d.ctl[CTL_T] & 1;
+__device__ __forceinline__ void count_phase(const Dev &d) {
+  const int32_t cur = __ldcg(d.ctl + CTL_T) & 1;
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
-  const int32_t nF = d.nfront[cur];
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
+  const int32_t nF = __ldcg(d.nfront + cur);
+  FOR_ROWS(i, nF) {
     const int32_t p = fp[i];
-    if (d.pdone[p]) continue;
+    if (__ldcg(d.pdone + p)) continue;
     const int32_t v = fv[i];
     int32_t l;
     if (!is_band(d, v, l)) continue;
@@ -307,6 +313,9 @@ __global__ void k_band_count(Dev d, Handles H) {
       else if (old == 1) d.ctl[CTL_SPLIT] = 1;
     }
   }
+}
+__global__ void k_band_count(Dev d, Handles H) {
+  count_phase(d);
   if (last_block_done(d.ctl + CTL_DONE_COUNT)) {
     int32_t s = __ldcg(d.ctl + CTL_SPLIT);
     for (int32_t p = 0; p < d.P && !s; ++p)
@@ -318,70 +327,49 @@ __global__ void k_band_count(Dev d, Handles H) {
 }
 
 // ------------------------------------------------------------------- next frontier
-// u joins the frontier iff it is not frozen and its closed neighbourhood holds the base and a
-// live layer.  Neighbour ids, then their states, are loaded before any test.
-template <int MAXD>
-__device__ __forceinline__ bool in_frontier_t(const Dev &d, int32_t u, int32_t b, int32_t deg) {
-  int32_t nlay[MAXD];
-  uint32_t partial = 0; // bit j: neighbour j holds a layer with value < 1 (base present if live)
-  {
-    int32_t nu[MAXD];
-#pragma unroll
-    for (int j = 0; j < MAXD; ++j) nu[j] = (j < deg) ? d.col[b + j] : u;
-#pragma unroll
-    for (int j = 0; j < MAXD; ++j) {
-      nlay[j] = (j < deg) ? d.lay[nu[j]] : 0;
-      if (j < deg && ph_lt1(d, nu[j])) partial |= 1u << j;
-    }
-  }
-  const int32_t lu = d.lay[u];
-  bool hb = false, hl = false;
-  if (lu == 0) hb = true;
-  else {
-    if (frozen_state(d.lstate[lu])) return false;
-    hl = true;
-    if (ph_lt1(d, u)) hb = true;
-  }
-#pragma unroll
-  for (int j = 0; j < MAXD; ++j) {
-    if (j < deg) {
-      if (nlay[j] == 0) { hb = true; continue; }
-      if (hb && hl) continue;
-      if (frozen_state(d.lstate[nlay[j]])) continue;
-      hl = true;
-      if ((partial >> j) & 1u) hb = true;
-    }
-  }
-  return hb && hl;
-}
-__device__ __noinline__ bool in_frontier_wide(const Dev &d, int32_t u, int32_t b, int32_t deg) {
-  return in_frontier_t<64>(d, u, b, deg < 64 ? deg : 64);
-}
-__device__ __forceinline__ bool in_frontier(const Dev &d, int32_t u) {
-  const int32_t b = d.rp[u], deg = d.rp[u + 1] - b;
-  if (deg <= 16) return in_frontier_t<16>(d, u, b, deg);
-  return in_frontier_wide(d, u, b, deg);
+// F_{t+1} = the vertices, not frozen, whose closed neighbourhood holds the base and a live
+// layer (only those can change: all rates of Eq. (2) vanish elsewhere).  gives(w) is what w
+// contributes to such a test: bit 0 the base (no layer, or a live layer below 1), bit 1 a
+// live layer; a frozen plateau contributes nothing.  A vertex u qualifies iff gives(u) = 3 or
+// some neighbour w has gives(u) | gives(w) = 3, and every such pair has an endpoint in F_t:
+// a pair with neither endpoint in F_t kept its values through step t, so it qualified at the
+// end of step t - 1 already and put both endpoints into F_t (events only take contributions
+// away: a split freezes a plateau, an extinction ends a layer, a merge relabels live layers).
+// So F_{t+1} is found from the pairs (v, u), v in F_t, u a neighbour of v: O(degree) per row.
+__device__ __forceinline__ uint32_t gives(const Dev &d, int32_t w) {
+  const int32_t l = d.lay[w];
+  const bool lt1 = ph_lt1(d, w);
+  if (l == 0) return 1u;
+  if (frozen_state(d.lstate[l])) return 0u;
+  return lt1 ? 3u : 2u;
 }
 
-// F_t -> F_{t+1}: a group of 16 lanes per row, lane j takes candidate j of the row's closed
-// neighbourhood (the row itself, then its neighbours; rows longer than 15 loop).  Also clears
-// the per-layer root counts of this step (each band root resets its layer's counter) and
+// F_t -> F_{t+1}: a group of 16 lanes per row, lane j takes the row's neighbour j (rows longer
+// than 16 loop); the row itself joins when it qualifies on its own or through any pair.  Also
+// clears the per-layer root counts of this step (each band root resets its layer's counter) and
 // accumulates the step record.
-__global__ void __launch_bounds__(256) k_frontier(Dev d) {
-  const int32_t t = d.ctl[CTL_T], cur = t & 1, nxt = cur ^ 1, tnext = t + 1;
+__device__ __forceinline__ void frontier_phase(const Dev &d) {
+  const int32_t t = __ldcg(d.ctl + CTL_T), cur = t & 1, nxt = cur ^ 1, tnext = t + 1;
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
-  const int32_t nF = d.nfront[cur];
+  const int32_t nF = __ldcg(d.nfront + cur);
   int32_t *__restrict__ nv_out = d.front[nxt];
   int32_t *__restrict__ np_out = d.front[nxt] + d.V;
   int32_t *nN_ptr = d.nfront + nxt;
   int32_t *pcount_next = d.pfront + (size_t)nxt * d.P;
   const int32_t lane = threadIdx.x & 15;
-  const int32_t group = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
-  const int32_t ngroup = (gridDim.x * blockDim.x) >> 4;
-  for (int32_t i = group; i < nF; i += ngroup) {
+  const unsigned half = 0xFFFFu << (threadIdx.x & 16);
+  auto add = [&](int32_t u, int32_t p) {
+    if (atomicExch(&d.stamp[u], tnext) == tnext) return;
+    const int32_t s = warp_append(nN_ptr, pcount_next, p);
+    if (!VCHK(d.err, s, d.V, 121)) return;
+    nv_out[s] = u;
+    np_out[s] = p;
+    d.fmark[u] = tnext;
+  };
+  FOR_ROWS16(i, nF) {
     const int32_t p = fp[i];
-    if (d.pdone[p]) continue;
+    if (__ldcg(d.pdone + p)) continue;
     const int32_t v = fv[i];
     if (lane == 0) {
       int32_t l;
@@ -394,27 +382,31 @@ __global__ void __launch_bounds__(256) k_frontier(Dev d) {
         }
       }
     }
+    const uint32_t gv = gives(d, v);
     const int32_t b = d.rp[v], e = d.rp[v + 1];
-    for (int32_t k = b - 1 + lane; k < e; k += 16) {
-      const int32_t u = (k < b) ? v : d.col[k];
+    bool join = gv == 3u;
+    for (int32_t k0 = b; k0 < e; k0 += 16) {
+      const int32_t k = k0 + lane;
+      if (k >= e) continue;
+      const int32_t u = d.col[k];
       if (!VCHK(d.err, u, d.V, 120)) continue;
-      if (atomicExch(&d.stamp[u], tnext) == tnext) continue;
-      if (!in_frontier(d, u)) continue;
-      const int32_t s = warp_append(nN_ptr, pcount_next, p);
-      if (!VCHK(d.err, s, d.V, 121)) continue;
-      nv_out[s] = u;
-      np_out[s] = p;
-      d.fmark[u] = tnext;
+      const uint32_t gu = gives(d, u);
+      if ((gv | gu) != 3u) continue;
+      join = true;
+      if (gu != 0u) add(u, p);
     }
+    join = __any_sync(half, join) && gv != 0u;
+    if (lane == 0 && join) add(v, p);
   }
 }
+__global__ void __launch_bounds__(256) k_frontier(Dev d) { frontier_phase(d); }
 
 // ------------------------------------------------------------------- epilogue
 // One block: per-problem bookkeeping, then the step counter advances; the WHILE node stops
 // when no problem is running (or at the hard step bound).
-__global__ void k_epilogue(Dev d, Handles H, int32_t max_steps) {
+__device__ __forceinline__ void epilogue_phase(const Dev &d, const Handles &H, int32_t max_steps) {
   __shared__ int32_t nact;
-  const int32_t t = d.ctl[CTL_T], cur = t & 1, nxt = cur ^ 1;
+  const int32_t t = __ldcg(d.ctl + CTL_T), cur = t & 1, nxt = cur ^ 1;
   int32_t *pcount_cur = d.pfront + (size_t)cur * d.P;
   int32_t *pcount_next = d.pfront + (size_t)nxt * d.P;
   if (threadIdx.x == 0) nact = 0;
@@ -451,6 +443,7 @@ __global__ void k_epilogue(Dev d, Handles H, int32_t max_steps) {
     if (H.use && (nact == 0 || t >= d.ctl[CTL_LIMIT])) cudaGraphSetConditional(H.loop, 0u);
   }
 }
+__global__ void k_epilogue(Dev d, Handles H, int32_t max_steps) { epilogue_phase(d, H, max_steps); }
 
 // ------------------------------------------------------------------- init
 // Seed region: the closed 1-ring of the seed vertex gets layer 1 with value 1 (Sec. 2: a

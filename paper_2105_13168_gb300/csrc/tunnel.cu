@@ -194,12 +194,12 @@ __device__ __noinline__ bool tupdate_row_wide(const Dev &d, const TDev &T, const
 
 template <class TV>
 __device__ __forceinline__ void tupdate_rows(const Dev &d, const TDev &T, const Params &P) {
-  const int32_t cur = d.ctl[CTL_TAU] & 1;
+  const int32_t cur = __ldcg(d.ctl + CTL_TAU) & 1;
   const int32_t *__restrict__ fv = T.fv[cur];
   const int32_t *__restrict__ fq = T.fq[cur];
-  const int32_t nF = T.nf[cur];
+  const int32_t nF = __ldcg(T.nf + cur);
   uint32_t redo = 0;
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
+  FOR_ROWS(i, nF) {
     const int32_t v = fv[i], q = fq[i];
     const int32_t deg = d.rp[v + 1] - d.rp[v];
     if (deg <= 16) redo += tupdate_row<16, TV>(d, T, P, i, q, v);
@@ -212,17 +212,18 @@ __device__ __forceinline__ void tupdate_rows(const Dev &d, const TDev &T, const 
   }
 }
 
-__global__ void __launch_bounds__(256) k_tupdate(Dev d, TDev T, Params P) {
+__device__ __forceinline__ void tupdate_phase(const Dev &d, const TDev &T, const Params &P) {
   if (T.phif) tupdate_rows<float>(d, T, P);
   else tupdate_rows<double>(d, T, P);
 }
+__global__ void __launch_bounds__(256) k_tupdate(Dev d, TDev T, Params P) { tupdate_phase(d, T, P); }
 
-__global__ void k_tapply(Dev d, TDev T, double theta) {
-  const int32_t tau = d.ctl[CTL_TAU], cur = tau & 1;
+__device__ __forceinline__ void tapply_phase(const Dev &d, const TDev &T, double theta) {
+  const int32_t tau = __ldcg(d.ctl + CTL_TAU), cur = tau & 1;
   const int32_t *__restrict__ fv = T.fv[cur];
   const int32_t *__restrict__ fq = T.fq[cur];
-  const int32_t nF = T.nf[cur];
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nF; i += gridDim.x * blockDim.x) {
+  const int32_t nF = __ldcg(T.nf + cur);
+  FOR_ROWS(i, nF) {
     const int32_t q = fq[i], v = fv[i];
     const int32_t p = T.pprob[q];
     const int32_t idx = T.pbase[q] + (v - d.voff[p]);
@@ -235,86 +236,75 @@ __global__ void k_tapply(Dev d, TDev T, double theta) {
     }
   }
 }
+__global__ void k_tapply(Dev d, TDev T, double theta) { tapply_phase(d, T, theta); }
 
 // u joins pass q's frontier iff it is in the domain, not a source, and its kept closed
-// neighbourhood holds both phases.
-template <int MAXD, class TV>
-__device__ __forceinline__ bool t_in_frontier_t(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
-                                                int32_t voff, int32_t u, int32_t b, int32_t deg) {
-  const int32_t iu = base + (u - voff);
-  const int8_t fu = T.flag[iu];
-  if (fu & F_SRC) return false;
-  const TV xu = tph_arr<TV>(T)[iu];
-  bool lay = val_pos(xu), bas = val_lt1(xu);
-  if (lay && bas) return true;
-  uint64_t kp;
-  TV nx[MAXD];
-  gather_kept<MAXD, TV>(d, T, q, step, base, voff, fu, u, b, deg, kp, nx);
-#pragma unroll
-  for (int j = 0; j < MAXD; ++j)
-    if ((kp >> j) & 1ull) {
-      if (val_pos(nx[j])) lay = true;
-      if (val_lt1(nx[j])) bas = true;
-    }
-  return lay && bas;
+// neighbourhood holds both phases (a value > 0 and a value < 1).  tgives(x): bit 0 the layer
+// (x > 0), bit 1 the base (x < 1).  As in the initial pass, u qualifies iff tgives(u) = 3 or
+// some kept neighbour w has tgives(u) | tgives(w) = 3, and every such pair has an endpoint in
+// the current frontier (a pair outside it kept its values and qualified one step earlier), so
+// the next frontier is found from the pairs (v, u), v in the frontier, u kept from v.
+template <class TV> __device__ __forceinline__ uint32_t tgives(TV x) {
+  return (val_pos(x) ? 1u : 0u) | (val_lt1(x) ? 2u : 0u);
 }
-template <class TV>
-__device__ __noinline__ bool t_in_frontier_wide(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
-                                                int32_t voff, int32_t u, int32_t b, int32_t deg) {
-  return t_in_frontier_t<64, TV>(d, T, q, step, base, voff, u, b, deg < 64 ? deg : 64);
-}
-__device__ __forceinline__ bool t_in_frontier(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
-                                              int32_t voff, int32_t u) {
-  if (!in_dom(d, u, step)) return false;
-  const int32_t b = d.rp[u], deg = d.rp[u + 1] - b;
-  if (T.phif) {
-    if (deg <= 16) return t_in_frontier_t<16, float>(d, T, q, step, base, voff, u, b, deg);
-    return t_in_frontier_wide<float>(d, T, q, step, base, voff, u, b, deg);
-  }
-  if (deg <= 16) return t_in_frontier_t<16, double>(d, T, q, step, base, voff, u, b, deg);
-  return t_in_frontier_wide<double>(d, T, q, step, base, voff, u, b, deg);
+__device__ __forceinline__ uint32_t tgives_at(const TDev &T, int32_t i) {
+  return T.phif ? tgives(T.phif[i]) : tgives(T.phi[i]);
 }
 
-// 16-lane groups per row, one lane per candidate of the row's kept closed neighbourhood.
-__global__ void __launch_bounds__(256) k_tfrontier(Dev d, TDev T) {
-  const int32_t tau = d.ctl[CTL_TAU], cur = tau & 1, nxt = cur ^ 1, tnext = tau + 1;
+// 16-lane groups per row, lane j takes the row's neighbour j (rows longer than 16 loop).
+__device__ __forceinline__ void tfrontier_phase(const Dev &d, const TDev &T) {
+  const int32_t tau = __ldcg(d.ctl + CTL_TAU), cur = tau & 1, nxt = cur ^ 1, tnext = tau + 1;
   const int32_t *__restrict__ fv = T.fv[cur];
   const int32_t *__restrict__ fq = T.fq[cur];
-  const int32_t nF = T.nf[cur];
+  const int32_t nF = __ldcg(T.nf + cur);
   int32_t *__restrict__ nv_out = T.fv[nxt];
   int32_t *__restrict__ nq_out = T.fq[nxt];
   int32_t *nN_ptr = T.nf + nxt;
   int32_t *qcnt_next = T.qcnt + (size_t)nxt * T.NP;
   const int32_t lane = threadIdx.x & 15;
-  const int32_t group = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
-  const int32_t ngroup = (gridDim.x * blockDim.x) >> 4;
-  for (int32_t i = group; i < nF; i += ngroup) {
+  const unsigned half = 0xFFFFu << (threadIdx.x & 16);
+  auto add = [&](int32_t u, int32_t iu, int32_t q) {
+    if (atomicExch(&T.stamp[iu], tnext) == tnext) return;
+    const int32_t s = warp_append(nN_ptr, qcnt_next, q);
+    if (!VCHK(T.err, s, T.PV, 331)) return;
+    nv_out[s] = u;
+    nq_out[s] = q;
+  };
+  FOR_ROWS16(i, nF) {
     const int32_t q = fq[i];
-    if (T.qdone[q] || T.qbstar[q] != 0x7fffffff) continue;
+    if (__ldcg(T.qdone + q) || __ldcg(T.qbstar + q) != 0x7fffffff) continue;
     const int32_t v = fv[i];
     const int32_t p = T.pprob[q], base = T.pbase[q], voff = d.voff[p], step = T.pstep[q];
-    const int8_t fl = T.flag[base + (v - voff)];
+    const int32_t iv = base + (v - voff);
+    if (!VCHK(T.err, iv, T.PV, 330)) continue;
+    const int8_t fl = T.flag[iv];
+    const uint32_t gv = tgives_at(T, iv);
     const int32_t b = d.rp[v], e = d.rp[v + 1];
-    for (int32_t k = b - 1 + lane; k < e; k += 16) {
-      const int32_t u = (k < b) ? v : d.col[k];
-      if (k >= b && !kept(d, T, q, step, base, voff, fl, u, k)) continue;
+    bool join = gv == 3u;
+    for (int32_t k0 = b; k0 < e; k0 += 16) {
+      const int32_t k = k0 + lane;
+      if (k >= e) continue;
+      const int32_t u = d.col[k];
+      if (!kept(d, T, q, step, base, voff, fl, u, k)) continue;
       const int32_t iu = base + (u - voff);
-      if (!VCHK(T.err, iu, T.PV, 330)) continue;
-      if (atomicExch(&T.stamp[iu], tnext) == tnext) continue;
-      if (!t_in_frontier(d, T, q, step, base, voff, u)) continue;
-      const int32_t s = warp_append(nN_ptr, qcnt_next, q);
-      if (!VCHK(T.err, s, T.PV, 331)) continue;
-      nv_out[s] = u;
-      nq_out[s] = q;
+      if (!VCHK(T.err, iu, T.PV, 332)) continue;
+      const uint32_t gu = tgives_at(T, iu);
+      if ((gv | gu) != 3u) continue;
+      join = true;
+      if (!(T.flag[iu] & F_SRC)) add(u, iu, q);
     }
+    join = __any_sync(half, join) && !(fl & F_SRC);
+    if (lane == 0 && join) add(v, iv, q);
   }
 }
 
+__global__ void __launch_bounds__(256) k_tfrontier(Dev d, TDev T) { tfrontier_phase(d, T); }
+
 // One block: pass bookkeeping, then the step counter advances; the WHILE node stops when no
 // pass is running (or at the hard step bound).
-__global__ void k_tepilogue(Dev d, TDev T, Handles H, int32_t max_steps) {
+__device__ __forceinline__ void tepilogue_phase(const Dev &d, const TDev &T, const Handles &H, int32_t max_steps) {
   __shared__ int32_t nact;
-  const int32_t tau = d.ctl[CTL_TAU], cur = tau & 1, nxt = cur ^ 1;
+  const int32_t tau = __ldcg(d.ctl + CTL_TAU), cur = tau & 1, nxt = cur ^ 1;
   int32_t *cnt_cur = T.qcnt + (size_t)cur * T.NP;
   int32_t *cnt_next = T.qcnt + (size_t)nxt * T.NP;
   if (threadIdx.x == 0) nact = 0;
@@ -338,6 +328,8 @@ __global__ void k_tepilogue(Dev d, TDev T, Handles H, int32_t max_steps) {
     if (H.use && (nact == 0 || tau >= d.ctl[CTL_TLIMIT])) cudaGraphSetConditional(H.loop, 0u);
   }
 }
+
+__global__ void k_tepilogue(Dev d, TDev T, Handles H, int32_t max_steps) { tepilogue_phase(d, T, H, max_steps); }
 
 // one thread per pass: greedy descent on (arrival, id), then closure along the loop
 __global__ void k_ttrace(Dev d, TDev T) {

@@ -192,6 +192,23 @@ __device__ __forceinline__ bool val_pos(float x) { return __float_as_int(x) > 0;
 __device__ __forceinline__ bool val_lt1(float x) { return __float_as_int(x) < 0x3F800000; }
 __device__ __forceinline__ bool val_band(float x) { return val_pos(x) && val_lt1(x); }
 
+// ------------------------------------------------------------ row loops
+// Grid-stride loops over the n rows of a frontier list that spread warps over the whole grid:
+// loop warp w runs as warp w / gridDim.x of block w % gridDim.x, so a frontier of a few
+// thousand rows occupies every SM instead of filling the first blocks (and so a few SMs)
+// while the rest idle.  Lanes of a warp take consecutive rows (FOR_ROWS: 32 rows per warp;
+// FOR_ROWS16: 2 rows per warp, 16 lanes each).  The loop bounds are uniform per warp; the body
+// runs once per row, `continue` moves on to the next row.
+#define VLS_WARP_LOOP(w, rows_per_warp, n)                                                          \
+  for (int32_t w = (int32_t)(blockIdx.x + gridDim.x * (threadIdx.x >> 5)); w * (rows_per_warp) < (n); \
+       w += (int32_t)(gridDim.x * (blockDim.x >> 5)))
+#define FOR_ROWS(i, n)                                                                              \
+  VLS_WARP_LOOP(vls_w_, 32, n)                                                                      \
+  for (int32_t i = vls_w_ * 32 + (int32_t)(threadIdx.x & 31); i < (n); i = INT32_MAX)
+#define FOR_ROWS16(i, n)                                                                            \
+  VLS_WARP_LOOP(vls_w_, 2, n)                                                                       \
+  for (int32_t i = vls_w_ * 2 + (int32_t)((threadIdx.x >> 4) & 1); i < (n); i = INT32_MAX)
+
 // ------------------------------------------------------------ stored values
 // The layer value of a vertex is stored as double (FP64 form) or float (FP32 form, d.phif
 // non-null).  Readers that only test a value use the bit tests above on the stored type.
