@@ -744,12 +744,12 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     CK(cudaEventRecord(ev[4], st));
     CK(cudaStreamSynchronize(st));
     if (!b.host_loop) {
-      // kernels run inside the graphs: 6 per initial step, 4 per merge phase, 1 per split
-      // phase, 4 per tunnel step
+      // kernels run inside the graphs: 5 per initial step, 4 per merge phase, 1 per split
+      // phase, 3 per tunnel step
       const int64_t steps = h_ctl[CTL_T] - 1;
-      b.launches += 6 * steps;
+      b.launches += 5 * steps;
       b.launches += 4 * (int64_t)h_ctl[CTL_NMERGE] + (int64_t)h_ctl[CTL_NSPLIT];
-      if (tunnel_tau > 0) b.launches += 4 * (int64_t)tunnel_tau;
+      if (tunnel_tau > 0) b.launches += 3 * (int64_t)tunnel_tau;
     }
 #ifdef VLS_CHECKED
     {

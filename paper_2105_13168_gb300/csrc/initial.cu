@@ -258,37 +258,22 @@ __device__ __forceinline__ void hook_phase(const Dev &d) {
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
   const int32_t nF = __ldcg(d.nfront + cur);
-  FOR_ROWS(i, nF) {
+  const int32_t lane = threadIdx.x & 15;
+  // 16 lanes per band row, one neighbour each: a neighbour joins the row's band component iff
+  // it is a frontier row of this step (band vertices are) holding the same live layer strictly
+  // between 0 and 1; the smaller id of each such pair unites
+  FOR_ROWS16(i, nF) {
     if (__ldcg(d.pdone + fp[i])) continue;
     const int32_t v = fv[i];
     int32_t l;
     if (!is_band(d, v, l)) continue;
-    const int32_t b = d.rp[v], deg = d.rp[v + 1] - b;
-    if (deg <= 16) {
-      // a neighbour joins v's band component iff it is a frontier row of this step (band
-      // vertices are) holding the same live layer strictly between 0 and 1
-      int32_t nu[16], nm[16], nl[16];
-      bool nb[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) nu[j] = (j < deg) ? d.col[b + j] : v;
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const bool ok = j < deg && nu[j] < v;
-        nm[j] = ok ? d.fmark[nu[j]] : -1;
-        nl[j] = ok ? d.lay[nu[j]] : 0;
-        nb[j] = ok && ph_band(d, nu[j]);
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (nm[j] == t && nl[j] == l && nb[j]) uf_unite(d.uf, nu[j], v);
-    } else {
-      for (int32_t k = b; k < b + deg; ++k) {
-        const int32_t u = d.col[k];
-        if (!VCHK(d.err, u, d.V, 130)) continue;
-        if (u >= v || d.fmark[u] != t) continue;
-        int32_t lu;
-        if (is_band(d, u, lu) && lu == l) uf_unite(d.uf, u, v);
-      }
+    const int32_t b = d.rp[v], e = d.rp[v + 1];
+    for (int32_t k = b + lane; k < e; k += 16) {
+      const int32_t u = d.col[k];
+      if (!VCHK(d.err, u, d.V, 130)) continue;
+      const int32_t fm = d.fmark[u], lu = d.lay[u];
+      const bool bu = ph_band(d, u);
+      if (u < v && fm == t && lu == l && bu) uf_unite(d.uf, u, v);
     }
   }
 }
@@ -307,7 +292,7 @@ __device__ __forceinline__ void count_phase(const Dev &d) {
     const int32_t v = fv[i];
     int32_t l;
     if (!is_band(d, v, l)) continue;
-    if (uf_find(d.uf, v) == v) {
+    if (__ldcg(d.uf + v) == v) { // hooking is complete: roots are exactly the self-parents
       const int32_t old = atomicAdd(&d.lcnt[l], 1);
       if (old == 0) atomicAdd(&d.nbl[p], 1);
       else if (old == 1) d.ctl[CTL_SPLIT] = 1;
@@ -399,7 +384,6 @@ __device__ __forceinline__ void frontier_phase(const Dev &d) {
     if (lane == 0 && join) add(v, p);
   }
 }
-__global__ void __launch_bounds__(256) k_frontier(Dev d) { frontier_phase(d); }
 
 // ------------------------------------------------------------------- epilogue
 // One block: per-problem bookkeeping, then the step counter advances; the WHILE node stops
@@ -412,21 +396,21 @@ __device__ __forceinline__ void epilogue_phase(const Dev &d, const Handles &H, i
   if (threadIdx.x == 0) nact = 0;
   __syncthreads();
   for (int32_t p = threadIdx.x; p < d.P; p += blockDim.x) {
-    if (!d.pdone[p]) {
+    if (!__ldcg(d.pdone + p)) {
       d.psteps[p] = t;
-      d.pupd[p] += pcount_cur[p];
+      d.pupd[p] += __ldcg(pcount_cur + p);
       if (d.record && t - 1 < d.rcap) {
         long long *r = d.rec + ((int64_t)p * d.rcap + (t - 1)) * 4;
-        const unsigned long long h = d.rhash[p];
-        r[0] = pcount_cur[p];
-        r[1] = d.rband[p];
+        const unsigned long long h = __ldcg(d.rhash + p);
+        r[0] = __ldcg(pcount_cur + p);
+        r[1] = __ldcg(d.rband + p);
         r[2] = (long long)(h & 0xffffffffull);
         r[3] = (long long)(h >> 32);
       }
       d.rband[p] = 0;
       d.rhash[p] = 0ull;
-      if (d.pstatus[p] != 0) d.pdone[p] = 1;
-      else if (pcount_next[p] == 0) d.pdone[p] = 1;
+      if (__ldcg(d.pstatus + p) != 0) d.pdone[p] = 1;
+      else if (__ldcg(pcount_next + p) == 0) d.pdone[p] = 1;
       else if (t >= max_steps) { d.pstatus[p] = VLS_EMAXSTEPS; d.pdone[p] = 1; }
       if (!d.pdone[p]) atomicAdd(&nact, 1);
     }
@@ -443,7 +427,11 @@ __device__ __forceinline__ void epilogue_phase(const Dev &d, const Handles &H, i
     if (H.use && (nact == 0 || t >= d.ctl[CTL_LIMIT])) cudaGraphSetConditional(H.loop, 0u);
   }
 }
-__global__ void k_epilogue(Dev d, Handles H, int32_t max_steps) { epilogue_phase(d, H, max_steps); }
+// The next frontier, then (epi = 1) the step's epilogue in the last block to finish.
+__global__ void __launch_bounds__(256) k_frontier(Dev d, Handles H, int32_t max_steps, int32_t epi) {
+  frontier_phase(d);
+  if (epi && last_block(d.ctl + CTL_DONE_FRONT)) epilogue_phase(d, H, max_steps);
+}
 
 // ------------------------------------------------------------------- init
 // Seed region: the closed 1-ring of the seed vertex gets layer 1 with value 1 (Sec. 2: a
@@ -504,7 +492,11 @@ cudaError_t init_state(Batch &b) {
   Dev &d = b.d;
   cudaStream_t st = b.st;
   k_init<<<(b.P + 127) / 128, 128, 0, st>>>(d, d.front[0], d.front[0] + b.V, d.nfront + 0); VLS_LAUNCH(b);
-  k_frontier<<<b.cfg[KK_FRONTIER].grid, b.cfg[KK_FRONTIER].threads, 0, st>>>(d); VLS_LAUNCH(b);
+  {
+    Handles H{};
+    H.use = 0;
+    k_frontier<<<b.cfg[KK_FRONTIER].grid, b.cfg[KK_FRONTIER].threads, 0, st>>>(d, H, b.opt.max_steps, 0); VLS_LAUNCH(b);
+  }
   cudaMemsetAsync(d.nfront + 0, 0, sizeof(int32_t), st);
   k_ctl_set<<<1, 1, 0, st>>>(d.ctl, CTL_T, 1); VLS_LAUNCH(b);
   return cudaGetLastError();
@@ -514,7 +506,7 @@ cudaError_t init_state(Batch &b) {
 // band hook; band count; IF(split / extinction) {...}; next frontier; epilogue }.
 cudaError_t build_initial_graph(Batch &b, cudaGraph_t *out) {
   cudaGraph_t g = nullptr, body = nullptr, mbody = nullptr, sbody = nullptr;
-  cudaGraphNode_t w, n_upd, n_app, n_if_m, n_hook, n_cnt, n_if_s, n_fr, n_ep;
+  cudaGraphNode_t w, n_upd, n_app, n_if_m, n_hook, n_cnt, n_if_s, n_fr;
   Handles H{};
   H.use = 1;
   cudaError_t e = cudaGraphCreate(&g, 0);
@@ -553,8 +545,7 @@ cudaError_t build_initial_graph(Batch &b, cudaGraph_t *out) {
     sbody = np.conditional.phGraph_out[0];
     GK(add_split_nodes(b, sbody));
   }
-  GK(add_kernel(&n_fr, body, &n_if_s, 1, k_frontier, G(KK_FRONTIER), T(KK_FRONTIER), b.d));
-  GK(add_kernel(&n_ep, body, &n_fr, 1, k_epilogue, dim3(1), dim3(256), b.d, H, b.opt.max_steps));
+  GK(add_kernel(&n_fr, body, &n_if_s, 1, k_frontier, G(KK_FRONTIER), T(KK_FRONTIER), b.d, H, b.opt.max_steps, 1));
 #undef GK
   *out = g;
   return cudaSuccess;
@@ -587,10 +578,7 @@ cudaError_t initial_step_host(Batch &b) {
   e = split_phase_host(b);
   if (e != cudaSuccess) return e;
   ps = b.prof.begin(st, KK_FRONTIER);
-  k_frontier<<<b.cfg[KK_FRONTIER].grid, b.cfg[KK_FRONTIER].threads, 0, st>>>(d); VLS_LAUNCH(b);
-  b.prof.end(st, ps);
-  ps = b.prof.begin(st, KK_EPILOGUE);
-  k_epilogue<<<1, 256, 0, st>>>(d, H, b.opt.max_steps); VLS_LAUNCH(b);
+  k_frontier<<<b.cfg[KK_FRONTIER].grid, b.cfg[KK_FRONTIER].threads, 0, st>>>(d, H, b.opt.max_steps, 1); VLS_LAUNCH(b);
   b.prof.end(st, ps);
   return cudaGetLastError();
 }

@@ -298,7 +298,6 @@ __device__ __forceinline__ void tfrontier_phase(const Dev &d, const TDev &T) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_tfrontier(Dev d, TDev T) { tfrontier_phase(d, T); }
 
 // One block: pass bookkeeping, then the step counter advances; the WHILE node stops when no
 // pass is running (or at the hard step bound).
@@ -310,11 +309,11 @@ __device__ __forceinline__ void tepilogue_phase(const Dev &d, const TDev &T, con
   if (threadIdx.x == 0) nact = 0;
   __syncthreads();
   for (int32_t q = threadIdx.x; q < T.NP; q += blockDim.x) {
-    if (!T.qdone[q]) {
+    if (!__ldcg(T.qdone + q)) {
       T.qsteps[q] = tau;
-      T.qupd[q] += cnt_cur[q];
-      if (T.qbstar[q] != 0x7fffffff) { T.qdone[q] = 1; T.qstatus[q] = VLS_OK; }
-      else if (cnt_next[q] == 0) { T.qdone[q] = 1; T.qstatus[q] = VLS_ELOOPFAIL; }
+      T.qupd[q] += __ldcg(cnt_cur + q);
+      if (__ldcg(T.qbstar + q) != 0x7fffffff) { T.qdone[q] = 1; T.qstatus[q] = VLS_OK; }
+      else if (__ldcg(cnt_next + q) == 0) { T.qdone[q] = 1; T.qstatus[q] = VLS_ELOOPFAIL; }
       else if (tau >= max_steps) { T.qdone[q] = 1; T.qstatus[q] = VLS_EMAXSTEPS; }
       if (!T.qdone[q]) atomicAdd(&nact, 1);
     }
@@ -329,7 +328,11 @@ __device__ __forceinline__ void tepilogue_phase(const Dev &d, const TDev &T, con
   }
 }
 
-__global__ void k_tepilogue(Dev d, TDev T, Handles H, int32_t max_steps) { tepilogue_phase(d, T, H, max_steps); }
+// The next frontier of every pass, then (epi = 1) the step's epilogue in the last block to finish.
+__global__ void __launch_bounds__(256) k_tfrontier(Dev d, TDev T, Handles H, int32_t max_steps, int32_t epi) {
+  tfrontier_phase(d, T);
+  if (epi && last_block(d.ctl + CTL_DONE_TFRONT)) tepilogue_phase(d, T, H, max_steps);
+}
 
 // one thread per pass: greedy descent on (arrival, id), then closure along the loop
 __global__ void k_ttrace(Dev d, TDev T) {
@@ -410,7 +413,11 @@ cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out) {
   cudaStream_t st = b.st;
   k_tinit<<<T.NP, 256, 0, st>>>(d, T, T.fv[0], T.fq[0], T.nf + 0); VLS_LAUNCH(b);
   k_tctl_set<<<1, 1, 0, st>>>(d.ctl, CTL_TAU, 0); VLS_LAUNCH(b);
-  k_tfrontier<<<b.cfg[KK_TFRONTIER].grid, b.cfg[KK_TFRONTIER].threads, 0, st>>>(d, T); VLS_LAUNCH(b);
+  {
+    Handles H0{};
+    H0.use = 0;
+    k_tfrontier<<<b.cfg[KK_TFRONTIER].grid, b.cfg[KK_TFRONTIER].threads, 0, st>>>(d, T, H0, b.opt.max_pass_steps, 0); VLS_LAUNCH(b);
+  }
   cudaMemsetAsync(T.nf + 0, 0, sizeof(int32_t), st);
   k_tctl_set<<<1, 1, 0, st>>>(d.ctl, CTL_TAU, 1); VLS_LAUNCH(b);
   cudaError_t e = cudaSuccess;
@@ -426,10 +433,7 @@ cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out) {
       k_tapply<<<b.cfg[KK_TAPPLY].grid, b.cfg[KK_TAPPLY].threads, 0, st>>>(d, T, b.prm.theta); VLS_LAUNCH(b);
       b.prof.end(st, ps);
       ps = b.prof.begin(st, KK_TFRONTIER);
-      k_tfrontier<<<b.cfg[KK_TFRONTIER].grid, b.cfg[KK_TFRONTIER].threads, 0, st>>>(d, T); VLS_LAUNCH(b);
-      b.prof.end(st, ps);
-      ps = b.prof.begin(st, KK_TEPILOGUE);
-      k_tepilogue<<<1, 256, 0, st>>>(d, T, H, b.opt.max_pass_steps); VLS_LAUNCH(b);
+      k_tfrontier<<<b.cfg[KK_TFRONTIER].grid, b.cfg[KK_TFRONTIER].threads, 0, st>>>(d, T, H, b.opt.max_pass_steps, 1); VLS_LAUNCH(b);
       b.prof.end(st, ps);
       if (tau % sync_every == 0) {
         int32_t act = 0;
@@ -442,16 +446,16 @@ cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out) {
     }
   } else {
     cudaGraph_t g = nullptr, body = nullptr;
-    cudaGraphNode_t w, n0, n1, n2, n3;
+    cudaGraphNode_t w, n0, n1, n2;
     Handles H{};
     H.use = 1;
     e = cudaGraphCreate(&g, 0);
     if (e == cudaSuccess) e = add_conditional(&w, g, nullptr, 0, cudaGraphCondTypeWhile, 1u, &H.loop, &body);
     if (e == cudaSuccess) e = add_kernel(&n0, body, nullptr, 0, k_tupdate, dim3(b.cfg[KK_TUPDATE].grid), dim3(b.cfg[KK_TUPDATE].threads), d, T, b.prm);
     if (e == cudaSuccess) e = add_kernel(&n1, body, &n0, 1, k_tapply, dim3(b.cfg[KK_TAPPLY].grid), dim3(b.cfg[KK_TAPPLY].threads), d, T, b.prm.theta);
-    if (e == cudaSuccess) e = add_kernel(&n2, body, &n1, 1, k_tfrontier, dim3(b.cfg[KK_TFRONTIER].grid), dim3(b.cfg[KK_TFRONTIER].threads), d, T);
     if (e == cudaSuccess)
-      e = add_kernel(&n3, body, &n2, 1, k_tepilogue, dim3(1), dim3(256), d, T, H, b.opt.max_pass_steps);
+      e = add_kernel(&n2, body, &n1, 1, k_tfrontier, dim3(b.cfg[KK_TFRONTIER].grid), dim3(b.cfg[KK_TFRONTIER].threads), d, T, H,
+                     b.opt.max_pass_steps, 1);
     cudaGraphExec_t ge = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
     if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);

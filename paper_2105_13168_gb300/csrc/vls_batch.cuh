@@ -56,12 +56,12 @@ struct TDev {
 
 // Kernel kinds timed in profile mode.
 enum KernelKind : int {
-  KK_UPDATE = 0, KK_TUPDATE, KK_APPLY, KK_HOOK, KK_COUNT, KK_FRONTIER, KK_EPILOGUE, KK_MERGE_GROUPS,
-  KK_TRACE, KK_MERGE_FINISH, KK_RELABEL, KK_SPLIT, KK_TAPPLY, KK_TFRONTIER, KK_TEPILOGUE, KK_COUNT_KINDS
+  KK_UPDATE = 0, KK_TUPDATE, KK_APPLY, KK_HOOK, KK_COUNT, KK_FRONTIER, KK_MERGE_GROUPS,
+  KK_TRACE, KK_MERGE_FINISH, KK_RELABEL, KK_SPLIT, KK_TAPPLY, KK_TFRONTIER, KK_COUNT_KINDS
 };
 static const char *const kKernelNames[KK_COUNT_KINDS] = {
-    "k_update", "k_tupdate", "k_apply", "k_band_hook", "k_band_count", "k_frontier", "k_epilogue",
-    "k_merge_groups", "k_trace", "k_merge_finish", "k_relabel", "k_split", "k_tapply", "k_tfrontier", "k_tepilogue"};
+    "k_update", "k_tupdate", "k_apply", "k_band_hook", "k_band_count", "k_frontier",
+    "k_merge_groups", "k_trace", "k_merge_finish", "k_relabel", "k_split", "k_tapply", "k_tfrontier"};
 
 // Optional CUDA-event timing of selected launches (pairs drawn from a context-owned pool).
 struct Prof {

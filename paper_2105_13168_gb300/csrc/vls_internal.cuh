@@ -143,6 +143,8 @@ enum Ctl : int {
   CTL_TLIMIT = 9,     // hard step bound of the tunnel passes
   CTL_NMERGE = 10,    // merge phases executed (launch accounting)
   CTL_NSPLIT = 11,    // split phases executed
+  CTL_DONE_FRONT = 12, // last-block counter of the initial-pass frontier kernel
+  CTL_DONE_TFRONT = 13, // last-block counter of the tunnel-pass frontier kernel
   CTL_SIZE = 16
 };
 
@@ -169,6 +171,21 @@ __device__ __forceinline__ bool last_block_done(int32_t *counter) {
     return true;
   }
   return false;
+}
+
+// True in every thread of the last block of the grid to finish (same protocol as above).
+__device__ __forceinline__ bool last_block(int32_t *counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(counter, 1) == (int32_t)gridDim.x - 1;
+    if (last) *counter = 0;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
 }
 
 // ----------------------------------------------------------- FP64 arithmetic
