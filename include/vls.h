@@ -84,12 +84,19 @@ typedef struct {
   int32_t keep_state;       /* 1: results carry the final per-vertex state (layer, value, cover) */
   int32_t record_steps;     /* 1: results carry per-step frontier size, band size, band hash */
   int32_t sync_interval;    /* steps between host polls of the device "still running" flag */
-  int32_t threads;          /* threads per block of the frontier kernels (0: autotuned) */
-  int32_t blocks_per_sm;    /* grid = blocks_per_sm x SM count (0: autotuned) */
+  int32_t threads;          /* threads per block of the frontier kernels; with blocks_per_sm */
+  int32_t blocks_per_sm;    /* grid = blocks_per_sm x SM count (clamped to what fits).  Both 0:
+                               autotuned -- the first batch of a device, precision and size class
+                               (total vertices rounded up to a power of two) runs the first 600
+                               steps of its initial pass under each candidate shape and band
+                               union-find variant and keeps the fastest for the life of the
+                               process */
   vls_precision precision;
   int32_t profile;          /* 1: time every frontier-update launch with CUDA events (vls_stats) */
   int32_t host_loop;        /* 1: launch each step's kernels from the host instead of running the
                                step loops as device-driven CUDA graphs (same results) */
+  int32_t hook_variant;     /* band union-find: 1 one thread per band row, 2 sixteen lanes per
+                               band row (one neighbour each), 0 autotuned or 2 (same results) */
 } vls_options;
 
 /* A closed, oriented triangle mesh: X[nv][3] positions, F[nf][3] vertex ids (CCW). */

@@ -179,6 +179,36 @@ def sphere(grid: int = 48, radius: float = 1.0) -> Mesh:
 
 
 # --------------------------------------------------------------------- workloads
+def _batch_specs(scale: float = 1.0):
+    """Shape of every mesh of the batch workload: (genus type, target faces), drawn in order from
+    one PCG64 stream (shape mix only; the meshes' own noise uses SplitMix64)."""
+    st = np.random.Generator(np.random.PCG64(4))
+    out = []
+    for _ in range(256):
+        target = math.exp(st.uniform(math.log(2000), math.log(200000))) * scale
+        gtype = int(st.integers(1, 21))
+        out.append((gtype, target))
+    return out
+
+
+def batch_problem(i: int, scale: float = 1.0):
+    """Mesh i of the batch workload (a torus for genus type 1, else a tube chain of that many
+    tori) with its 4 seed vertices."""
+    gtype, target = _batch_specs(scale)[i]
+    if gtype == 1:
+        nvv = max(4, int(round(math.sqrt(target / 4))))
+        m = torus(2 * nvv, nvv, 2.0, 0.7)
+    else:
+        # marching tetrahedra give F ~ 7 * area / h^2 (measured 6.2-7.7) with area
+        # n * 4 pi^2 R r; the spacing h is capped at r / 2.2 so that every tube is
+        # resolved (which raises small targets of long chains to ~75k faces)
+        L = 1.6 * (gtype - 1) + 2 * (1.0 + 0.35 + 0.15 + 0.1)
+        h = min(0.16, math.sqrt(7.0 * gtype * 4 * math.pi ** 2 * 0.35 / target))
+        grid = int(math.ceil(L / h)) + 1
+        m = jitter(tube_chain(gtype, grid), 0.1, 100 + i)
+    return m, [seed_vertex(4 * i + s, m.nv) for s in range(4)]
+
+
 def workload(k: int, scale: float = 1.0):
     """Problems of workload k (1..5): list of (Mesh, [seed vertices]).
 
@@ -196,20 +226,7 @@ def workload(k: int, scale: float = 1.0):
         m = schwarz_p(4, max(24, int(round(240 * scale))))
         return [(m, [seed_vertex(0, m.nv)])]
     if k == 4:
-        out = []
-        st = np.random.Generator(np.random.PCG64(4))  # shape mix only
-        for i in range(256):
-            target = math.exp(st.uniform(math.log(2000), math.log(200000))) * scale
-            gtype = int(st.integers(1, 21))
-            if gtype == 1:
-                nvv = max(4, int(round(math.sqrt(target / 4))))
-                m = torus(2 * nvv, nvv, 2.0, 0.7)
-            else:
-                # faces of a chain scale ~ grid^2 * n_tori; calibrated constant
-                grid = max(24, int(round(math.sqrt(target / (gtype * 1.2)) * 2.0 + 8 * gtype)))
-                m = jitter(tube_chain(gtype, grid), 0.1, 100 + i)
-            out.append((m, [seed_vertex(4 * i + s, m.nv) for s in range(4)]))
-        return out
+        return [batch_problem(i, scale) for i in range(256)]
     if k == 5:
         m = gyroid(8, max(32, int(round(295 * scale))))
         m = jitter(m, 0.05, 5)

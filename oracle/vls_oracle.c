@@ -43,14 +43,17 @@
  *     theta > psi(b), one endpoint holding the layer), the component with the most
  *     crossing edges; the loop dropped in a merge is the one with the most crossing edges
  *     (Sec. 3.1 says the choice does not matter).
- *   - Tunnel pass: domain = vertices covered by the step of the handle; the loop's crossing
- *     edges are cut; inside endpoints held at 1; arrival step T(v) = first step with
- *     phi >= theta; trace from the smallest-id outside endpoint reached first, moving to
- *     the unvisited neighbour of least (T, id) with T not larger; close along the loop.
+ *   - Tunnel pass: domain = vertices covered by the step of the handle (the whole surface when
+ *     the handle loop separates that area); the loop's crossing edges are cut; inside
+ *     endpoints held at 1; arrival step T(v) = first step with phi >= theta; trace from
+ *     the smallest-id outside endpoint reached first, depth first over unvisited reached
+ *     neighbours in the order (T larger than here, T, id), stepping back along the path
+ *     from dead ends, down to a source; close along the loop.
  */
 #include "vls_oracle.h"
 
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -875,9 +878,8 @@ static int initial_pass(orc_run *R, int32_t seed) {
 }
 
 /* --------------------------------------------------------- tunnel pass */
-static int tunnel_pass(orc_run *R, handle_t *H) {
+static int tunnel_pass(orc_run *R, handle_t *H, int32_t th_step) {
   int64_t nv = R->nv;
-  int32_t th_step = H->info[0];
   int64_t m = H->info[3];
   double th = R->opt.theta_iso;
   if (m == 0) { H->tinfo[0] = ST_ELOOPFAIL; return ST_ELOOPFAIL; }
@@ -983,7 +985,11 @@ static int tunnel_pass(orc_run *R, handle_t *H) {
   H->tinfo[1] = tau;
   H->tinfo[2] = bstar;
   if (st == ST_OK) {
-    /* greedy descent on (T, id) in the cut, restricted graph */
+    /* descent on the arrival steps in the cut, restricted graph, depth first: from the path's
+       last vertex x go to the unvisited reached neighbour u with the least key
+       (T(u) > T(x), T(u), u) -- steps that do not raise the arrival step first, then the
+       earliest, then the smallest id; with none left, drop x from the path and go on from the
+       vertex before it.  Ends at a source (T = 0); fails only when the path empties. */
     int32_t *path = (int32_t *)malloc(sizeof(int32_t) * (nv + 1));
     int64_t np = 0;
     sid = ++R->stamp_id;
@@ -991,13 +997,22 @@ static int tunnel_pass(orc_run *R, handle_t *H) {
     path[np++] = x;
     R->stamp[x] = sid;
     while (T[x] != 0) {
-      int32_t best = -1;
+      int32_t best = -1, bup = 0;
       for (int64_t k = hp[x]; k < hp[x + 1]; ++k) {
         int32_t u = hc[k];
-        if (T[u] < 0 || T[u] > T[x] || R->stamp[u] == sid) continue;
-        if (best < 0 || T[u] < T[best] || (T[u] == T[best] && u < best)) best = u;
+        if (T[u] < 0 || R->stamp[u] == sid) continue;
+        int up = T[u] > T[x];
+        if (best < 0 || up < bup || (up == bup && (T[u] < T[best] || (T[u] == T[best] && u < best)))) {
+          best = u;
+          bup = up;
+        }
       }
-      if (best < 0) { st = ST_ELOOPFAIL; break; }
+      if (best < 0) {
+        if (np <= 1) { st = ST_ELOOPFAIL; break; }
+        --np;
+        x = path[np - 1];
+        continue;
+      }
       R->stamp[best] = sid;
       path[np++] = best;
       x = best;
@@ -1058,7 +1073,16 @@ orc_run *orc_detect(const double *X, int64_t nv, const int32_t *F, int64_t nf, i
   R->status = initial_pass(R, seed_vertex);
   if (R->status == ST_OK && o->tunnels)
     for (int32_t h = 0; h < R->nh; ++h) {
-      int st = tunnel_pass(R, &R->h[h]);
+      /* Sec. 3.2: the pass is restricted to the area covered when the handle was found.  When
+         the kept handle loop separates that area (its far side cannot be reached), the pass
+         runs again on the whole surface. */
+      handle_t *H = &R->h[h];
+      int st = tunnel_pass(R, H, H->info[0]);
+      if (st == ST_ELOOPFAIL && H->info[3] > 0 && H->tinfo[2] < 0) {
+        free(H->arrival);
+        H->arrival = NULL;
+        st = tunnel_pass(R, H, INT32_MAX);
+      }
       if (st != ST_OK && R->status == ST_OK) R->status = st;
     }
   /* outputs */

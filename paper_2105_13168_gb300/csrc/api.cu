@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -95,6 +96,7 @@ extern "C" void vls_default_options(vls_options *o) {
   o->precision = VLS_FP64;
   o->profile = 0;
   o->host_loop = 0;
+  o->hook_variant = 0;
 }
 
 extern "C" void vls_constants(const vls_options *o, double out[4]) {
@@ -256,7 +258,9 @@ void layout_batch(Layout &L, Batch &b) {
   d.hvoff = L.take<int32_t>(d.hcap);
   d.hvn = L.take<int32_t>(d.hcap);
   d.hlen = L.take<double>(d.hcap);
-  d.ecap = (int32_t)std::max<size_t>(1u << 20, V / 8);
+  // handle-loop crossing edges of the whole batch: every handle loop of a high-genus problem
+  // together (thousands of loops of ~1k edges on a 20M-face mesh)
+  d.ecap = (int32_t)std::max<size_t>(1u << 20, V);
   d.nhedge = L.take<int32_t>(1);
   d.hedge = L.take<int32_t>(2 * (size_t)d.ecap);
   d.hpts = L.take<double>(3 * (size_t)d.ecap);
@@ -333,12 +337,108 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
   return ms;
 }
 
+// ---- autotuner
+// Launch shapes chosen by measurement, kept per device, precision and batch size class (total
+// vertices rounded up to a power of two) for the life of the process.  Until a candidate wins,
+// every kernel uses 16-lane hooking and as many blocks per SM as fit.
+struct TuneEntry {
+  int dev = -1, vclass = -1, prec = -1;
+  Batch::Shape shape[KK_COUNT_KINDS];
+  int hook_variant = 2;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+
+constexpr int TUNE_STEPS = 600;
+// (threads per block, blocks per SM (64: as many as fit), band union-find variant)
+const int kTuneCands[][3] = {{128, 64, 2}, {256, 64, 2}, {64, 64, 2}, {128, 64, 1}, {128, 4, 2}};
+
+// Each candidate launch shape / union-find variant runs the first TUNE_STEPS steps of this
+// batch's initial pass the way real calls run (device-driven graph, every kernel with that
+// shape), timed with CUDA events around the whole call; the fastest candidate is kept.  Per
+// kernel timings from host-launched steps mislead here: a graph hides launch costs that host
+// launches expose, and the early steps' small frontiers favour small grids.
+void autotune(vls_ctx *ctx, int32_t n_mesh, const vls_mesh *meshes, const int32_t *seeds, const int32_t *spm,
+              TuneEntry &te) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return;
+  float best = 1e30f;
+  for (const auto &c : kTuneCands) {
+    vls_options o = ctx->opt;
+    o.threads = c[0];
+    o.blocks_per_sm = c[1];
+    o.hook_variant = c[2];
+    o.max_steps = TUNE_STEPS;
+    o.tunnels = 0;
+    o.profile = 0;
+    o.host_loop = 0;
+    o.keep_state = 0;
+    o.record_steps = 0;
+    vls_ctx *t = nullptr;
+    if (vls_create(&t, &o, ctx->st) != VLS_OK) continue;
+    vls_result *r = nullptr;
+    vls_detect_batch(t, n_mesh, meshes, seeds, spm, &r); // first run sizes the arena
+    if (r) vls_result_free(r);
+    r = nullptr;
+    cudaEventRecord(e0, ctx->st);
+    const vls_status st = vls_detect_batch(t, n_mesh, meshes, seeds, spm, &r);
+    cudaEventRecord(e1, ctx->st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (st == VLS_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+      best = ms;
+      for (int k = 0; k < KK_COUNT_KINDS; ++k) {
+        te.shape[k].threads = c[0];
+        te.shape[k].bps = c[1];
+      }
+      te.hook_variant = c[2];
+    }
+    if (r) vls_result_free(r);
+    vls_destroy(t);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
 }  // namespace
 
 extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_mesh *meshes, const int32_t *seeds,
                                        const int32_t *seeds_per_mesh, vls_result **out) {
   if (!ctx || !out || n_mesh <= 0 || !meshes || !seeds || !seeds_per_mesh) return VLS_EINVAL;
   *out = nullptr;
+  // launch shapes: explicit options, else the autotuned table of this device / size class
+  TuneEntry tuned;
+  bool have_tuned = false;
+  if (ctx->opt.threads == 0 && ctx->opt.blocks_per_sm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int64_t vt = 0;
+    for (int32_t m = 0, si = 0; m < n_mesh; ++m) {
+      if (seeds_per_mesh[m] < 0) return VLS_EINVAL;
+      vt += (int64_t)std::max<int64_t>(meshes[m].nv, 0) * seeds_per_mesh[m];
+      si += seeds_per_mesh[m];
+    }
+    int vclass = 0;
+    while (vclass < 62 && (int64_t(1) << vclass) < vt) ++vclass;
+    const int prec = (int)ctx->opt.precision;
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      for (const TuneEntry &e : g_tune)
+        if (e.dev == dev && e.vclass == vclass && e.prec == prec) {
+          tuned = e;
+          have_tuned = true;
+        }
+    }
+    if (!have_tuned) {
+      tuned.dev = dev;
+      tuned.vclass = vclass;
+      tuned.prec = prec;
+      autotune(ctx, n_mesh, meshes, seeds, seeds_per_mesh, tuned);
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune.push_back(tuned);
+      have_tuned = true;
+    }
+  }
   vls_result *res = new (std::nothrow) vls_result();
   if (!res) return VLS_ENOMEM;
   // problems (mesh-major, seed-minor); those failing host checks never reach the device
@@ -368,10 +468,16 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
   b.sm_count = ctx->sm;
   // row kernels (one thread per frontier row): small blocks spread a few thousand rows over
   // every SM; group kernels (16 lanes per row): 256-thread blocks
-  b.threads = ctx->opt.threads > 0 ? ctx->opt.threads : 128;
-  b.grid = ctx->sm * (ctx->opt.blocks_per_sm > 0 ? ctx->opt.blocks_per_sm : 16);
-  b.gthreads = 256;
-  b.ggrid = ctx->sm * 4;
+  if (have_tuned) {
+    for (int k = 0; k < KK_COUNT_KINDS; ++k) b.shape[k] = tuned.shape[k];
+    b.hook_variant = tuned.hook_variant;
+  } else {
+    for (int k = 0; k < KK_COUNT_KINDS; ++k) {
+      b.shape[k].threads = ctx->opt.threads;
+      b.shape[k].bps = ctx->opt.blocks_per_sm;
+    }
+  }
+  if (ctx->opt.hook_variant == 1 || ctx->opt.hook_variant == 2) b.hook_variant = ctx->opt.hook_variant;
   configure_initial(b);
   configure_events(b);
   configure_tunnel(b);
@@ -593,16 +699,51 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     // a pass that did not run reports (status -1, stop step 0, first vertex 0)
     std::vector<int32_t> h_tstatus(h_nh, -1), h_tsteps(h_nh, 0), h_tb(h_nh, 0), h_tvoff(h_nh, 0), h_tvn(h_nh, 0);
     std::vector<int32_t> h_tverts;
-    std::vector<long long> h_qupd;
-    if (!pass_h.empty()) {
-      const int32_t NP = (int32_t)pass_h.size();
+    // passes run in chunks whose dense per-pass state (one entry per vertex of the pass's
+    // problem, about 45 B each) fits a bound set by the free device memory
+    int64_t pv_cap = int64_t(1) << 29;
+    {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) pv_cap = std::min<int64_t>(pv_cap, (int64_t)(fr / 2 / 48));
+      // VLS_PASS_VERTS overrides the bound (smaller chunks; the results do not change)
+      if (const char *ev = std::getenv("VLS_PASS_VERTS")) pv_cap = std::atoll(ev);
+      pv_cap = std::max<int64_t>(pv_cap, 1);
+    }
+    // Sec. 3.2: a pass is restricted to the area covered when its handle was found.  A pass
+    // that cannot reach the far side there (the kept handle loop separates that area) runs a
+    // second time on the whole surface (domain step INT32_MAX).
+    std::vector<int32_t> pass_dom(h_nh, 0);
+    for (int32_t h : pass_h) pass_dom[h] = h_hstep[h];
+    for (int round = 0; round < 2 && !pass_h.empty(); ++round) {
+    if (round == 1) {
+      std::vector<int32_t> again;
+      for (int32_t h : pass_h)
+        if (h_tstatus[h] == VLS_ELOOPFAIL && h_tb[h] < 0 && h_hn[h] > 0) {
+          again.push_back(h);
+          pass_dom[h] = INT32_MAX;
+        }
+      pass_h.swap(again);
+    }
+    for (size_t c0 = 0; c0 < pass_h.size();) {
+      size_t c1 = c0;
+      int64_t pv_chunk = 0;
+      while (c1 < pass_h.size()) {
+        const int32_t p = h_hprob[pass_h[c1]];
+        const int64_t n = b.voff[p + 1] - b.voff[p];
+        if (c1 > c0 && pv_chunk + n > pv_cap) break;
+        pv_chunk += n;
+        ++c1;
+      }
+      const std::vector<int32_t> chunk(pass_h.begin() + (std::ptrdiff_t)c0, pass_h.begin() + (std::ptrdiff_t)c1);
+      c0 = c1;
+      const int32_t NP = (int32_t)chunk.size();
       std::vector<int32_t> pbase(NP + 1), pprob(NP), pstep(NP), pcoff(NP), pcn(NP), heoff(NP), hen(NP);
       int64_t PV = 0, ncut = 0;
       for (int32_t q = 0; q < NP; ++q) {
-        const int32_t h = pass_h[q], p = h_hprob[h];
+        const int32_t h = chunk[q], p = h_hprob[h];
         pbase[q] = (int32_t)PV;
         pprob[q] = p;
-        pstep[q] = h_hstep[h];
+        pstep[q] = pass_dom[h];
         heoff[q] = h_hoff[h];
         hen[q] = h_hn[h];
         pcoff[q] = (int32_t)ncut;
@@ -620,7 +761,6 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       if (L.bytes > ctx->arena.cap) {
         // grow: the batch state must survive, so copy it into the new arena
         char *old = ctx->arena.base;
-        const size_t oldcap = ctx->arena.cap;
         char *nb = nullptr;
         CK(cudaMalloc(&nb, L.bytes + L.bytes / 8));
         CK(cudaMemcpyAsync(nb, old, keep, cudaMemcpyDeviceToDevice, st));
@@ -632,7 +772,6 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
         Layout L2{&ctx->arena, false};
         layout_batch(L2, b);
         cudaFree(old);
-        (void)oldcap;
       }
       ctx->arena.used = keep;
       Layout L3{&ctx->arena, false};
@@ -646,6 +785,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       CK(cudaMemcpyAsync(const_cast<int32_t *>(T.pcn), pcn.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
       CK(cudaMemcpyAsync(const_cast<int32_t *>(T.heoff), heoff.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
       CK(cudaMemcpyAsync(const_cast<int32_t *>(T.hen), hen.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
+      b.h2d += (int64_t)sizeof(int32_t) * (7 * NP + 1);
       CK(cudaMemsetAsync(T.flag, 0, (size_t)PV, st));
       if (T.phif) CK(cudaMemsetAsync(T.phif, 0, sizeof(float) * PV, st));
       else CK(cudaMemsetAsync(T.phi, 0, sizeof(double) * PV, st));
@@ -660,8 +800,11 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       CK(cudaMemsetAsync(T.qupd, 0, sizeof(long long) * NP, st));
       CK(cudaMemsetAsync(T.ntverts, 0, sizeof(int32_t), st));
       CK(cudaMemsetAsync(T.tvn, 0, sizeof(int32_t) * NP, st));
-      CK(run_tunnels(b, &tunnel_tau));
+      int32_t chunk_tau = 0;
+      CK(run_tunnels(b, &chunk_tau));
+      tunnel_tau += chunk_tau; // launch accounting: steps summed over chunks
       std::vector<int32_t> qs(NP), qst(NP), qb(NP), tvo(NP), tvn(NP);
+      std::vector<long long> qupd(NP);
       int32_t ntv = 0;
       CK(cudaMemcpyAsync(qs.data(), T.qstatus, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(qst.data(), T.qsteps, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
@@ -669,28 +812,28 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       CK(cudaMemcpyAsync(tvo.data(), T.tvoff, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(tvn.data(), T.tvn, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(&ntv, T.ntverts, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-      h_qupd.resize(NP);
-      CK(cudaMemcpyAsync(h_qupd.data(), T.qupd, sizeof(long long) * NP, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(qupd.data(), T.qupd, sizeof(long long) * NP, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       b.d2h += (int64_t)(5 * sizeof(int32_t) + sizeof(long long)) * NP + (int64_t)sizeof(int32_t);
       ntv = std::min(ntv, T.tvcap);
-      h_tverts.resize(ntv);
-      if (ntv) CK(cudaMemcpyAsync(h_tverts.data(), T.tverts, sizeof(int32_t) * ntv, cudaMemcpyDeviceToHost, st));
+      const size_t tv0 = h_tverts.size();
+      h_tverts.resize(tv0 + (size_t)ntv);
+      if (ntv) CK(cudaMemcpyAsync(h_tverts.data() + tv0, T.tverts, sizeof(int32_t) * ntv, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
       b.d2h += (int64_t)sizeof(int32_t) * ntv;
       for (int32_t q = 0; q < NP; ++q) {
-        const int32_t h = pass_h[q];
+        const int32_t h = chunk[q];
         h_tstatus[h] = qs[q];
         h_tsteps[h] = qst[q];
         h_tb[h] = qb[q] == 0x7fffffff ? -1 : qb[q];
-        h_tvoff[h] = tvo[q];
+        h_tvoff[h] = (int32_t)tv0 + tvo[q];
         h_tvn[h] = tvn[q];
-      }
-      // per-problem pass statistics
-      for (int32_t q = 0; q < NP; ++q) {
+        // per-problem pass statistics
         ProbResult &r = res->p[dev_probs[pprob[q]]];
-        r.stats.pass_updates += h_qupd[q];
+        r.stats.pass_updates += qupd[q];
         r.tunnel_steps = std::max(r.tunnel_steps, qst[q]);
       }
+    }
     }
     CK(cudaEventRecord(ev[3], st));
     // ---- download

@@ -279,6 +279,46 @@ __device__ __forceinline__ void hook_phase(const Dev &d) {
 }
 __global__ void k_band_hook(Dev d) { hook_phase(d); }
 
+// The other union-find variant: one thread per band row unites the row with each qualifying
+// neighbour in turn (neighbour states gathered first).
+__global__ void k_band_hook_row(Dev d) {
+  const int32_t t = __ldcg(d.ctl + CTL_T), cur = t & 1;
+  const int32_t *__restrict__ fv = d.front[cur];
+  const int32_t *__restrict__ fp = d.front[cur] + d.V;
+  const int32_t nF = __ldcg(d.nfront + cur);
+  FOR_ROWS(i, nF) {
+    if (__ldcg(d.pdone + fp[i])) continue;
+    const int32_t v = fv[i];
+    int32_t l;
+    if (!is_band(d, v, l)) continue;
+    const int32_t b = d.rp[v], deg = d.rp[v + 1] - b;
+    if (deg <= 16) {
+      int32_t nu[16], nm[16], nl[16];
+      bool nb[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) nu[j] = (j < deg) ? d.col[b + j] : v;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const bool ok = j < deg && nu[j] < v;
+        nm[j] = ok ? d.fmark[nu[j]] : -1;
+        nl[j] = ok ? d.lay[nu[j]] : 0;
+        nb[j] = ok && ph_band(d, nu[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (nm[j] == t && nl[j] == l && nb[j]) uf_unite(d.uf, nu[j], v);
+    } else {
+      for (int32_t k = b; k < b + deg; ++k) {
+        const int32_t u = d.col[k];
+        if (!VCHK(d.err, u, d.V, 131)) continue;
+        if (u >= v || d.fmark[u] != t) continue;
+        int32_t lu;
+        if (is_band(d, u, lu) && lu == l) uf_unite(d.uf, u, v);
+      }
+    }
+  }
+}
+
 // Component roots per layer.  A layer reaching two roots, or a problem with a live layer
 // that has no root (no band left), sends the step through the split phase.
 __device__ __forceinline__ void count_phase(const Dev &d) {
@@ -533,7 +573,8 @@ cudaError_t build_initial_graph(Batch &b, cudaGraph_t *out) {
     mbody = np.conditional.phGraph_out[0];
     GK(add_merge_nodes(b, mbody));
   }
-  GK(add_kernel(&n_hook, body, &n_if_m, 1, k_band_hook, G(KK_HOOK), T(KK_HOOK), b.d));
+  GK(add_kernel(&n_hook, body, &n_if_m, 1, b.hook_variant == 1 ? k_band_hook_row : k_band_hook, G(KK_HOOK), T(KK_HOOK),
+                b.d));
   GK(add_kernel(&n_cnt, body, &n_hook, 1, k_band_count, G(KK_COUNT), T(KK_COUNT), b.d, H));
   {
     cudaGraphNodeParams np = {};
@@ -570,7 +611,9 @@ cudaError_t initial_step_host(Batch &b) {
   cudaError_t e = merge_phase_host(b);
   if (e != cudaSuccess) return e;
   ps = b.prof.begin(st, KK_HOOK);
-  k_band_hook<<<b.cfg[KK_HOOK].grid, b.cfg[KK_HOOK].threads, 0, st>>>(d); VLS_LAUNCH(b);
+  if (b.hook_variant == 1) k_band_hook_row<<<b.cfg[KK_HOOK].grid, b.cfg[KK_HOOK].threads, 0, st>>>(d);
+  else k_band_hook<<<b.cfg[KK_HOOK].grid, b.cfg[KK_HOOK].threads, 0, st>>>(d);
+  VLS_LAUNCH(b);
   b.prof.end(st, ps);
   ps = b.prof.begin(st, KK_COUNT);
   k_band_count<<<b.cfg[KK_COUNT].grid, b.cfg[KK_COUNT].threads, 0, st>>>(d, H); VLS_LAUNCH(b);
@@ -584,12 +627,11 @@ cudaError_t initial_step_host(Batch &b) {
 }
 
 void configure_initial(Batch &b) {
-  const int rt = b.threads; // row kernels: one thread per frontier row
-  b.cfg[KK_UPDATE] = wave_cfg(b, k_update, rt);
-  b.cfg[KK_APPLY] = wave_cfg(b, k_apply, rt);
-  b.cfg[KK_HOOK] = wave_cfg(b, k_band_hook, rt);
-  b.cfg[KK_COUNT] = wave_cfg(b, k_band_count, rt);
-  b.cfg[KK_FRONTIER] = wave_cfg(b, k_frontier, 256); // 16 lanes per row
+  b.cfg[KK_UPDATE] = row_cfg(b, k_update, KK_UPDATE, 128); // one thread per frontier row
+  b.cfg[KK_APPLY] = row_cfg(b, k_apply, KK_APPLY, 128);
+  b.cfg[KK_HOOK] = b.hook_variant == 1 ? row_cfg(b, k_band_hook_row, KK_HOOK, 128) : row_cfg(b, k_band_hook, KK_HOOK, 256);
+  b.cfg[KK_COUNT] = row_cfg(b, k_band_count, KK_COUNT, 128);
+  b.cfg[KK_FRONTIER] = row_cfg(b, k_frontier, KK_FRONTIER, 256); // 16 lanes per row
 }
 
 cudaError_t final_checks(Batch &b) {

@@ -109,7 +109,7 @@ __device__ void na_scan(const int32_t *cnt, int32_t *rp, int32_t n) {
 }
 
 __global__ void __launch_bounds__(NA_THREADS) k_tunnel_noalloc(unsigned char *scratch, const int32_t *F, int32_t nf,
-                                                                int32_t nv, const int32_t *cover, int32_t step,
+                                                                int32_t nv, const int32_t *cover, int32_t handle_step,
                                                                 const int32_t *edges, int32_t ne, Params P,
                                                                 int32_t max_steps, int32_t *out_verts,
                                                                 int32_t *out_info) {
@@ -162,6 +162,11 @@ __global__ void __launch_bounds__(NA_THREADS) k_tunnel_noalloc(unsigned char *sc
       while (j >= s.rp[v] && s.col[j] > c) { s.col[j + 1] = s.col[j]; --j; }
       s.col[j + 1] = c;
     }
+  // The pass runs on the area covered when the handle was found; when the handle loop
+  // separates that area (the far side is never reached), it runs again on the whole surface.
+  int32_t step = handle_step;
+  const int32_t ncut = 2 * ne;
+  for (int attempt = 0; attempt < 2; ++attempt) {
   // ---- pass state: sources held at 1, targets, cut half-edges
   for (int32_t v = tid; v < nv; v += nth) {
     s.flag[v] = 0;
@@ -186,7 +191,6 @@ __global__ void __launch_bounds__(NA_THREADS) k_tunnel_noalloc(unsigned char *sc
     s.fv[0][atomicAdd(&nfr[0], 1)] = a;
   }
   __syncthreads();
-  const int32_t ncut = 2 * ne;
   if (tid == 0)
     for (int32_t i = 1; i < ncut; ++i) {
       const int32_t x = s.cut[i];
@@ -263,27 +267,43 @@ __global__ void __launch_bounds__(NA_THREADS) k_tunnel_noalloc(unsigned char *sc
     }
   }
   __syncthreads();
+  if (status != VLS_ELOOPFAIL || bstar != 0x7fffffff || ne == 0) break;
+  step = INT32_MAX;
+  __syncthreads();
+  }
   if (tid != 0) return;
   out_info[0] = status;
   out_info[1] = stop;
   out_info[2] = status == VLS_OK ? bstar : (status == -1 ? 0 : -1);
   out_info[3] = 0;
   if (status != VLS_OK) return;
-  // greedy descent on (arrival, id) over kept edges, then closure along the loop
+  // depth-first descent on (arrival raised, arrival, id) over kept edges with steps back from
+  // dead ends, then closure along the loop
   int32_t np = 0, x = bstar;
   s.path[np++] = x;
   s.flag[x] |= NF_VIS;
   while (s.T[x] != 0) {
     const int32_t tx = s.T[x];
-    int32_t best = -1, tb = 0;
+    int32_t best = -1, tb = 0, bup = 0;
     for (int32_t k = s.rp[x]; k < s.rp[x + 1]; ++k) {
       const int32_t u = s.col[k];
       if (!na_kept(s, cover, step, ncut, x, u, k)) continue;
       const int32_t tu = s.T[u];
-      if (tu < 0 || tu > tx || (s.flag[u] & NF_VIS)) continue;
-      if (best < 0 || tu < tb || (tu == tb && u < best)) { best = u; tb = tu; }
+      if (tu < 0 || (s.flag[u] & NF_VIS)) continue;
+      const int32_t up = tu > tx ? 1 : 0;
+      if (best < 0 || up < bup || (up == bup && (tu < tb || (tu == tb && u < best)))) {
+        best = u;
+        tb = tu;
+        bup = up;
+      }
     }
-    if (best < 0 || np >= nv) { out_info[0] = VLS_ELOOPFAIL; return; }
+    if (best < 0) {
+      if (np <= 1) { out_info[0] = VLS_ELOOPFAIL; return; }
+      --np;
+      x = s.path[np - 1];
+      continue;
+    }
+    if (np >= nv) { out_info[0] = VLS_ELOOPFAIL; return; }
     s.flag[best] |= NF_VIS;
     s.path[np++] = best;
     x = best;

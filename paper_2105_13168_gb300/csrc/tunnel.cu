@@ -348,19 +348,32 @@ __global__ void k_ttrace(Dev d, TDev T) {
     path[np++] = x;
     T.flag[base + (x - voff)] |= F_VIS;
     bool fail = false;
+    // depth first: the unvisited reached neighbour of least (arrival raised, arrival, id); from a
+    // dead end, step back along the path
     while (T.T[base + (x - voff)] != 0) {
       const int32_t tx = T.T[base + (x - voff)];
       const int8_t fx = T.flag[base + (x - voff)];
-      int32_t best = -1, tb = 0;
+      int32_t best = -1, tb = 0, bup = 0;
       for (int32_t k = d.rp[x]; k < d.rp[x + 1]; ++k) {
         const int32_t u = d.col[k];
         if (!kept(d, T, q, step, base, voff, fx, u, k)) continue;
         const int32_t iu = base + (u - voff);
         const int32_t tu = T.T[iu];
-        if (tu < 0 || tu > tx || (T.flag[iu] & F_VIS)) continue;
-        if (best < 0 || tu < tb || (tu == tb && u < best)) { best = u; tb = tu; }
+        if (tu < 0 || (T.flag[iu] & F_VIS)) continue;
+        const int32_t up = tu > tx ? 1 : 0;
+        if (best < 0 || up < bup || (up == bup && (tu < tb || (tu == tb && u < best)))) {
+          best = u;
+          tb = tu;
+          bup = up;
+        }
       }
-      if (best < 0 || !VCHK(T.err, np, nvp, 341)) { fail = true; break; }
+      if (best < 0) {
+        if (np <= 1) { fail = true; break; }
+        --np;
+        x = path[np - 1];
+        continue;
+      }
+      if (!VCHK(T.err, np, nvp, 341)) { fail = true; break; }
       T.flag[base + (best - voff)] |= F_VIS;
       path[np++] = best;
       x = best;
@@ -400,9 +413,9 @@ __global__ void k_tctl_set(int32_t *ctl, int32_t idx, int32_t v) { ctl[idx] = v;
 }  // namespace
 
 void configure_tunnel(Batch &b) {
-  b.cfg[KK_TUPDATE] = wave_cfg(b, k_tupdate, b.threads);
-  b.cfg[KK_TAPPLY] = wave_cfg(b, k_tapply, b.threads);
-  b.cfg[KK_TFRONTIER] = wave_cfg(b, k_tfrontier, 256);
+  b.cfg[KK_TUPDATE] = row_cfg(b, k_tupdate, KK_TUPDATE, 128);
+  b.cfg[KK_TAPPLY] = row_cfg(b, k_tapply, KK_TAPPLY, 128);
+  b.cfg[KK_TFRONTIER] = row_cfg(b, k_tfrontier, KK_TFRONTIER, 256);
 }
 
 // Runs all passes of b.td (already laid out by the host): init, F_1, then one graph launch

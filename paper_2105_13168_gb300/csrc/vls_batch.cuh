@@ -103,12 +103,16 @@ struct Batch {
   int32_t P = 0, V = 0, NF = 0, Lcap = 0;
   int64_t nnz = 0;
   int sm_count = 148;
-  int grid = 0, threads = 64;     // row kernels
-  int ggrid = 0, gthreads = 256;  // 16-lanes-per-row kernels and vertex scans
-  // per-kernel launch shape: one resident wave (SM count x resident blocks per SM)
+  // per-kernel launch shape: grid (SM count x blocks per SM) and threads per block
   struct Cfg {
     int grid = 0, threads = 0;
   } cfg[KK_COUNT_KINDS];
+  // requested launch shape per kernel kind: threads per block, blocks per SM (0 = as many as
+  // fit); set from the options or by the autotuner before configure_*()
+  struct Shape {
+    int threads = 0, bps = 0;
+  } shape[KK_COUNT_KINDS];
+  int hook_variant = 2; // band union-find: 1 one thread per band row, 2 sixteen lanes per row
   long long launches = 0;
   Arena *arena = nullptr;
   // host copies of problem tables
@@ -162,6 +166,18 @@ template <class K> inline Batch::Cfg wave_cfg(const Batch &b, K kernel, int thre
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess || nb < 1) nb = 1;
   Batch::Cfg c;
   c.grid = b.sm_count * nb;
+  c.threads = threads;
+  return c;
+}
+// Launch shape of row kernel `kind`: b.shape[kind] (threads, blocks per SM) clamped to what fits
+// on an SM; dflt_threads when no shape was requested.
+template <class K> inline Batch::Cfg row_cfg(const Batch &b, K kernel, int kind, int dflt_threads) {
+  const int threads = b.shape[kind].threads > 0 ? b.shape[kind].threads : dflt_threads;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0) != cudaSuccess || nb < 1) nb = 1;
+  const int bps = b.shape[kind].bps > 0 && b.shape[kind].bps < nb ? b.shape[kind].bps : nb;
+  Batch::Cfg c;
+  c.grid = b.sm_count * bps;
   c.threads = threads;
   return c;
 }

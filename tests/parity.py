@@ -6,6 +6,9 @@ different order on the GPU, compared to 1e-12 relative of the coordinate scale."
 import numpy as np
 
 FP64_REL = 1e-12
+# FP32 form: value tolerance, and loop-point / Reeb-position tolerance (relative to coordinates)
+FP32_TOL = 2e-6
+GEOM_TOL = 1e-4
 
 
 def assert_close(a, b, rel=FP64_REL, what=""):
@@ -47,3 +50,52 @@ def assert_parity(g, o, state=True, records=True):
         assert np.array_equal(g.layer, o.layer)
         assert np.array_equal(g.cover, o.cover)
         assert_close(g.phi, o.phi, what="phi")
+
+
+def close(a, b, rel, what):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    assert a.shape == b.shape, (what, a.shape, b.shape)
+    if a.size == 0:
+        return 0.0
+    scale = max(1.0, float(np.abs(b).max()))
+    err = float(np.abs(a - b).max())
+    assert err <= rel * scale, f"{what}: max abs err {err:.3e} > {rel:.1e} * {scale:.3e}"
+    return err
+
+
+def assert_fp32_parity(g, o):
+    """Exact integer results, bounded record / cover differences, values within FP32_TOL while
+    no decision differed.  Returns (max value error or None, differing record steps, differing
+    cover steps)."""
+    assert g.status == o.status, (g.status_name, o.status_name)
+    assert g.genus == o.genus
+    assert g.events() == o.events()
+    assert np.array_equal(g.layers, o.layers)
+    assert len(g.records) == len(o.records), (len(g.records), len(o.records))
+    rec_bad = int((g.records != o.records).any(axis=1).sum())
+    # a node position is the mean of an event step's band: one vertex more or less in that band
+    # (a differing record) moves it by about the band's extent over its size
+    close(g.node_pos, o.node_pos, GEOM_TOL if rec_bad == 0 else 1e-2, "reeb node positions")
+    assert len(g.handles) == len(o.handles)
+    for i, (hg, ho) in enumerate(zip(g.handles, o.handles)):
+        assert (hg.step, hg.layer, hg.node) == (ho.step, ho.layer, ho.node), f"handle {i}"
+        assert np.array_equal(hg.edges, ho.edges), f"handle {i} crossing edges differ"
+        assert np.array_equal(hg.verts, ho.verts), f"handle {i} vertices differ"
+        close(hg.points, ho.points, GEOM_TOL, f"handle {i} points")
+        assert abs(hg.length - ho.length) <= GEOM_TOL * max(1.0, ho.length) * 10
+    assert len(g.tunnels) == len(o.tunnels)
+    for i, (tg, to) in enumerate(zip(g.tunnels, o.tunnels)):
+        assert (tg.status, tg.stop_step, tg.bstar) == (to.status, to.stop_step, to.bstar), f"tunnel {i}"
+        assert np.array_equal(tg.verts, to.verts), f"tunnel {i} differs"
+    assert np.array_equal(g.layer, o.layer)
+    cov_bad = int((g.cover != o.cover).sum())
+    assert rec_bad <= 0.02 * max(1, len(o.records)), f"{rec_bad} of {len(o.records)} step records differ"
+    assert cov_bad <= 1e-3 * g.cover.size, f"{cov_bad} cover steps differ"
+    err = None
+    if rec_bad == 0:
+        err = float(np.abs(g.phi - o.phi).max()) if g.phi.size else 0.0
+        assert err <= FP32_TOL, f"phi max abs err {err:.3e} > {FP32_TOL:.1e}"
+    return err, rec_bad, cov_bad
+
+

@@ -133,3 +133,39 @@ def test_stats_are_consistent(vls):
     assert g.stats["merges"] == o.counters[3] and g.stats["splits"] == o.counters[4]
     assert g.stats["ends"] == o.counters[5] and g.stats["layers"] == o.counters[6]
     assert g.stats["steps"] == o.steps
+
+
+@pytest.mark.parametrize("threads,bps,variant", [(64, 1, 1), (256, 64, 2), (128, 2, 1), (128, 4, 2)])
+def test_launch_shapes_and_union_find_variants(vls, threads, bps, variant):
+    """Every launch shape and both band union-find variants give the oracle's results (the
+    autotuner may pick any of them)."""
+    m = meshgen.tube_chain(2, 64)
+    s = meshgen.seed_vertex(1, m.nv)
+    g = run_gpu(vls, [(m, [s])], threads=threads, blocks_per_sm=bps, hook_variant=variant)[0]
+    assert_parity(g, run_orc(m, s))
+
+
+def test_tunnel_passes_in_chunks(vls, monkeypatch):
+    """Tunnel passes split into memory-bounded chunks (here one pass per chunk) give the same
+    loops as all passes at once."""
+    m = meshgen.tube_chain(3, 80)
+    s = meshgen.seed_vertex(0, m.nv)
+    whole = run_gpu(vls, [(m, [s, s + 1])])
+    monkeypatch.setenv("VLS_PASS_VERTS", "1")
+    chunked = run_gpu(vls, [(m, [s, s + 1])])
+    for a, b in zip(whole, chunked):
+        assert [t.verts.tolist() for t in a.tunnels] == [t.verts.tolist() for t in b.tunnels]
+        assert [(t.status, t.stop_step, t.bstar) for t in a.tunnels] == [(t.status, t.stop_step, t.bstar) for t in b.tunnels]
+        assert len(a.tunnels) == 3
+    assert_parity(chunked[0], run_orc(m, s))
+
+
+@pytest.mark.parametrize("mesh,seed", [(44, 2), (51, 2)])
+def test_tunnel_pass_fallbacks(vls, mesh, seed):
+    """Batch mesh 44 seed 2: a handle loop separates the area covered at its step and the pass
+    runs again on the whole surface.  Batch mesh 51 seed 2: a pass front stalls and the problem
+    ends ELOOPFAIL.  Both exactly as the oracle."""
+    m, seeds = meshgen.batch_problem(mesh)
+    s = seeds[seed]
+    g = run_gpu(vls, [(m, [s])])[0]
+    assert_parity(g, run_orc(m, s))

@@ -1,0 +1,157 @@
+"""The Schwarz-P, batched and gyroid workloads on the GPU, each in one batched call (the launch
+configuration the benchmark uses).
+
+- **Oracle parity** where the oracle finishes in seconds:
+  - the Schwarz-P solid at grid scale 0.35;
+  - a sample of 16 problems of the full batch;
+  - a 2-period gyroid at the full workload's sampling density.
+- **Properties at full size**, which hold at any size:
+  - every problem OK;
+  - as many handle loops and tunnel loops as the genus from the Euler characteristic;
+  - the Reeb graph's cycle rank equal to the genus;
+  - the FP32 form identical to the FP64 form on every event and loop.
+
+The oracle runs in a spawn process pool started before the first GPU call.
+"""
+import concurrent.futures as cf
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import meshgen
+from parity import assert_fp32_parity, assert_parity
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+BATCH_SAMPLE = list(range(0, 1024, 64))  # 16 problems spread over the batch
+
+
+def _oracle_problem(args):
+    import meshgen as mg
+    import oracle as orc
+
+    kind, idx = args
+    if kind == "batch":
+        m, ss = mg.batch_problem(idx // 4)
+        s = ss[idx % 4]
+    elif kind == "schwarz":
+        m, ss = mg.workload(3, 0.35)[0]
+        s = ss[0]
+    else:  # gyroid, 2 periods at the full workload's grid density
+        m = mg.jitter(mg.gyroid(2, 76), 0.05, 5)
+        s = mg.seed_vertex(0, m.nv)
+    return orc.detect(m, s, record_steps=1)
+
+
+@pytest.fixture(scope="module")
+def oracle_results():
+    jobs = [("batch", i) for i in BATCH_SAMPLE] + [("schwarz", 0), ("gyroid", 0)]
+    with cf.ProcessPoolExecutor(max_workers=8, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_problem, jobs))
+    return {"batch": res[:len(BATCH_SAMPLE)], "schwarz": res[-2], "gyroid": res[-1]}
+
+
+@pytest.fixture(scope="module")
+def vls(oracle_results):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_13168_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_2105_13168_gb300 as v
+
+    v.load()
+    return v
+
+
+def run(vls, problems, precision, **kw):
+    import torch
+
+    dev = torch.device("cuda", 0)
+    meshes = [(torch.from_numpy(m.X).to(dev), torch.from_numpy(m.F).to(dev)) for m, _ in problems]
+    ctx = vls.vls_create(vls.vls_default_options(precision=precision, **kw))
+    try:
+        res = vls.vls_detect_batch(ctx, meshes, [s for _, s in problems], device=True)
+        try:
+            return vls.read_result(res)
+        finally:
+            vls.vls_result_free(res)
+    finally:
+        vls.vls_destroy(ctx)
+
+
+def check_properties(out, genera, exact_genus=True):
+    """Every problem OK, one tunnel loop per handle loop, Reeb cycle rank = handle count, and
+    the handle count equal to the genus -- or, where handles narrower than the diffuse band
+    (about 4 edges) are not resolved (exact_genus=False), at most the genus."""
+    assert len(out) == len(genera)
+    for i, (p, g) in enumerate(zip(out, genera)):
+        assert p.status == 0, (i, p.status_name)
+        assert p.genus == g
+        nh = len(p.handles)
+        assert len(p.tunnels) == nh and all(t.status == 0 for t in p.tunnels), i
+        assert p.reeb_cycle_rank() == nh, (i, p.reeb_cycle_rank(), nh)
+        assert (nh == g) if exact_genus else (0 < nh <= g), (i, nh, g)
+
+
+def same_integer_results(a, b):
+    assert a.status == b.status and a.events() == b.events()
+    assert np.array_equal(a.layers, b.layers)
+    assert [(h.step, h.layer) for h in a.handles] == [(h.step, h.layer) for h in b.handles]
+    assert all(np.array_equal(x.edges, y.edges) and np.array_equal(x.verts, y.verts) for x, y in zip(a.handles, b.handles))
+    assert all(np.array_equal(x.verts, y.verts) for x, y in zip(a.tunnels, b.tunnels))
+
+
+def test_schwarz_p_full_size(vls):
+    probs = meshgen.workload(3)
+    m = probs[0][0]
+    assert m.nf > 5_000_000 and m.genus() == 81
+    f32 = run(vls, probs, "fp32")
+    f64 = run(vls, probs, "fp64")
+    check_properties(f32, [81], exact_genus=False)
+    check_properties(f64, [81], exact_genus=False)
+    same_integer_results(f32[0], f64[0])
+    print(f"Schwarz-P full size: {len(f32[0].handles)} handle and tunnel loops of genus 81")
+
+
+def test_schwarz_p_oracle_parity(vls, oracle_results):
+    o = oracle_results["schwarz"]
+    probs = meshgen.workload(3, 0.35)
+    assert o.status == 0 and 0 < len(o.handles) <= probs[0][0].genus()
+    g64 = run(vls, probs, "fp64", keep_state=1, record_steps=1)[0]
+    assert_parity(g64, o)
+    g32 = run(vls, probs, "fp32", keep_state=1, record_steps=1)[0]
+    assert_fp32_parity(g32, o)
+
+
+def test_batch_full_size(vls, oracle_results):
+    probs = meshgen.workload(4)
+    genera = [m.genus() for m, ss in probs for _ in ss]
+    assert len(genera) == 1024 and min(genera) == 1 and max(genera) == 20
+    out = run(vls, probs, "fp32", keep_state=1, record_steps=1)
+    check_properties(out, genera)
+    for i, o in zip(BATCH_SAMPLE, oracle_results["batch"]):
+        assert_fp32_parity(out[i], o)
+    out64 = run(vls, probs, "fp64", keep_state=1, record_steps=1)
+    for i, o in zip(BATCH_SAMPLE, oracle_results["batch"]):
+        assert_parity(out64[i], o)
+
+
+def test_gyroid_full_size(vls):
+    probs = meshgen.workload(5)
+    m = probs[0][0]
+    assert m.nf > 20_000_000
+    out = run(vls, probs, "fp32")
+    check_properties(out, [m.genus()], exact_genus=False)
+    print(f"gyroid full size: {len(out[0].handles)} handle and tunnel loops of genus {m.genus()}")
+
+
+def test_gyroid_oracle_parity(vls, oracle_results):
+    o = oracle_results["gyroid"]
+    m = meshgen.jitter(meshgen.gyroid(2, 76), 0.05, 5)
+    s = meshgen.seed_vertex(0, m.nv)
+    assert o.status == 0 and 10 < len(o.handles) <= m.genus()
+    assert_parity(run(vls, [(m, [s])], "fp64", keep_state=1, record_steps=1)[0], o)
+    assert_fp32_parity(run(vls, [(m, [s])], "fp32", keep_state=1, record_steps=1)[0], o)

@@ -350,3 +350,46 @@ def test_homology_checker_brute_force_gf2():
         assert brute_null == (not c.any())
         assert topo.primal_is_null(z.astype(np.uint8)) == brute_null
         assert (not topo.class_primal(z.astype(np.uint8)).any()) == brute_null
+
+
+def _separated_in_covered_area(m, cover, h):
+    """True if cutting handle loop h splits the area covered by its step so that no kept path
+    joins the loop's two sides (breadth-first search on the cut, restricted graph)."""
+    from collections import deque
+
+    nbr = [set() for _ in range(m.nv)]
+    for f in m.F:
+        for k in range(3):
+            a, b = int(f[k]), int(f[(k + 1) % 3])
+            nbr[a].add(b)
+            nbr[b].add(a)
+    e = h.edges.reshape(-1, 2)
+    cut = {(int(a), int(b)) for a, b in e} | {(int(b), int(a)) for a, b in e}
+    dom = (cover >= 0) & (cover <= h.step)
+    src, tgt = {int(a) for a, _ in e}, {int(b) for _, b in e}
+    seen, q = set(src), deque(src)
+    while q:
+        v = q.popleft()
+        for u in nbr[v]:
+            if dom[u] and u not in seen and (v, u) not in cut:
+                seen.add(u)
+                q.append(u)
+    return not (seen & tgt)
+
+
+def test_tunnel_pass_leaves_a_separated_covered_area():
+    """Batch mesh 44 (4 coarse tori), seed 2: the loop kept at the step-226 merge separates the
+    area covered by then (Sec. 3.2 restricts the pass to it), so the pass runs again on the whole
+    surface; every tunnel loop is then a non-contractible cycle crossing its handle loop an odd
+    number of times."""
+    m, seeds = meshgen.batch_problem(44)
+    r = oracle.detect(m, seeds[2])
+    assert r.status == OK and len(r.handles) == len(r.tunnels) == m.genus() == 4
+    assert [_separated_in_covered_area(m, r.cover, h) for h in r.handles] == [False, True, False, False]
+    topo = Topo(m.F, m.nv)
+    for h, t in zip(r.handles, r.tunnels):
+        assert t.status == OK
+        x = topo.crossing_edges(h.edges)
+        z = topo.vertex_cycle_edges(t.verts)
+        assert topo.is_primal_cycle(z) and not topo.primal_is_null(z) and topo.cut_connected_primal(z)
+        assert int((x & z).sum()) % 2 == 1
