@@ -215,6 +215,8 @@ void layout_batch(Layout &L, Batch &b) {
   d.lprob = L.take<int32_t>(Lc);
   d.front[0] = L.take<int32_t>(2 * V);
   d.front[1] = L.take<int32_t>(2 * V);
+  d.fseg[0] = L.take<int32_t>(V);
+  d.fseg[1] = L.take<int32_t>(V);
   d.nfront = L.take<int32_t>(2);
   d.onl = L.take<int32_t>(V);
   d.olay = L.take<int32_t>(KMAX * V);
@@ -317,10 +319,20 @@ __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
 
-#define CK(x)                                  \
-  do {                                         \
-    cudaError_t _e = (x);                      \
-    if (_e != cudaSuccess) { err = _e; goto fail; } \
+// VLS_DEBUG=1 reports the first failing runtime call of a batch on stderr
+bool debug_on() {
+  const char *e = std::getenv("VLS_DEBUG");
+  return e && e[0] == '1';
+}
+#define CK(x)                                                                                     \
+  do {                                                                                            \
+    cudaError_t _e = (x);                                                                         \
+    if (_e != cudaSuccess) {                                                                      \
+      if (debug_on()) std::fprintf(stderr, "vls: %s failed at api.cu:%d: %s\n", #x, __LINE__,      \
+                                   cudaGetErrorString(_e));                                       \
+      err = _e;                                                                                   \
+      goto fail;                                                                                  \
+    }                                                                                             \
   } while (0)
 
 int64_t *g_d2h_counter = nullptr; // bytes downloaded by the call in progress (single-threaded ctx)
@@ -701,7 +713,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     std::vector<int32_t> h_tverts;
     // passes run in chunks whose dense per-pass state (one entry per vertex of the pass's
     // problem, about 45 B each) fits a bound set by the free device memory
-    int64_t pv_cap = int64_t(1) << 29;
+    int64_t pv_cap = (int64_t(1) << 30) - (int64_t(1) << 20); // pass-vertex ids stay below INT32_MAX / 2
     {
       size_t fr = 0, tot = 0;
       if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) pv_cap = std::min<int64_t>(pv_cap, (int64_t)(fr / 2 / 48));
@@ -713,6 +725,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     // that cannot reach the far side there (the kept handle loop separates that area) runs a
     // second time on the whole surface (domain step INT32_MAX).
     std::vector<int32_t> pass_dom(h_nh, 0);
+    const size_t keep_batch = ctx->arena.used;
     for (int32_t h : pass_h) pass_dom[h] = h_hstep[h];
     for (int round = 0; round < 2 && !pass_h.empty(); ++round) {
     if (round == 1) {
@@ -752,9 +765,13 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
         PV += b.voff[p + 1] - b.voff[p];
       }
       pbase[NP] = (int32_t)PV;
-      if (PV >= INT32_MAX / 2) { err = cudaErrorMemoryAllocation; goto fail; }
+      if (PV >= INT32_MAX / 2) {
+        if (debug_on()) std::fprintf(stderr, "vls: tunnel chunk of %lld pass-vertices\n", (long long)PV);
+        err = cudaErrorMemoryAllocation;
+        goto fail;
+      }
       // the tunnel state lives after the batch state in the arena
-      const size_t keep = ctx->arena.used;
+      const size_t keep = keep_batch; // every chunk's tunnel state starts after the batch state
       Layout L{&ctx->arena, true};
       L.bytes = keep;
       layout_tunnels(L, b, NP, PV, ncut);
@@ -1011,7 +1028,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       ProbResult &r = res->p[dev_probs[q]];
       if (r.status == VLS_OK)
         for (auto &T : r.tunnels)
-          if (T.info[0] != VLS_OK) { r.status = T.info[0]; break; }
+          if (T.info[0] > 0) { r.status = T.info[0]; break; } // -1: the pass did not run
     }
   }
   for (int i = 0; i < 5; ++i)

@@ -183,9 +183,6 @@ __global__ void __launch_bounds__(1024) k_trace(Dev d, Params P) {
   const int32_t tb = blockIdx.x;
   if (tb >= *d.ntrace) return;
   const int32_t t = d.ctl[CTL_T], cur = t & 1;
-  const int32_t *__restrict__ fv = d.front[cur];
-  const int32_t *__restrict__ fp = d.front[cur] + d.V;
-  const int32_t *nF_ptr = d.nfront + cur;
   const int32_t g = d.tgroup[tb], l = d.tlayer[tb], p = d.gprob[g];
   const double th = P.theta;
   unsigned long long *key = d.tkey + (int64_t)tb * TRACE_CAP;
@@ -199,10 +196,11 @@ __global__ void __launch_bounds__(1024) k_trace(Dev d, Params P) {
   __shared__ unsigned long long best;
   if (threadIdx.x == 0) { n = 0; best = 0ull; }
   __syncthreads();
-  const int32_t nF = *nF_ptr;
-  for (int32_t i = threadIdx.x; i < nF; i += blockDim.x) {
-    if (fp[i] != p) continue;
-    const int32_t v = fv[i];
+  // this problem's frontier rows (the isoline of l lies in their closed neighbourhood)
+  const int32_t *__restrict__ seg = d.fseg[cur] + d.voff[p];
+  const int32_t ns = d.pfront[(size_t)cur * d.P + p];
+  for (int32_t j = threadIdx.x; j < ns; j += blockDim.x) {
+    const int32_t v = seg[j];
     const double pv = psi_iso(d, v, l);
     const bool hv = holds(d, v, l);
     for (int32_t k = d.rp[v]; k < d.rp[v + 1]; ++k) {
@@ -356,9 +354,6 @@ __global__ void __launch_bounds__(1024) k_merge_finish(Dev d, Params P) {
   if (ng == 0) return;
   const int32_t t = d.ctl[CTL_T], cur = t & 1;
   const int32_t *__restrict__ fv = d.front[cur];
-  const int32_t *__restrict__ fp = d.front[cur] + d.V;
-  const int32_t *nF_ptr = d.nfront + cur;
-  const int32_t nF = *nF_ptr;
   const int32_t ntr = *d.ntrace;
   const double th = P.theta;
   __shared__ int32_t s_first, s_drop, s_eoff, s_hidx, s_N, s_nodeloc;
@@ -384,9 +379,10 @@ __global__ void __launch_bounds__(1024) k_merge_finish(Dev d, Params P) {
     {
       double acc[3] = {0.0, 0.0, 0.0};
       int32_t cnt = 0;
-      for (int32_t i = threadIdx.x; i < nF; i += blockDim.x) {
-        if (fp[i] != p) continue;
-        const int32_t v = fv[i];
+      const int32_t *__restrict__ seg = d.fseg[cur] + d.voff[p];
+      const int32_t ns = d.pfront[(size_t)cur * d.P + p];
+      for (int32_t j = threadIdx.x; j < ns; j += blockDim.x) {
+        const int32_t v = seg[j];
         bool inb = false;
         for (int32_t j = 0; j < nm; ++j) inb |= in_band_of(d, v, mem[j]);
         if (inb) {
@@ -494,13 +490,21 @@ __global__ void __launch_bounds__(1024) k_merge_finish(Dev d, Params P) {
   for (int32_t c = threadIdx.x; c < nc; c += blockDim.x) d.multi[fv[d.coll[c]]] = -1;
 }
 
+// Literal relabel (Sec. 3.1: the merged layers' entries move to the new layer), over the vertex
+// ranges of the problems that merged this step only.
 __global__ void k_relabel(Dev d) {
-  if (*d.ngroups == 0) return;
-  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < d.V; v += gridDim.x * blockDim.x) {
-    const int32_t l = d.lay[v];
-    if (l != 0) {
-      const int32_t f = d.lfwd[l];
-      if (f != 0) d.lay[v] = f;
+  const int32_t ng = *d.ngroups;
+  for (int32_t g = 0; g < ng; ++g) {
+    const int32_t p = d.gprob[g];
+    bool seen = false;
+    for (int32_t h = 0; h < g; ++h) seen |= d.gprob[h] == p;
+    if (seen) continue;
+    for (int32_t v = d.voff[p] + blockIdx.x * blockDim.x + threadIdx.x; v < d.voff[p + 1]; v += gridDim.x * blockDim.x) {
+      const int32_t l = d.lay[v];
+      if (l != 0) {
+        const int32_t f = d.lfwd[l];
+        if (f != 0) d.lay[v] = f;
+      }
     }
   }
 }
@@ -510,10 +514,9 @@ __global__ void __launch_bounds__(256) k_split(Dev d) {
   const int32_t p = blockIdx.x;
   if (p >= d.P || d.pdone[p]) return;
   const int32_t t = d.ctl[CTL_T], cur = t & 1;
-  const int32_t *__restrict__ fv = d.front[cur];
-  const int32_t *__restrict__ fp = d.front[cur] + d.V;
-  const int32_t *nF_ptr = d.nfront + cur;
-  const int32_t nF = *nF_ptr;
+  // this problem's frontier rows
+  const int32_t *__restrict__ seg = d.fseg[cur] + d.voff[p];
+  const int32_t ns = d.pfront[(size_t)cur * d.P + p];
   constexpr int MAXC = 64;
   __shared__ int32_t roots[MAXC], child[MAXC];
   __shared__ int32_t s_c, s_nroot, s_nodeloc, s_lc;
@@ -537,9 +540,9 @@ __global__ void __launch_bounds__(256) k_split(Dev d) {
     int32_t cnt = 0;
     if (c == 0) {
       // extinction: mean of this step's rows that hold l
-      for (int32_t i = threadIdx.x; i < nF; i += blockDim.x)
-        if (fp[i] == p && d.lay[fv[i]] == l) {
-          for (int q = 0; q < 3; ++q) acc[q] += d.X[3 * (int64_t)fv[i] + q];
+      for (int32_t j = threadIdx.x; j < ns; j += blockDim.x)
+        if (d.lay[seg[j]] == l) {
+          for (int q = 0; q < 3; ++q) acc[q] += d.X[3 * (int64_t)seg[j] + q];
           ++cnt;
         }
       block_sum3(acc, cnt, s_pos, &s_cnt);
@@ -557,9 +560,8 @@ __global__ void __launch_bounds__(256) k_split(Dev d) {
       continue;
     }
     // split: collect the component roots (smallest vertex of each component)
-    for (int32_t i = threadIdx.x; i < nF; i += blockDim.x) {
-      if (fp[i] != p) continue;
-      const int32_t v = fv[i];
+    for (int32_t j = threadIdx.x; j < ns; j += blockDim.x) {
+      const int32_t v = seg[j];
       if (d.lay[v] != l) continue;
       if (!ph_band(d, v)) continue;
       for (int q = 0; q < 3; ++q) acc[q] += d.X[3 * (int64_t)v + q];
@@ -591,9 +593,8 @@ __global__ void __launch_bounds__(256) k_split(Dev d) {
     }
     __syncthreads();
     const int32_t nr = s_nroot;
-    for (int32_t i = threadIdx.x; i < nF; i += blockDim.x) {
-      if (fp[i] != p) continue;
-      const int32_t v = fv[i];
+    for (int32_t j = threadIdx.x; j < ns; j += blockDim.x) {
+      const int32_t v = seg[j];
       if (d.lay[v] != l) continue;
       if (!ph_band(d, v)) continue;
       const int32_t r = uf_find(d.uf, v);

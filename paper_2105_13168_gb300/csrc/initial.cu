@@ -384,13 +384,17 @@ __device__ __forceinline__ void frontier_phase(const Dev &d) {
   int32_t *pcount_next = d.pfront + (size_t)nxt * d.P;
   const int32_t lane = threadIdx.x & 15;
   const unsigned half = 0xFFFFu << (threadIdx.x & 16);
+  int32_t *__restrict__ seg_out = d.fseg[nxt];
   auto add = [&](int32_t u, int32_t p) {
     if (atomicExch(&d.stamp[u], tnext) == tnext) return;
-    const int32_t s = warp_append(nN_ptr, pcount_next, p);
+    int32_t ks;
+    const int32_t s = warp_append(nN_ptr, pcount_next, p, &ks);
     if (!VCHK(d.err, s, d.V, 121)) return;
     nv_out[s] = u;
     np_out[s] = p;
     d.fmark[u] = tnext;
+    const int32_t j = d.voff[p] + ks;
+    if (VCHK(d.err, j, d.voff[p + 1], 122)) seg_out[j] = u;
   };
   FOR_ROWS16(i, nF) {
     const int32_t p = fp[i];

@@ -83,6 +83,8 @@ struct Dev {
   // frontier lists (double buffered) and per-row outputs
   int32_t *front[2];
   int32_t *nfront;   // [2]
+  int32_t *fseg[2];  // [V] per step parity: the frontier's vertices grouped by problem (problem p's
+                     // pfront[p] vertices at fseg[voff[p]..]) for kernels that work per problem
   int32_t *onl;      // [Vcap] layers in the new row
   int32_t *olay;     // [Vcap * KMAX]
   double *ophi;      // [Vcap * KMAX]
@@ -362,15 +364,19 @@ __device__ __forceinline__ void uf_unite(int32_t *par, int32_t a, int32_t b) {
 
 // Append to a list shared by the whole grid with one atomic per warp (the lanes that reach this
 // call together), and bump a per-key counter with one atomic per key present in the warp.
-// Returns this lane's slot.  Must be called only by lanes that append.
-__device__ __forceinline__ int32_t warp_append(int32_t *counter, int32_t *key_counts, int32_t key) {
+// Returns this lane's slot; *key_slot (if given) receives the lane's position among its key's
+// entries.  Must be called only by lanes that append.
+__device__ __forceinline__ int32_t warp_append(int32_t *counter, int32_t *key_counts, int32_t key,
+                                               int32_t *key_slot = nullptr) {
   namespace cg = cooperative_groups;
   cg::coalesced_group g = cg::coalesced_threads();
   int32_t base = 0;
   if (g.thread_rank() == 0) base = atomicAdd(counter, (int32_t)g.size());
   base = g.shfl(base, 0) + (int32_t)g.thread_rank();
   cg::coalesced_group kg = cg::labeled_partition(g, key);
-  if (kg.thread_rank() == 0) atomicAdd(&key_counts[key], (int32_t)kg.size());
+  int32_t kb = 0;
+  if (kg.thread_rank() == 0) kb = atomicAdd(&key_counts[key], (int32_t)kg.size());
+  if (key_slot) *key_slot = kg.shfl(kb, 0) + (int32_t)kg.thread_rank();
   return base;
 }
 

@@ -169,3 +169,12 @@ def test_tunnel_pass_fallbacks(vls, mesh, seed):
     s = seeds[seed]
     g = run_gpu(vls, [(m, [s])])[0]
     assert_parity(g, run_orc(m, s))
+
+
+def test_tunnels_off_keeps_status_ok(vls):
+    """With the tunnel passes switched off a finished problem is OK, its tunnel records say
+    'did not run' (status -1)."""
+    m = meshgen.tube_chain(2, 56)
+    g = run_gpu(vls, [(m, [meshgen.seed_vertex(0, m.nv)])], tunnels=0)[0]
+    assert g.status == 0 and len(g.handles) == 2
+    assert all(t.status == -1 for t in g.tunnels)
