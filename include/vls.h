@@ -95,7 +95,7 @@ typedef struct {
   int32_t profile;          /* 1: time every frontier-update launch with CUDA events (vls_stats) */
   int32_t host_loop;        /* 1: launch each step's kernels from the host instead of running the
                                step loops as device-driven CUDA graphs (same results) */
-  int32_t hook_variant;     /* band union-find: 1 one thread per band row, 2 sixteen lanes per
+  int32_t hook_variant;     /* band union-find: 1 one thread per band row, 2 a group of 8 lanes per
                                band row (one neighbour each), 0 autotuned or 2 (same results) */
 } vls_options;
 

@@ -352,7 +352,7 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 // ---- autotuner
 // Launch shapes chosen by measurement, kept per device, precision and batch size class (total
 // vertices rounded up to a power of two) for the life of the process.  Until a candidate wins,
-// every kernel uses 16-lane hooking and as many blocks per SM as fit.
+// every kernel uses lane-group hooking and as many blocks per SM as fit.
 struct TuneEntry {
   int dev = -1, vclass = -1, prec = -1;
   Batch::Shape shape[KK_COUNT_KINDS];
@@ -479,7 +479,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
   b.arena = &ctx->arena;
   b.sm_count = ctx->sm;
   // row kernels (one thread per frontier row): small blocks spread a few thousand rows over
-  // every SM; group kernels (16 lanes per row): 256-thread blocks
+  // every SM; lane-group kernels (GL lanes per row): 256-thread blocks
   if (have_tuned) {
     for (int k = 0; k < KK_COUNT_KINDS; ++k) b.shape[k] = tuned.shape[k];
     b.hook_variant = tuned.hook_variant;

@@ -349,9 +349,16 @@ __global__ void __launch_bounds__(1024) k_trace(Dev d, Params P) {
 }
 
 // ------------------------------------------------------------------ merge finish
+// One block per problem that merges this step (the block of the problem's first group): its
+// groups in order, so layer ids, Reeb nodes and handle loops of a problem are created in the same
+// order as by the oracle; problems proceed in parallel.
 __global__ void __launch_bounds__(1024) k_merge_finish(Dev d, Params P) {
   const int32_t ng = *d.ngroups;
-  if (ng == 0) return;
+  const int32_t b0 = blockIdx.x;
+  if (b0 >= ng) return;
+  const int32_t pb = d.gprob[b0];
+  for (int32_t h = 0; h < b0; ++h)
+    if (d.gprob[h] == pb) return; // an earlier block owns this problem
   const int32_t t = d.ctl[CTL_T], cur = t & 1;
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t ntr = *d.ntrace;
@@ -359,8 +366,9 @@ __global__ void __launch_bounds__(1024) k_merge_finish(Dev d, Params P) {
   __shared__ int32_t s_first, s_drop, s_eoff, s_hidx, s_N, s_nodeloc;
   __shared__ double s_pos[3];
   __shared__ int32_t s_cnt;
-  for (int32_t g = 0; g < ng; ++g) {
+  for (int32_t g = b0; g < ng; ++g) {
     const int32_t p = d.gprob[g];
+    if (p != pb) continue;
     const int32_t nm = d.gnmem[g];
     const int32_t *mem = d.gmem + g * MAX_GROUP;
     if (threadIdx.x == 0) {
@@ -485,15 +493,18 @@ __global__ void __launch_bounds__(1024) k_merge_finish(Dev d, Params P) {
     }
     __syncthreads();
   }
-  // collision rows are single-layer again
-  const int32_t nc = *d.ncoll;
-  for (int32_t c = threadIdx.x; c < nc; c += blockDim.x) d.multi[fv[d.coll[c]]] = -1;
 }
 
 // Literal relabel (Sec. 3.1: the merged layers' entries move to the new layer), over the vertex
 // ranges of the problems that merged this step only.
 __global__ void k_relabel(Dev d) {
   const int32_t ng = *d.ngroups;
+  // collision rows are single-layer again
+  {
+    const int32_t *__restrict__ fv = d.front[d.ctl[CTL_T] & 1];
+    const int32_t nc = *d.ncoll;
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) d.multi[fv[d.coll[c]]] = -1;
+  }
   for (int32_t g = 0; g < ng; ++g) {
     const int32_t p = d.gprob[g];
     bool seen = false;
@@ -616,7 +627,7 @@ cudaError_t add_merge_nodes(Batch &b, cudaGraph_t g) {
   cudaGraphNode_t n0, n1, n2, n3;
   cudaError_t e = add_kernel(&n0, g, nullptr, 0, k_merge_groups, dim3(1), dim3(32), d, luf, touched);
   if (e == cudaSuccess) e = add_kernel(&n1, g, &n0, 1, k_trace, dim3(MAX_TRACES), dim3(1024), d, b.prm);
-  if (e == cudaSuccess) e = add_kernel(&n2, g, &n1, 1, k_merge_finish, dim3(1), dim3(1024), d, b.prm);
+  if (e == cudaSuccess) e = add_kernel(&n2, g, &n1, 1, k_merge_finish, dim3(MAX_TRACES), dim3(1024), d, b.prm);
   if (e == cudaSuccess) e = add_kernel(&n3, g, &n2, 1, k_relabel, dim3(b.cfg[KK_RELABEL].grid), dim3(b.cfg[KK_RELABEL].threads), d);
   return e;
 }
@@ -641,7 +652,7 @@ cudaError_t merge_phase_host(Batch &b) {
   k_trace<<<MAX_TRACES, 1024, 0, st>>>(d, b.prm); VLS_LAUNCH(b);
   b.prof.end(st, ps);
   ps = b.prof.begin(st, KK_MERGE_FINISH);
-  k_merge_finish<<<1, 1024, 0, st>>>(d, b.prm); VLS_LAUNCH(b);
+  k_merge_finish<<<MAX_TRACES, 1024, 0, st>>>(d, b.prm); VLS_LAUNCH(b);
   b.prof.end(st, ps);
   ps = b.prof.begin(st, KK_RELABEL);
   k_relabel<<<b.cfg[KK_RELABEL].grid, b.cfg[KK_RELABEL].threads, 0, st>>>(d); VLS_LAUNCH(b);

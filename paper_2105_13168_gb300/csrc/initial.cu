@@ -258,17 +258,17 @@ __device__ __forceinline__ void hook_phase(const Dev &d) {
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
   const int32_t nF = __ldcg(d.nfront + cur);
-  const int32_t lane = threadIdx.x & 15;
-  // 16 lanes per band row, one neighbour each: a neighbour joins the row's band component iff
+  const int32_t lane = group_lane();
+  // GL lanes per band row, one neighbour each: a neighbour joins the row's band component iff
   // it is a frontier row of this step (band vertices are) holding the same live layer strictly
   // between 0 and 1; the smaller id of each such pair unites
-  FOR_ROWS16(i, nF) {
+  FOR_ROWS_G(i, nF) {
     if (__ldcg(d.pdone + fp[i])) continue;
     const int32_t v = fv[i];
     int32_t l;
     if (!is_band(d, v, l)) continue;
     const int32_t b = d.rp[v], e = d.rp[v + 1];
-    for (int32_t k = b + lane; k < e; k += 16) {
+    for (int32_t k = b + lane; k < e; k += GL) {
       const int32_t u = d.col[k];
       if (!VCHK(d.err, u, d.V, 130)) continue;
       const int32_t fm = d.fmark[u], lu = d.lay[u];
@@ -369,8 +369,8 @@ __device__ __forceinline__ uint32_t gives(const Dev &d, int32_t w) {
   return lt1 ? 3u : 2u;
 }
 
-// F_t -> F_{t+1}: a group of 16 lanes per row, lane j takes the row's neighbour j (rows longer
-// than 16 loop); the row itself joins when it qualifies on its own or through any pair.  Also
+// F_t -> F_{t+1}: a group of GL lanes per row, lane j takes the row's neighbour j (rows longer
+// than GL loop); the row itself joins when it qualifies on its own or through any pair.  Also
 // clears the per-layer root counts of this step (each band root resets its layer's counter) and
 // accumulates the step record.
 __device__ __forceinline__ void frontier_phase(const Dev &d) {
@@ -382,8 +382,8 @@ __device__ __forceinline__ void frontier_phase(const Dev &d) {
   int32_t *__restrict__ np_out = d.front[nxt] + d.V;
   int32_t *nN_ptr = d.nfront + nxt;
   int32_t *pcount_next = d.pfront + (size_t)nxt * d.P;
-  const int32_t lane = threadIdx.x & 15;
-  const unsigned half = 0xFFFFu << (threadIdx.x & 16);
+  const int32_t lane = group_lane();
+  const unsigned grp = group_mask();
   int32_t *__restrict__ seg_out = d.fseg[nxt];
   auto add = [&](int32_t u, int32_t p) {
     if (atomicExch(&d.stamp[u], tnext) == tnext) return;
@@ -396,7 +396,7 @@ __device__ __forceinline__ void frontier_phase(const Dev &d) {
     const int32_t j = d.voff[p] + ks;
     if (VCHK(d.err, j, d.voff[p + 1], 122)) seg_out[j] = u;
   };
-  FOR_ROWS16(i, nF) {
+  FOR_ROWS_G(i, nF) {
     const int32_t p = fp[i];
     if (__ldcg(d.pdone + p)) continue;
     const int32_t v = fv[i];
@@ -414,7 +414,7 @@ __device__ __forceinline__ void frontier_phase(const Dev &d) {
     const uint32_t gv = gives(d, v);
     const int32_t b = d.rp[v], e = d.rp[v + 1];
     bool join = gv == 3u;
-    for (int32_t k0 = b; k0 < e; k0 += 16) {
+    for (int32_t k0 = b; k0 < e; k0 += GL) {
       const int32_t k = k0 + lane;
       if (k >= e) continue;
       const int32_t u = d.col[k];
@@ -424,7 +424,7 @@ __device__ __forceinline__ void frontier_phase(const Dev &d) {
       join = true;
       if (gu != 0u) add(u, p);
     }
-    join = __any_sync(half, join) && gv != 0u;
+    join = __any_sync(grp, join) && gv != 0u;
     if (lane == 0 && join) add(v, p);
   }
 }
@@ -635,7 +635,7 @@ void configure_initial(Batch &b) {
   b.cfg[KK_APPLY] = row_cfg(b, k_apply, KK_APPLY, 128);
   b.cfg[KK_HOOK] = b.hook_variant == 1 ? row_cfg(b, k_band_hook_row, KK_HOOK, 128) : row_cfg(b, k_band_hook, KK_HOOK, 256);
   b.cfg[KK_COUNT] = row_cfg(b, k_band_count, KK_COUNT, 128);
-  b.cfg[KK_FRONTIER] = row_cfg(b, k_frontier, KK_FRONTIER, 256); // 16 lanes per row
+  b.cfg[KK_FRONTIER] = row_cfg(b, k_frontier, KK_FRONTIER, 256); // GL lanes per row
 }
 
 cudaError_t final_checks(Batch &b) {

@@ -30,7 +30,7 @@ __device__ __forceinline__ bool in_dom(const Dev &d, int32_t u, int32_t step) {
   const int32_t c = d.cover[u];
   return c >= 0 && c <= step;
 }
-// half-edge slot k (v -> u) is cut in pass q
+// grp-edge slot k (v -> u) is cut in pass q
 __device__ __forceinline__ bool is_cut(const TDev &T, int32_t q, int32_t k) {
   const int32_t *c = T.cut + T.pcoff[q];
   int32_t lo = 0, hi = T.pcn[q] - 1;
@@ -251,7 +251,7 @@ __device__ __forceinline__ uint32_t tgives_at(const TDev &T, int32_t i) {
   return T.phif ? tgives(T.phif[i]) : tgives(T.phi[i]);
 }
 
-// 16-lane groups per row, lane j takes the row's neighbour j (rows longer than 16 loop).
+// GL-lane groups per row, lane j takes the row's neighbour j (rows longer than GL loop).
 __device__ __forceinline__ void tfrontier_phase(const Dev &d, const TDev &T) {
   const int32_t tau = __ldcg(d.ctl + CTL_TAU), cur = tau & 1, nxt = cur ^ 1, tnext = tau + 1;
   const int32_t *__restrict__ fv = T.fv[cur];
@@ -261,8 +261,8 @@ __device__ __forceinline__ void tfrontier_phase(const Dev &d, const TDev &T) {
   int32_t *__restrict__ nq_out = T.fq[nxt];
   int32_t *nN_ptr = T.nf + nxt;
   int32_t *qcnt_next = T.qcnt + (size_t)nxt * T.NP;
-  const int32_t lane = threadIdx.x & 15;
-  const unsigned half = 0xFFFFu << (threadIdx.x & 16);
+  const int32_t lane = group_lane();
+  const unsigned grp = group_mask();
   auto add = [&](int32_t u, int32_t iu, int32_t q) {
     if (atomicExch(&T.stamp[iu], tnext) == tnext) return;
     const int32_t s = warp_append(nN_ptr, qcnt_next, q);
@@ -270,7 +270,7 @@ __device__ __forceinline__ void tfrontier_phase(const Dev &d, const TDev &T) {
     nv_out[s] = u;
     nq_out[s] = q;
   };
-  FOR_ROWS16(i, nF) {
+  FOR_ROWS_G(i, nF) {
     const int32_t q = fq[i];
     if (__ldcg(T.qdone + q) || __ldcg(T.qbstar + q) != 0x7fffffff) continue;
     const int32_t v = fv[i];
@@ -281,7 +281,7 @@ __device__ __forceinline__ void tfrontier_phase(const Dev &d, const TDev &T) {
     const uint32_t gv = tgives_at(T, iv);
     const int32_t b = d.rp[v], e = d.rp[v + 1];
     bool join = gv == 3u;
-    for (int32_t k0 = b; k0 < e; k0 += 16) {
+    for (int32_t k0 = b; k0 < e; k0 += GL) {
       const int32_t k = k0 + lane;
       if (k >= e) continue;
       const int32_t u = d.col[k];
@@ -293,7 +293,7 @@ __device__ __forceinline__ void tfrontier_phase(const Dev &d, const TDev &T) {
       join = true;
       if (!(T.flag[iu] & F_SRC)) add(u, iu, q);
     }
-    join = __any_sync(half, join) && !(fl & F_SRC);
+    join = __any_sync(grp, join) && !(fl & F_SRC);
     if (lane == 0 && join) add(v, iv, q);
   }
 }

@@ -112,7 +112,7 @@ struct Batch {
   struct Shape {
     int threads = 0, bps = 0;
   } shape[KK_COUNT_KINDS];
-  int hook_variant = 2; // band union-find: 1 one thread per band row, 2 sixteen lanes per row
+  int hook_variant = 2; // band union-find: 1 one thread per band row, 2 a lane group per row
   long long launches = 0;
   Arena *arena = nullptr;
   // host copies of problem tables

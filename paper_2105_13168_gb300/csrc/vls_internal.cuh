@@ -215,18 +215,23 @@ __device__ __forceinline__ bool val_band(float x) { return val_pos(x) && val_lt1
 // Grid-stride loops over the n rows of a frontier list that spread warps over the whole grid:
 // loop warp w runs as warp w / gridDim.x of block w % gridDim.x, so a frontier of a few
 // thousand rows occupies every SM instead of filling the first blocks (and so a few SMs)
-// while the rest idle.  Lanes of a warp take consecutive rows (FOR_ROWS: 32 rows per warp;
-// FOR_ROWS16: 2 rows per warp, 16 lanes each).  The loop bounds are uniform per warp; the body
-// runs once per row, `continue` moves on to the next row.
+// while the rest idle.  Lanes of a warp take consecutive rows (FOR_ROWS: 32 rows per warp, one
+// lane each; FOR_ROWS_G: 32 / GL rows per warp, a group of GL lanes each that share the row's
+// neighbours).  The loop bounds are uniform per warp; the body runs once per row, `continue`
+// moves on to the next row.
+constexpr int GL = 8; // lanes per row of the neighbour-parallel kernels (mesh degrees are 3..10)
 #define VLS_WARP_LOOP(w, rows_per_warp, n)                                                          \
   for (int32_t w = (int32_t)(blockIdx.x + gridDim.x * (threadIdx.x >> 5)); w * (rows_per_warp) < (n); \
        w += (int32_t)(gridDim.x * (blockDim.x >> 5)))
 #define FOR_ROWS(i, n)                                                                              \
   VLS_WARP_LOOP(vls_w_, 32, n)                                                                      \
   for (int32_t i = vls_w_ * 32 + (int32_t)(threadIdx.x & 31); i < (n); i = INT32_MAX)
-#define FOR_ROWS16(i, n)                                                                            \
-  VLS_WARP_LOOP(vls_w_, 2, n)                                                                       \
-  for (int32_t i = vls_w_ * 2 + (int32_t)((threadIdx.x >> 4) & 1); i < (n); i = INT32_MAX)
+#define FOR_ROWS_G(i, n)                                                                            \
+  VLS_WARP_LOOP(vls_w_, 32 / GL, n)                                                                 \
+  for (int32_t i = vls_w_ * (32 / GL) + (int32_t)((threadIdx.x & 31) / GL); i < (n); i = INT32_MAX)
+// lane within the row's group, and the warp mask of the group
+__device__ __forceinline__ int32_t group_lane() { return (int32_t)(threadIdx.x & (GL - 1)); }
+__device__ __forceinline__ unsigned group_mask() { return ((1u << GL) - 1u) << (threadIdx.x & (32 - GL)); }
 
 // ------------------------------------------------------------ stored values
 // The layer value of a vertex is stored as double (FP64 form) or float (FP32 form, d.phif
