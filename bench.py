@@ -20,7 +20,8 @@ roofline = the initial-pass frontier update kernel (the diffusion SpMV): algorit
          inside the library, against the measured HBM copy bandwidth;
 cpu_baseline = the plain CPU oracle on a bounded sample of the same workload;
 check_vs_oracle = those sampled problems' GPU results against the oracle's: integer
-         results identical, max |phi - phi_oracle|, rows redone in FP64.
+         results identical, max |phi - phi_oracle|, rows redone in FP64, and the largest
+         residual of the FP64 mass check of the diffusion step over the batch.
 
 --impl reference times the CPU oracle itself (the only reference implementation of this
 method available here) with the same metric and JSON layout.
@@ -425,7 +426,9 @@ def main():
     cout = vls.read_result(res)
     vls.vls_result_free(res)
     vls.vls_destroy(cctx)
-    check = {"problems_checked": len(orc_results), "rechecks": cout[0].stats["rechecks"],
+    check = {"problems_checked": len(orc_results),
+             "mass_check_max_resid": max(p.stats["mass_resid"] for p in cout),
+             "rechecks": cout[0].stats["rechecks"],
              "pass_rechecks": cout[0].stats["pass_rechecks"], "row_updates": rows,
              "pass_updates": sum(p.stats["pass_updates"] for p in cout)}
     if orc_results:

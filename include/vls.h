@@ -128,6 +128,12 @@ typedef struct {
    * a decision within recheck_margin of its threshold (or several layers) and was redone in
    * FP64 (batch-wide); 0 in the FP64 form */
   int64_t rechecks, pass_rechecks;
+  /* Mass check of the diffusion step, in FP64: at every initial-pass step the base's Laplacian
+   * weighted by the lumped masses (m_v = d_v / s, so that m_v L_vu = 1 is symmetric) must sum to
+   * zero over the rows that can change; this is the largest |sum| / sum of the terms'
+   * magnitudes seen over the problem's steps.  Rounding alone gives about 1e-16 in the FP64
+   * form and 1e-7 in the FP32 form; a wrong operator entry or a lost neighbour gives far more. */
+  double mass_resid;
 } vls_stats;
 
 /* Fill *o with the defaults above. */

@@ -202,6 +202,9 @@ void layout_batch(Layout &L, Batch &b) {
   d.phi = f32 ? nullptr : L.take<double>(V);
   d.phif = f32 ? L.take<float>(V) : nullptr;
   d.nrecheck = L.take<unsigned long long>(2);
+  d.mslots = P <= (size_t)MASS_SPREAD_MAXP ? MASS_SLOTS : 1;
+  d.pmass = L.take<double>(2 * (size_t)d.mslots * P);
+  d.pmres = L.take<double>(P);
   d.cover = L.take<int32_t>(V);
   d.stamp = L.take<int32_t>(V);
   d.fmark = L.take<int32_t>(V);
@@ -508,6 +511,8 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     P.theta = ctx->opt.theta_iso;
     P.lv[0] = 0.0;
     for (int k = 1; k <= LV_MAX; ++k) P.lv[k] = P.s / (double)k;
+    P.mv[0] = 0.0;
+    for (int k = 1; k <= LV_MAX; ++k) P.mv[k] = (double)k / P.s;
     P.mun[0] = 0.0;
     for (int k = 1; k <= KMAX + 1; ++k) P.mun[k] = P.mu / (double)k;
     P.margin = ctx->opt.recheck_margin;
@@ -627,6 +632,8 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     if (d.phif) CK(cudaMemsetAsync(d.phif, 0, sizeof(float) * b.V, st));
     else CK(cudaMemsetAsync(d.phi, 0, sizeof(double) * b.V, st));
     CK(cudaMemsetAsync(d.nrecheck, 0, sizeof(unsigned long long) * 2, st));
+    CK(cudaMemsetAsync(d.pmass, 0, sizeof(double) * 2 * d.mslots * b.P, st));
+    CK(cudaMemsetAsync(d.pmres, 0, sizeof(double) * b.P, st));
     CK(cudaMemsetAsync(d.cover, 0xff, sizeof(int32_t) * b.V, st));
     CK(cudaMemsetAsync(d.stamp, 0, sizeof(int32_t) * b.V, st));
     CK(cudaMemsetAsync(d.fmark, 0, sizeof(int32_t) * b.V, st));
@@ -857,6 +864,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     std::vector<int32_t> nkind, nstep, nprob, nlocal, lstate, lbirth, ldeath, lcount, psteps, pev, hedge, hverts;
     std::vector<double> npos, hpts;
     std::vector<int64_t> pupd;
+    std::vector<double> pmres;
     int32_t ne = 0;
     CK(cudaMemcpyAsync(&ne, d.nhedge, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -865,7 +873,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     if (!d2h(nkind, d.nkind, h_nn, st) || !d2h(nstep, d.nstep, h_nn, st) || !d2h(nprob, d.nprob, h_nn, st) ||
         !d2h(nlocal, d.nlocal, h_nn, st) || !d2h(npos, d.npos, 3 * (size_t)h_nn, st) ||
         !d2h(lcount, d.lcount, b.P, st) || !d2h(psteps, d.psteps, b.P, st) || !d2h(pev, d.pev, 3 * (size_t)b.P, st) ||
-        !d2h(pupd, reinterpret_cast<const int64_t *>(d.pupd), b.P, st) || !d2h(hedge, d.hedge, 2 * (size_t)ne, st) ||
+        !d2h(pupd, reinterpret_cast<const int64_t *>(d.pupd), b.P, st) || !d2h(pmres, d.pmres, b.P, st) || !d2h(hedge, d.hedge, 2 * (size_t)ne, st) ||
         !d2h(hverts, d.hverts, ne, st) || !d2h(hpts, d.hpts, 3 * (size_t)ne, st) ||
         !d2h(lstate, d.lstate, b.Lcap, st) || !d2h(lbirth, d.lbirth, b.Lcap, st) || !d2h(ldeath, d.ldeath, b.Lcap, st)) {
       err = cudaErrorUnknown;
@@ -900,7 +908,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     b.d2h += (int64_t)sizeof(h_ctl);
     unsigned long long h_rechk[2] = {0ull, 0ull};
     CK(cudaMemcpyAsync(h_rechk, d.nrecheck, sizeof(h_rechk), cudaMemcpyDeviceToHost, st));
-    b.d2h += (int64_t)sizeof(h_rechk);
+    b.d2h += (int64_t)sizeof(h_rechk) + (int64_t)sizeof(double) * b.P;
     CK(cudaEventRecord(ev[4], st));
     CK(cudaStreamSynchronize(st));
     if (!b.host_loop) {
@@ -956,6 +964,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       r.stats.d2h_bytes = b.d2h;
       r.stats.rechecks = (int64_t)h_rechk[0];
       r.stats.pass_rechecks = (int64_t)h_rechk[1];
+      r.stats.mass_resid = pmres[q];
       const int32_t nl = lcount[q];
       r.layers.resize(3 * (size_t)nl);
       for (int32_t l = 1; l <= nl; ++l) {

@@ -29,7 +29,7 @@ __device__ __forceinline__ int32_t append(int32_t *counter) { return atomicAdd(c
 // FP32 form are widened exactly, so the row is the FP64 step from the stored inputs.
 template <int MAXD, class TV>
 __device__ __forceinline__ void row_f64(const Params &P, int nl, const int32_t *ls, int32_t lv, int32_t o, TV xv,
-                                        const int32_t *nlay, const TV *nx, int32_t deg, double *out) {
+                                        const int32_t *nlay, const TV *nx, int32_t deg, double *out, double2 &mass) {
   const double Lv = P.lv[deg];
   const double xvd = (double)xv;
   const double xb = dsub(1.0, lv != 0 ? xvd : 0.0);
@@ -58,7 +58,20 @@ __device__ __forceinline__ void row_f64(const Params &P, int nl, const int32_t *
       if (nlay[j] == 0) accb = dadd(accb, Lv);                                         // Lv * 1.0
       else if (val_lt1(nx[j])) accb = dadd(accb, dmul(Lv, dsub(1.0, (double)nx[j]))); // zero terms skipped
     }
+  // mass check: m_v (L base)_v less the flux into frozen neighbours (never rows), and the
+  // magnitude of its terms, sum_u base(u) + d base(v)
+  double fzb = 0.0; // base held by frozen neighbours (a dead plateau holds none)
+  int nfz = 0;
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j)
+    if (j < deg && nlay[j] < 0) {
+      ++nfz;
+      if (val_lt1(nx[j])) fzb += 1.0 - (double)nx[j];
+    }
+  const double bnd = fzb - (double)nfz * xb;
+  mass = make_double2(0.0, dadd(dmul(P.mv[deg], accb), dmul((double)deg, xb)));
   accb = dadd(accb, dmul(-P.s, xb));
+  mass.x = dmul(P.mv[deg], accb) - bnd;
   if (!vertex_update(P, nl, x, lap, xb, accb, out)) {
 #pragma unroll
     for (int q = 0; q < KMAX; ++q)
@@ -70,7 +83,8 @@ __device__ __forceinline__ void row_f64(const Params &P, int nl, const int32_t *
 // when a decision of the step lies within the recheck margin (the row is then redone in FP64).
 template <int MAXD>
 __device__ __forceinline__ bool row_f32(const Params &P, int32_t l, int32_t lv, int32_t o, float xv,
-                                        const int32_t *nlay, const float *nx, int32_t deg, double &out) {
+                                        const int32_t *nlay, const float *nx, int32_t deg, double &out,
+                                        double2 &mass) {
   const float Lv = P.f_lv[deg];
   const float plat = (o != 0 && l == o) ? 1.f : 0.f;
   float acc = 0.f, accb = 0.f;
@@ -85,15 +99,44 @@ __device__ __forceinline__ bool row_f32(const Params &P, int32_t l, int32_t lv, 
   const float xb = 1.f - (lv != 0 ? xv : 0.f);
   const float lap = fmaf(-P.f_s, x, acc);
   const float lapb = fmaf(-P.f_s, xb, accb);
+  // mass check (FP64 from the FP32 sums): m_v (L base)_v less the flux into frozen neighbours,
+  // and the magnitude of its terms
+  float fzb = 0.f; // base held by frozen neighbours (a dead plateau holds none: exact 0)
+  int nfz = 0;
+#pragma unroll
+  for (int j = 0; j < MAXD; ++j)
+    if (j < deg && nlay[j] < 0) {
+      ++nfz;
+      fzb += 1.f - nx[j];
+    }
+  const double bnd = (double)fzb - (double)nfz * (double)xb;
+  mass = make_double2(P.mv[deg] * (double)lapb - bnd, P.mv[deg] * (double)accb + (double)deg * (double)xb);
   float y;
   if (!vertex_update_f32(P, x, lap, xb, lapb, y)) return false;
   out = (double)y;
   return true;
 }
 
-template <int MAXD, class TV>
-__device__ __forceinline__ bool update_row(const Dev &d, const Params &P, int32_t i, int32_t p, int32_t v, int32_t b,
-                                           int32_t deg) {
+// FP32 form: the FP64 redo of a row from its gathered inputs (rounded to float keeping every
+// threshold's side), out of line so that the hot row keeps few registers.  Rare: a collision or
+// a decision within the margin.
+template <int MAXD>
+__device__ __noinline__ void row_redo(const Params &P, int nl, const int32_t *ls, int32_t lv, int32_t o, float xv,
+                                      const int32_t *nlay, const float *nx, int32_t deg, double *out, double2 &mass) {
+  row_f64<MAXD, float>(P, nl, ls, lv, o, xv, nlay, nx, deg, out, mass);
+  for (int q = 0; q < nl; ++q) out[q] = (double)f32_keep_side(out[q], P.theta);
+}
+
+// One frontier row.  FP32 form: the common case (one layer and the base) in FP32, a row that
+// needs FP64 (several layers, or a decision within the margin) redone out of line from the same
+// gathered inputs (FAST = true), or all in FP64 and rounded keeping every threshold's side
+// (FAST = false: the out-of-line path of rows longer than the register path).  FP64 form: the
+// FP64 row.
+enum RowOutcome : int { ROW_DONE = 0, ROW_REDONE = 1 };
+
+template <int MAXD, class TV, bool FAST>
+__device__ __forceinline__ int update_row(const Dev &d, const Params &P, int32_t i, int32_t p, int32_t v, int32_t b,
+                                          int32_t deg, double2 &mass) {
   const TV *__restrict__ ph = ph_arr<TV>(d);
   // nlay[j]: layer of neighbour j, 0 for the base only, -1 for a frozen plateau
   int32_t nlay[MAXD];
@@ -138,23 +181,36 @@ __device__ __forceinline__ bool update_row(const Dev &d, const Params &P, int32_
   if (ovf) {
     atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_ESLOTS);
     d.onl[i] = -1;
-    return false;
+    return ROW_DONE;
   }
-  if (!hb || nl == 0) { d.onl[i] = -1; return false; }
+  if (!hb || nl == 0) { d.onl[i] = -1; return ROW_DONE; }
   double out[KMAX];
-  bool redo = false;
-  if constexpr (sizeof(TV) == sizeof(float)) {
+  int outcome = ROW_DONE;
+  if constexpr (sizeof(TV) == sizeof(float) && FAST) {
     // FP32 form: one layer in FP32; several layers (a collision: merge arithmetic follows)
-    // and rows near a decision are computed in FP64 and rounded keeping their side
-    if (nl != 1 || !row_f32<MAXD>(P, ls[0], lv, o, xv, nlay, nx, deg, out[0])) {
-      row_f64<MAXD, TV>(P, nl, ls, lv, o, xv, nlay, nx, deg, out);
+    // and rows near a decision are redone in FP64 from copies of the gathered inputs (only
+    // the copies live in local memory)
+    if (nl != 1 || !row_f32<MAXD>(P, ls[0], lv, o, xv, nlay, nx, deg, out[0], mass)) {
+      int32_t cl[MAXD], cls[KMAX];
+      float cx[MAXD];
+      double co[KMAX];
 #pragma unroll
-      for (int q = 0; q < KMAX; ++q)
-        if (q < nl) out[q] = (double)f32_keep_side(out[q], P.theta);
-      redo = true;
+      for (int j = 0; j < MAXD; ++j) { cl[j] = nlay[j]; cx[j] = nx[j]; }
+#pragma unroll
+      for (int q = 0; q < KMAX; ++q) cls[q] = ls[q];
+      row_redo<MAXD>(P, nl, cls, lv, o, xv, cl, cx, deg, co, mass);
+#pragma unroll
+      for (int q = 0; q < KMAX; ++q) out[q] = co[q];
+      outcome = ROW_REDONE;
     }
+  } else if constexpr (sizeof(TV) == sizeof(float)) {
+    row_f64<MAXD, TV>(P, nl, ls, lv, o, xv, nlay, nx, deg, out, mass);
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q)
+      if (q < nl) out[q] = (double)f32_keep_side(out[q], P.theta);
+    outcome = ROW_REDONE;
   } else {
-    row_f64<MAXD, TV>(P, nl, ls, lv, o, xv, nlay, nx, deg, out);
+    row_f64<MAXD, TV>(P, nl, ls, lv, o, xv, nlay, nx, deg, out, mass);
   }
   int cnt = 0;
 #pragma unroll
@@ -165,13 +221,31 @@ __device__ __forceinline__ bool update_row(const Dev &d, const Params &P, int32_
       ++cnt;
     }
   d.onl[i] = cnt;
-  return redo;
+  return outcome;
+}
+
+// Rows longer than the register path: out of line.
+constexpr int ROW_REG = 12; // longest row of the register path (mesh degrees are 3..10)
+template <class TV>
+__device__ __noinline__ int update_row_wide(const Dev &d, const Params &P, int32_t i, int32_t p, int32_t v, int32_t b,
+                                            int32_t deg, double2 &mass) {
+  return update_row<64, TV, false>(d, P, i, p, v, b, deg, mass);
 }
 
 template <class TV>
-__device__ __noinline__ bool update_row_wide(const Dev &d, const Params &P, int32_t i, int32_t p, int32_t v, int32_t b,
-                                             int32_t deg) {
-  return update_row<64, TV>(d, P, i, p, v, b, deg);
+__device__ __forceinline__ int update_one(const Dev &d, const Params &P, const int32_t *fv, int32_t i, int32_t p,
+                                          double2 &mass) {
+  if (__ldcg(d.pdone + p)) { d.onl[i] = -1; return ROW_DONE; }
+  const int32_t v = fv[i];
+  if (!VCHK(d.err, v, d.V, 101)) { d.onl[i] = -1; return ROW_DONE; }
+  const int32_t b = d.rp[v], e = d.rp[v + 1];
+  if (!VCHK(d.err, e, d.nnz + 1, 102) || !VCHK(d.err, b, e + 1, 103)) { d.onl[i] = -1; return ROW_DONE; }
+  const int32_t deg = e - b;
+  if (deg <= ROW_REG) return update_row<ROW_REG, TV, true>(d, P, i, p, v, b, deg, mass);
+  if (deg <= 64) return update_row_wide<TV>(d, P, i, p, v, b, deg, mass);
+  atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_EINVAL);
+  d.onl[i] = -1;
+  return ROW_DONE;
 }
 
 template <class TV>
@@ -181,17 +255,41 @@ __device__ __forceinline__ void update_rows(const Dev &d, const Params &P) {
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
   const int32_t nF = __ldcg(d.nfront + cur);
   uint32_t redo = 0;
-  FOR_ROWS(i, nF) {
-    const int32_t p = fp[i];
-    if (__ldcg(d.pdone + p)) { d.onl[i] = -1; continue; }
-    const int32_t v = fv[i];
-    if (!VCHK(d.err, v, d.V, 101)) { d.onl[i] = -1; continue; }
-    const int32_t b = d.rp[v], e = d.rp[v + 1];
-    if (!VCHK(d.err, e, d.nnz + 1, 102) || !VCHK(d.err, b, e + 1, 103)) { d.onl[i] = -1; continue; }
-    const int32_t deg = e - b;
-    if (deg <= 16) redo += update_row<16, TV>(d, P, i, p, v, b, deg);
-    else if (deg <= 64) redo += update_row_wide<TV>(d, P, i, p, v, b, deg);
-    else { atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_EINVAL); d.onl[i] = -1; }
+  const int32_t lane = (int32_t)(threadIdx.x & 31);
+  VLS_WARP_LOOP(w, 32, nF) { // one row per lane (as FOR_ROWS), then the warp's mass sums
+    const int32_t i = w * 32 + lane;
+    int32_t p = -1;
+    double2 mass = make_double2(0.0, 0.0);
+    if (i < nF) {
+      p = fp[i];
+      redo += update_one<TV>(d, P, fv, i, p, mass) == ROW_REDONE;
+    }
+    // mass check sums: FP64 atomics on per-problem slots spread over MASS_SLOTS addresses (the
+    // frontier list interleaves problems, and same-address atomics serialise).  A warp with few
+    // problems sums each problem's rows first: one pair of atomics per problem per warp.
+    const int32_t slot = (int32_t)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) & (d.mslots - 1));
+    const unsigned peers = __match_any_sync(0xffffffffu, p);
+    unsigned leaders = __ballot_sync(0xffffffffu, lane == __ffs(peers) - 1);
+    if (__popc(leaders) <= 4) {
+      while (leaders) {
+        const int32_t q = __shfl_sync(0xffffffffu, p, __ffs(leaders) - 1);
+        leaders &= leaders - 1;
+        double sx = p == q ? mass.x : 0.0, sy = p == q ? mass.y : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          sx += __shfl_xor_sync(0xffffffffu, sx, off);
+          sy += __shfl_xor_sync(0xffffffffu, sy, off);
+        }
+        if (lane == 0 && q >= 0 && sy != 0.0) {
+          atomicAdd(&d.pmass[((int64_t)q * d.mslots + slot) * 2], sx);
+          atomicAdd(&d.pmass[((int64_t)q * d.mslots + slot) * 2 + 1], sy);
+        }
+      }
+    } else if (mass.y != 0.0) {
+      const int32_t ls = (slot + lane) & (d.mslots - 1);
+      atomicAdd(&d.pmass[((int64_t)p * d.mslots + ls) * 2], mass.x);
+      atomicAdd(&d.pmass[((int64_t)p * d.mslots + ls) * 2 + 1], mass.y);
+    }
   }
   if constexpr (sizeof(TV) == sizeof(float)) {
     redo = __reduce_add_sync(0xffffffffu, redo);
@@ -199,11 +297,8 @@ __device__ __forceinline__ void update_rows(const Dev &d, const Params &P) {
   }
 }
 
-__device__ __forceinline__ void update_phase(const Dev &d, const Params &P) {
-  if (d.phif) update_rows<float>(d, P);
-  else update_rows<double>(d, P);
-}
-__global__ void __launch_bounds__(256) k_update(Dev d, Params P) { update_phase(d, P); }
+// One instantiation per stored value type, so that each form gets its own register budget.
+template <class TV> __global__ void __launch_bounds__(256, VLS_UPDATE_MINB) k_update(Dev d, Params P) { update_rows<TV>(d, P); }
 
 // ------------------------------------------------------------------- apply
 // Also starts the band labelling: every row is its own union-find root (only band rows are
@@ -453,6 +548,20 @@ __device__ __forceinline__ void epilogue_phase(const Dev &d, const Handles &H, i
       }
       d.rband[p] = 0;
       d.rhash[p] = 0ull;
+      {
+        // mass check of this step's diffusion: the base's Laplacian, weighted by the lumped
+        // masses, sums to zero over the rows that can change (every other row has a uniform
+        // closed neighbourhood); the FP64 residual relative to the terms' magnitude
+        double2 *pm = reinterpret_cast<double2 *>(d.pmass) + (int64_t)p * d.mslots;
+        double sm = 0.0, mag = 0.0;
+        for (int k = 0; k < d.mslots; ++k) {
+          const double2 a = __ldcg(pm + k);
+          sm += a.x;
+          mag += a.y;
+          pm[k] = make_double2(0.0, 0.0);
+        }
+        if (mag > 0.0) d.pmres[p] = fmax(d.pmres[p], fabs(sm) / mag);
+      }
       if (__ldcg(d.pstatus + p) != 0) d.pdone[p] = 1;
       else if (__ldcg(pcount_next + p) == 0) d.pdone[p] = 1;
       else if (t >= max_steps) { d.pstatus[p] = VLS_EMAXSTEPS; d.pdone[p] = 1; }
@@ -565,7 +674,8 @@ cudaError_t build_initial_graph(Batch &b, cudaGraph_t *out) {
   GK(add_conditional(&w, g, nullptr, 0, cudaGraphCondTypeWhile, 1u, &H.loop, &body));
   GK(cudaGraphConditionalHandleCreate(&H.merge, body, 0u, cudaGraphCondAssignDefault));
   GK(cudaGraphConditionalHandleCreate(&H.split, body, 0u, cudaGraphCondAssignDefault));
-  GK(add_kernel(&n_upd, body, nullptr, 0, k_update, G(KK_UPDATE), T(KK_UPDATE), b.d, b.prm));
+  GK(add_kernel(&n_upd, body, nullptr, 0, b.d.phif ? k_update<float> : k_update<double>, G(KK_UPDATE), T(KK_UPDATE),
+                b.d, b.prm));
   GK(add_kernel(&n_app, body, &n_upd, 1, k_apply, G(KK_APPLY), T(KK_APPLY), b.d, H));
   {
     cudaGraphNodeParams np = {};
@@ -607,7 +717,9 @@ cudaError_t initial_step_host(Batch &b) {
   Handles H{};
   H.use = 0;
   long ps = b.prof.begin(st, KK_UPDATE);
-  k_update<<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm); VLS_LAUNCH(b);
+  if (d.phif) k_update<float><<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm);
+  else k_update<double><<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm);
+  VLS_LAUNCH(b);
   b.prof.end(st, ps);
   ps = b.prof.begin(st, KK_APPLY);
   k_apply<<<b.cfg[KK_APPLY].grid, b.cfg[KK_APPLY].threads, 0, st>>>(d, H); VLS_LAUNCH(b);
@@ -631,7 +743,8 @@ cudaError_t initial_step_host(Batch &b) {
 }
 
 void configure_initial(Batch &b) {
-  b.cfg[KK_UPDATE] = row_cfg(b, k_update, KK_UPDATE, 128); // one thread per frontier row
+  b.cfg[KK_UPDATE] = b.opt.precision == VLS_FP32_RECHECK ? row_cfg(b, k_update<float>, KK_UPDATE, 128)
+                                                           : row_cfg(b, k_update<double>, KK_UPDATE, 128); // thread per row
   b.cfg[KK_APPLY] = row_cfg(b, k_apply, KK_APPLY, 128);
   b.cfg[KK_HOOK] = b.hook_variant == 1 ? row_cfg(b, k_band_hook_row, KK_HOOK, 128) : row_cfg(b, k_band_hook, KK_HOOK, 256);
   b.cfg[KK_COUNT] = row_cfg(b, k_band_count, KK_COUNT, 128);

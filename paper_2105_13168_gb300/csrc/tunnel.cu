@@ -212,11 +212,10 @@ __device__ __forceinline__ void tupdate_rows(const Dev &d, const TDev &T, const 
   }
 }
 
-__device__ __forceinline__ void tupdate_phase(const Dev &d, const TDev &T, const Params &P) {
-  if (T.phif) tupdate_rows<float>(d, T, P);
-  else tupdate_rows<double>(d, T, P);
+// One instantiation per stored value type, so that each form gets its own register budget.
+template <class TV> __global__ void __launch_bounds__(256, VLS_UPDATE_MINB) k_tupdate(Dev d, TDev T, Params P) {
+  tupdate_rows<TV>(d, T, P);
 }
-__global__ void __launch_bounds__(256) k_tupdate(Dev d, TDev T, Params P) { tupdate_phase(d, T, P); }
 
 __device__ __forceinline__ void tapply_phase(const Dev &d, const TDev &T, double theta) {
   const int32_t tau = __ldcg(d.ctl + CTL_TAU), cur = tau & 1;
@@ -413,7 +412,8 @@ __global__ void k_tctl_set(int32_t *ctl, int32_t idx, int32_t v) { ctl[idx] = v;
 }  // namespace
 
 void configure_tunnel(Batch &b) {
-  b.cfg[KK_TUPDATE] = row_cfg(b, k_tupdate, KK_TUPDATE, 128);
+  b.cfg[KK_TUPDATE] = b.opt.precision == VLS_FP32_RECHECK ? row_cfg(b, k_tupdate<float>, KK_TUPDATE, 128)
+                                                            : row_cfg(b, k_tupdate<double>, KK_TUPDATE, 128);
   b.cfg[KK_TAPPLY] = row_cfg(b, k_tapply, KK_TAPPLY, 128);
   b.cfg[KK_TFRONTIER] = row_cfg(b, k_tfrontier, KK_TFRONTIER, 256);
 }
@@ -440,7 +440,9 @@ cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out) {
     const int sync_every = b.opt.sync_interval > 0 ? b.opt.sync_interval : 16;
     for (int32_t tau = 1;; ++tau) {
       long ps = b.prof.begin(st, KK_TUPDATE);
-      k_tupdate<<<b.cfg[KK_TUPDATE].grid, b.cfg[KK_TUPDATE].threads, 0, st>>>(d, T, b.prm); VLS_LAUNCH(b);
+      if (T.phif) k_tupdate<float><<<b.cfg[KK_TUPDATE].grid, b.cfg[KK_TUPDATE].threads, 0, st>>>(d, T, b.prm);
+      else k_tupdate<double><<<b.cfg[KK_TUPDATE].grid, b.cfg[KK_TUPDATE].threads, 0, st>>>(d, T, b.prm);
+      VLS_LAUNCH(b);
       b.prof.end(st, ps);
       ps = b.prof.begin(st, KK_TAPPLY);
       k_tapply<<<b.cfg[KK_TAPPLY].grid, b.cfg[KK_TAPPLY].threads, 0, st>>>(d, T, b.prm.theta); VLS_LAUNCH(b);
@@ -464,7 +466,7 @@ cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out) {
     H.use = 1;
     e = cudaGraphCreate(&g, 0);
     if (e == cudaSuccess) e = add_conditional(&w, g, nullptr, 0, cudaGraphCondTypeWhile, 1u, &H.loop, &body);
-    if (e == cudaSuccess) e = add_kernel(&n0, body, nullptr, 0, k_tupdate, dim3(b.cfg[KK_TUPDATE].grid), dim3(b.cfg[KK_TUPDATE].threads), d, T, b.prm);
+    if (e == cudaSuccess) e = add_kernel(&n0, body, nullptr, 0, T.phif ? k_tupdate<float> : k_tupdate<double>, dim3(b.cfg[KK_TUPDATE].grid), dim3(b.cfg[KK_TUPDATE].threads), d, T, b.prm);
     if (e == cudaSuccess) e = add_kernel(&n1, body, &n0, 1, k_tapply, dim3(b.cfg[KK_TAPPLY].grid), dim3(b.cfg[KK_TAPPLY].threads), d, T, b.prm.theta);
     if (e == cudaSuccess)
       e = add_kernel(&n2, body, &n1, 1, k_tfrontier, dim3(b.cfg[KK_TFRONTIER].grid), dim3(b.cfg[KK_TFRONTIER].threads), d, T, H,

@@ -29,16 +29,26 @@ constexpr int KMAX = 4;            // non-base layers that may meet at one verte
 constexpr int MAX_GROUP = 32;      // layers in one merge group
 constexpr int MAX_TRACES = 64;     // isoline traces per step (all problems)
 constexpr int TRACE_CAP = 1 << 16; // crossing edges per traced isoline
+constexpr int MASS_SLOTS = 16;     // accumulators per problem of the mass check (power of two)
+constexpr int MASS_SPREAD_MAXP = 64; // batches of at most this many problems spread them
 
 enum LayerState : int32_t { L_UNUSED = 0, L_ALIVE = 1, L_DEAD = 2, L_MERGED = 3, L_ENDED = 4 };
 enum NodeKind : int32_t { N_SEED = 0, N_SPLIT = 1, N_MERGE = 2, N_END = 3 };
 
 constexpr int LV_MAX = 64; // longest row of the register / local-memory row paths
 
+// Minimum resident blocks of 256 threads per SM that the frontier-update kernels are compiled
+// for (it caps their registers: 2 -> 128, 3 -> 80, 4 -> 64 per thread).  The rows are chains of
+// dependent gathers, so more resident warps hide more of their latency.
+#ifndef VLS_UPDATE_MINB
+#define VLS_UPDATE_MINB 3
+#endif
+
 struct Params {
   double mu, e, w, ah, dt, s, eps0, one_m_eps, theta;
   double lv[LV_MAX + 1];  // s / d: off-diagonal operator entry of a row with d kept neighbours
   double mun[KMAX + 2];   // mu / n for n phases meeting at a vertex
+  double mv[LV_MAX + 1];  // d / s: lumped mass of a row with d neighbours (m_v L_vu = 1, symmetric)
   // FP32 form: the same constants rounded to float, and the recheck margin
   double margin;
   float f_e, f_w, f_ah, f_dt, f_s, f_eps0, f_one_m_eps, f_theta, f_margin;
@@ -72,6 +82,11 @@ struct Dev {
   double *phi;       // FP64 form: layer values
   float *phif;       // FP32 form: layer values (non-null selects the FP32 form; phi unused)
   unsigned long long *nrecheck; // [2] rows redone in FP64: initial pass, tunnel passes
+  double *pmass;     // [P][mslots][2] this step's sum over frontier rows of m_v (L base)_v, and of its
+                     // terms' magnitudes, spread over mslots addresses per problem
+  int32_t mslots;    // a power of two: MASS_SLOTS for batches of few problems (their rows share a few
+                     // addresses), 1 for many (rows spread over many problems already)
+  double *pmres;     // [P] largest relative residual |sum| / magnitude over the steps so far
   int32_t *cover;
   int32_t *stamp;    // candidate dedup stamp (step id)
   int32_t *fmark;    // step at which the vertex was last in the frontier

@@ -52,7 +52,7 @@ def test_torus_fp32_parity(vls):
     s = meshgen.seed_vertex(0, m.nv)
     (g,), (o,) = run_pair(vls, [(m, [s])])
     assert o.status == 0
-    err, _, _, _ = assert_fp32_parity(g, o)
+    err, _, _, _ = assert_fp32_parity(g, o, m.X)
     assert g.stats["rechecks"] > 0
     assert g.stats["rechecks"] < g.stats["row_updates"]
     print(f"torus fp32: max |phi - oracle| = {err}, rechecks {g.stats['rechecks']} of "
@@ -64,7 +64,7 @@ def test_torus_fp32_state_each_phase(vls, steps):
     m = meshgen.torus(64, 32, 2.0, 0.7)
     s = meshgen.seed_vertex(0, m.nv)
     (g,), (o,) = run_pair(vls, [(m, [s])], max_steps=steps, tunnels=0)
-    assert_fp32_parity(g, o)
+    assert_fp32_parity(g, o, m.X)
 
 
 @pytest.mark.parametrize("name", ["chain2", "chain3", "capsules", "sphere", "torus_small"])
@@ -75,14 +75,14 @@ def test_shapes_fp32_parity(vls, name):
     seeds = [meshgen.seed_vertex(sd, m.nv) for sd in range(2)]
     gpu, orc = run_pair(vls, [(m, seeds)])
     for g, o in zip(gpu, orc):
-        assert_fp32_parity(g, o)
+        assert_fp32_parity(g, o, m.X)
 
 
 def test_tube_chain_small_fp32_batch(vls):
     """The tube-chain workload at grid scale 0.35 (8 tori, ~63k faces), 4 seeds in one batch."""
     probs = meshgen.workload(2, 0.35)
     gpu, orc = run_pair(vls, probs)
-    out = [assert_fp32_parity(g, o) for g, o in zip(gpu, orc)]
+    out = [assert_fp32_parity(g, o, probs[0][0].X) for g, o in zip(gpu, orc)]
     rows = sum(g.stats["row_updates"] for g in gpu)
     print(f"tube chain 0.35 fp32: record steps differing {[r for _, r, _, _ in out]}, cover steps differing "
           f"{[c for _, _, c, _ in out]}, tunnel loops differing {[t for _, _, _, t in out]}, "
@@ -95,7 +95,7 @@ def test_tube_chain_small_fp32_values_mid_run(vls, steps):
     m, seeds = meshgen.workload(2, 0.35)[0]
     gpu, orc = run_pair(vls, [(m, seeds)], max_steps=steps, tunnels=0)
     for g, o in zip(gpu, orc):
-        err, rec_bad, _, _ = assert_fp32_parity(g, o)
+        err, rec_bad, _, _ = assert_fp32_parity(g, o, m.X)
         if rec_bad == 0:
             assert err <= FP32_TOL
 
@@ -123,7 +123,7 @@ def test_fp32_margin_option(vls):
     m = meshgen.torus(24, 12)
     s = meshgen.seed_vertex(0, m.nv)
     (g,), (o,) = run_pair(vls, [(m, [s])], gpu_kw={"recheck_margin": 0.2})
-    assert_fp32_parity(g, o)
+    assert_fp32_parity(g, o, m.X)
     assert g.stats["rechecks"] >= 0.5 * g.stats["row_updates"]
     for bad in (0.0, -1.0, 0.5):
         with pytest.raises(RuntimeError):

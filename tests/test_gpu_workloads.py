@@ -131,7 +131,7 @@ def test_schwarz_p_oracle_parity(vls, oracle_results):
     g64 = run(vls, probs, "fp64", keep_state=1, record_steps=1)[0]
     assert_parity(g64, o)
     g32 = run(vls, probs, "fp32", keep_state=1, record_steps=1)[0]
-    assert_fp32_parity(g32, o)
+    assert_fp32_parity(g32, o, probs[0][0].X)
 
 
 def test_batch_full_size(vls, oracle_results):
@@ -151,7 +151,7 @@ def test_batch_full_size(vls, oracle_results):
     ok = [i for i in range(len(out)) if i not in stalled]
     check_properties([out[i] for i in ok], [genera[i] for i in ok])
     for i, o in zip(BATCH_SAMPLE, oracle_results["batch"]):
-        assert_fp32_parity(out[i], o)
+        assert_fp32_parity(out[i], o, flat[i][0].X)
     out64 = run(vls, probs, "fp64", keep_state=1, record_steps=1)
     for i, o in zip(BATCH_SAMPLE, oracle_results["batch"]):
         assert_parity(out64[i], o)
@@ -172,4 +172,4 @@ def test_gyroid_oracle_parity(vls, oracle_results):
     s = meshgen.seed_vertex(0, m.nv)
     assert o.status == 0 and 10 < len(o.handles) <= m.genus()
     assert_parity(run(vls, [(m, [s])], "fp64", keep_state=1, record_steps=1)[0], o)
-    assert_fp32_parity(run(vls, [(m, [s])], "fp32", keep_state=1, record_steps=1)[0], o)
+    assert_fp32_parity(run(vls, [(m, [s])], "fp32", keep_state=1, record_steps=1)[0], o, m.X)
