@@ -59,9 +59,14 @@ typedef enum {
  *                     (snap at eps0 or 1 - eps0, the level theta_iso) or where several layers
  *                     meet is recomputed in FP64 from the same stored inputs, and its values are
  *                     rounded to float without crossing any threshold.  FP64 is used for nothing
- *                     else on the step path.
+ *                     else on the step path but the mass check (vls_stats.mass_resid).
+ *   VLS_BF16_RECHECK  values stored as bfloat16 (8 significant bits); the step arithmetic is that of
+ *                     VLS_FP32_RECHECK on the widened values, with the same FP64 recheck, and every
+ *                     stored value is rounded to bfloat16 without crossing any threshold.  Halves the
+ *                     value bytes again; the coarser storage moves the trajectory away from the FP64
+ *                     one by far more than FP32 storage does (see vls_result_state).
  */
-typedef enum { VLS_FP64 = 0, VLS_FP32_RECHECK = 1 } vls_precision;
+typedef enum { VLS_FP64 = 0, VLS_FP32_RECHECK = 1, VLS_BF16_RECHECK = 2 } vls_precision;
 
 /*
  * Options.  Defaults (vls_default_options) are the paper's constants (Sec. 2,
@@ -77,7 +82,7 @@ typedef struct {
   double eps0;              /* snap: values below eps0 -> 0, above 1 - eps0 -> 1 */
   double theta_iso;         /* isoline level of handle loops, arrival level of tunnel passes */
   double lbar;              /* operator length scale; <= 0 selects eta / 4 */
-  double recheck_margin;    /* FP32 form: rows deciding within this of a threshold are redone in FP64; (0, 0.25) */
+  double recheck_margin;    /* FP32 / BF16 forms: rows deciding within this of a threshold are redone in FP64; (0, 0.25) */
   int32_t max_steps;        /* initial-pass step limit (per problem) */
   int32_t max_pass_steps;   /* tunnel-pass step limit (per pass) */
   int32_t tunnels;          /* 1: run the tunnel passes (Sec. 3.2) */
@@ -124,7 +129,7 @@ typedef struct {
   double ms_update, ms_pass_update;
   int64_t n_update, n_pass_update;
   int64_t h2d_bytes, d2h_bytes; /* batch-wide host<->device bytes of this call */
-  /* precision = VLS_FP32_RECHECK: rows of the initial pass / tunnel passes whose FP32 step had
+  /* precision = VLS_FP32_RECHECK or VLS_BF16_RECHECK: rows of the initial pass / tunnel passes whose FP32 step had
    * a decision within recheck_margin of its threshold (or several layers) and was redone in
    * FP64 (batch-wide); 0 in the FP64 form */
   int64_t rechecks, pass_rechecks;

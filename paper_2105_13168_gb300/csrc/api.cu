@@ -137,8 +137,8 @@ extern "C" vls_status vls_create(vls_ctx **ctx, const vls_options *o, void *stre
   if (!c) return VLS_ENOMEM;
   if (o) c->opt = *o;
   else vls_default_options(&c->opt);
-  if ((c->opt.precision != VLS_FP64 && c->opt.precision != VLS_FP32_RECHECK) ||
-      (c->opt.precision == VLS_FP32_RECHECK && !(c->opt.recheck_margin > 0.0 && c->opt.recheck_margin < 0.25))) {
+  if ((c->opt.precision != VLS_FP64 && c->opt.precision != VLS_FP32_RECHECK && c->opt.precision != VLS_BF16_RECHECK) ||
+      (c->opt.precision != VLS_FP64 && !(c->opt.recheck_margin > 0.0 && c->opt.recheck_margin < 0.25))) {
     delete c;
     return VLS_EINVAL;
   }
@@ -198,9 +198,10 @@ void layout_batch(Layout &L, Batch &b) {
   d.pupd = L.take<int64_t>(P);
   d.pev = L.take<int32_t>(4 * P);
   d.lay = L.take<int32_t>(V);
-  const bool f32 = b.opt.precision == VLS_FP32_RECHECK;
-  d.phi = f32 ? nullptr : L.take<double>(V);
-  d.phif = f32 ? L.take<float>(V) : nullptr;
+  const vls_precision pr = b.opt.precision;
+  d.phi = pr == VLS_FP64 ? L.take<double>(V) : nullptr;
+  d.phif = pr == VLS_FP32_RECHECK ? L.take<float>(V) : nullptr;
+  d.phih = pr == VLS_BF16_RECHECK ? L.take<__nv_bfloat16>(V) : nullptr;
   d.nrecheck = L.take<unsigned long long>(2);
   d.mslots = P <= (size_t)MASS_SPREAD_MAXP ? MASS_SLOTS : 1;
   d.pmass = L.take<double>(2 * (size_t)d.mslots * P);
@@ -292,9 +293,10 @@ void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut) {
   T.heoff = L.take<int32_t>(NP);
   T.hen = L.take<int32_t>(NP);
   T.flag = L.take<int8_t>(PV);
-  const bool f32 = b.opt.precision == VLS_FP32_RECHECK;
-  T.phi = f32 ? nullptr : L.take<double>(PV);
-  T.phif = f32 ? L.take<float>(PV) : nullptr;
+  const vls_precision pr = b.opt.precision;
+  T.phi = pr == VLS_FP64 ? L.take<double>(PV) : nullptr;
+  T.phif = pr == VLS_FP32_RECHECK ? L.take<float>(PV) : nullptr;
+  T.phih = pr == VLS_BF16_RECHECK ? L.take<__nv_bfloat16>(PV) : nullptr;
   T.T = L.take<int32_t>(PV);
   T.stamp = L.take<int32_t>(PV);
   T.fv[0] = L.take<int32_t>(PV);
@@ -629,7 +631,8 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     // ---- state init
     CK(cudaMemcpyAsync(d.pstatus, h_status.data(), sizeof(int32_t) * b.P, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(d.lay, 0, sizeof(int32_t) * b.V, st));
-    if (d.phif) CK(cudaMemsetAsync(d.phif, 0, sizeof(float) * b.V, st));
+    if (d.phih) CK(cudaMemsetAsync(d.phih, 0, sizeof(__nv_bfloat16) * b.V, st));
+    else if (d.phif) CK(cudaMemsetAsync(d.phif, 0, sizeof(float) * b.V, st));
     else CK(cudaMemsetAsync(d.phi, 0, sizeof(double) * b.V, st));
     CK(cudaMemsetAsync(d.nrecheck, 0, sizeof(unsigned long long) * 2, st));
     CK(cudaMemsetAsync(d.pmass, 0, sizeof(double) * 2 * d.mslots * b.P, st));
@@ -811,7 +814,8 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       CK(cudaMemcpyAsync(const_cast<int32_t *>(T.hen), hen.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
       b.h2d += (int64_t)sizeof(int32_t) * (7 * NP + 1);
       CK(cudaMemsetAsync(T.flag, 0, (size_t)PV, st));
-      if (T.phif) CK(cudaMemsetAsync(T.phif, 0, sizeof(float) * PV, st));
+      if (T.phih) CK(cudaMemsetAsync(T.phih, 0, sizeof(__nv_bfloat16) * PV, st));
+      else if (T.phif) CK(cudaMemsetAsync(T.phif, 0, sizeof(float) * PV, st));
       else CK(cudaMemsetAsync(T.phi, 0, sizeof(double) * PV, st));
       CK(cudaMemsetAsync(T.T, 0xff, sizeof(int32_t) * PV, st));
       CK(cudaMemsetAsync(T.stamp, 0, sizeof(int32_t) * PV, st));
@@ -887,7 +891,21 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
         err = cudaErrorUnknown;
         goto fail;
       }
-      if (d.phif) {
+      if (d.phih) {
+        std::vector<uint16_t> phih_all;
+        if (!d2h(phih_all, reinterpret_cast<const uint16_t *>(d.phih), b.V, st)) {
+          err = cudaErrorUnknown;
+          goto fail;
+        }
+        CK(cudaStreamSynchronize(st));
+        phi_all.resize(phih_all.size());
+        for (size_t k = 0; k < phih_all.size(); ++k) { // a bfloat16 is the high half of a float
+          const uint32_t bits = (uint32_t)phih_all[k] << 16;
+          float f;
+          memcpy(&f, &bits, sizeof f);
+          phi_all[k] = f;
+        }
+      } else if (d.phif) {
         std::vector<float> phif_all;
         if (!d2h(phif_all, d.phif, b.V, st)) {
           err = cudaErrorUnknown;

@@ -10,6 +10,8 @@
 //   epilogue per-problem termination, step limit, step records.
 // A frontier row is one thread: the Laplacian of each layer is a sequential sum over the
 // row in CSR order (diagonal last), the same rounding order as the FP64 oracle.
+#include <type_traits>
+
 #include "vls_batch.cuh"
 
 namespace vls {
@@ -31,7 +33,7 @@ template <int MAXD, class TV>
 __device__ __forceinline__ void row_f64(const Params &P, int nl, const int32_t *ls, int32_t lv, int32_t o, TV xv,
                                         const int32_t *nlay, const TV *nx, int32_t deg, double *out, double2 &mass) {
   const double Lv = P.lv[deg];
-  const double xvd = (double)xv;
+  const double xvd = to_f64(xv);
   const double xb = dsub(1.0, lv != 0 ? xvd : 0.0);
   double x[KMAX], lap[KMAX];
 #pragma unroll 1
@@ -42,7 +44,7 @@ __device__ __forceinline__ void row_f64(const Params &P, int nl, const int32_t *
 #pragma unroll
     for (int j = 0; j < MAXD; ++j) {
       if (j < deg) {
-        const double psi = nlay[j] == l ? (double)nx[j] : (nlay[j] < 0 ? plat : 0.0);
+        const double psi = nlay[j] == l ? to_f64(nx[j]) : (nlay[j] < 0 ? plat : 0.0);
         // terms are >= 0 and acc starts at +0: skipping a zero term leaves acc bit-identical
         if (val_pos(psi)) acc = dadd(acc, dmul(Lv, psi));
       }
@@ -56,7 +58,7 @@ __device__ __forceinline__ void row_f64(const Params &P, int nl, const int32_t *
   for (int j = 0; j < MAXD; ++j)
     if (j < deg) {
       if (nlay[j] == 0) accb = dadd(accb, Lv);                                         // Lv * 1.0
-      else if (val_lt1(nx[j])) accb = dadd(accb, dmul(Lv, dsub(1.0, (double)nx[j]))); // zero terms skipped
+      else if (val_lt1(nx[j])) accb = dadd(accb, dmul(Lv, dsub(1.0, to_f64(nx[j])))); // zero terms skipped
     }
   // mass check: m_v (L base)_v less the flux into frozen neighbours (never rows), and the
   // magnitude of its terms, sum_u base(u) + d base(v)
@@ -66,7 +68,7 @@ __device__ __forceinline__ void row_f64(const Params &P, int nl, const int32_t *
   for (int j = 0; j < MAXD; ++j)
     if (j < deg && nlay[j] < 0) {
       ++nfz;
-      if (val_lt1(nx[j])) fzb += 1.0 - (double)nx[j];
+      if (val_lt1(nx[j])) fzb += 1.0 - to_f64(nx[j]);
     }
   const double bnd = fzb - (double)nfz * xb;
   mass = make_double2(0.0, dadd(dmul(P.mv[deg], accb), dmul((double)deg, xb)));
@@ -81,19 +83,21 @@ __device__ __forceinline__ void row_f64(const Params &P, int nl, const int32_t *
 
 // FP32 row of the common case (one layer l and the base, Eq. (2) with n = 2).  Returns false
 // when a decision of the step lies within the recheck margin (the row is then redone in FP64).
-template <int MAXD>
-__device__ __forceinline__ bool row_f32(const Params &P, int32_t l, int32_t lv, int32_t o, float xv,
-                                        const int32_t *nlay, const float *nx, int32_t deg, double &out,
+template <int MAXD, class TN>
+__device__ __forceinline__ bool row_f32(const Params &P, int32_t l, int32_t lv, int32_t o, TN xvs,
+                                        const int32_t *nlay, const TN *nx, int32_t deg, double &out,
                                         double2 &mass) {
   const float Lv = P.f_lv[deg];
   const float plat = (o != 0 && l == o) ? 1.f : 0.f;
+  const float xv = to_f32(xvs);
   float acc = 0.f, accb = 0.f;
 #pragma unroll
   for (int j = 0; j < MAXD; ++j)
     if (j < deg) {
-      const float psi = nlay[j] == l ? nx[j] : (nlay[j] < 0 ? plat : 0.f);
+      const float xj = to_f32(nx[j]);
+      const float psi = nlay[j] == l ? xj : (nlay[j] < 0 ? plat : 0.f);
       acc = fmaf(Lv, psi, acc);
-      accb = fmaf(Lv, nlay[j] == 0 ? 1.f : 1.f - nx[j], accb);
+      accb = fmaf(Lv, nlay[j] == 0 ? 1.f : 1.f - xj, accb);
     }
   const float x = (lv == l) ? xv : 0.f;
   const float xb = 1.f - (lv != 0 ? xv : 0.f);
@@ -107,24 +111,24 @@ __device__ __forceinline__ bool row_f32(const Params &P, int32_t l, int32_t lv, 
   for (int j = 0; j < MAXD; ++j)
     if (j < deg && nlay[j] < 0) {
       ++nfz;
-      fzb += 1.f - nx[j];
+      fzb += 1.f - to_f32(nx[j]);
     }
   const double bnd = (double)fzb - (double)nfz * (double)xb;
   mass = make_double2(P.mv[deg] * (double)lapb - bnd, P.mv[deg] * (double)accb + (double)deg * (double)xb);
   float y;
   if (!vertex_update_f32(P, x, lap, xb, lapb, y)) return false;
-  out = (double)y;
+  out = round_keep<TN>((double)y, P.theta); // exact for float storage
   return true;
 }
 
 // FP32 form: the FP64 redo of a row from its gathered inputs (rounded to float keeping every
 // threshold's side), out of line so that the hot row keeps few registers.  Rare: a collision or
 // a decision within the margin.
-template <int MAXD>
-__device__ __noinline__ void row_redo(const Params &P, int nl, const int32_t *ls, int32_t lv, int32_t o, float xv,
-                                      const int32_t *nlay, const float *nx, int32_t deg, double *out, double2 &mass) {
-  row_f64<MAXD, float>(P, nl, ls, lv, o, xv, nlay, nx, deg, out, mass);
-  for (int q = 0; q < nl; ++q) out[q] = (double)f32_keep_side(out[q], P.theta);
+template <int MAXD, class TN>
+__device__ __noinline__ void row_redo(const Params &P, int nl, const int32_t *ls, int32_t lv, int32_t o, TN xv,
+                                      const int32_t *nlay, const TN *nx, int32_t deg, double *out, double2 &mass) {
+  row_f64<MAXD, TN>(P, nl, ls, lv, o, xv, nlay, nx, deg, out, mass);
+  for (int q = 0; q < nl; ++q) out[q] = round_keep<TN>(out[q], P.theta);
 }
 
 // One frontier row.  FP32 form: the common case (one layer and the base) in FP32, a row that
@@ -148,7 +152,7 @@ __device__ __forceinline__ int update_row(const Dev &d, const Params &P, int32_t
 #pragma unroll
     for (int j = 0; j < MAXD; ++j) {
       nlay[j] = (j < deg) ? d.lay[nu[j]] : 0;
-      nx[j] = (j < deg) ? ph[nu[j]] : (TV)0;
+      nx[j] = (j < deg) ? ph[nu[j]] : TV(0.0f);
     }
   }
   const int32_t lv = d.lay[v];
@@ -186,13 +190,13 @@ __device__ __forceinline__ int update_row(const Dev &d, const Params &P, int32_t
   if (!hb || nl == 0) { d.onl[i] = -1; return ROW_DONE; }
   double out[KMAX];
   int outcome = ROW_DONE;
-  if constexpr (sizeof(TV) == sizeof(float) && FAST) {
-    // FP32 form: one layer in FP32; several layers (a collision: merge arithmetic follows)
-    // and rows near a decision are redone in FP64 from copies of the gathered inputs (only
-    // the copies live in local memory)
+  if constexpr (!std::is_same<TV, double>::value && FAST) {
+    // FP32 / BF16 forms: one layer in FP32; several layers (a collision: merge arithmetic
+    // follows) and rows near a decision are redone in FP64 from copies of the gathered inputs
+    // (only the copies live in local memory)
     if (nl != 1 || !row_f32<MAXD>(P, ls[0], lv, o, xv, nlay, nx, deg, out[0], mass)) {
       int32_t cl[MAXD], cls[KMAX];
-      float cx[MAXD];
+      TV cx[MAXD];
       double co[KMAX];
 #pragma unroll
       for (int j = 0; j < MAXD; ++j) { cl[j] = nlay[j]; cx[j] = nx[j]; }
@@ -203,11 +207,11 @@ __device__ __forceinline__ int update_row(const Dev &d, const Params &P, int32_t
       for (int q = 0; q < KMAX; ++q) out[q] = co[q];
       outcome = ROW_REDONE;
     }
-  } else if constexpr (sizeof(TV) == sizeof(float)) {
+  } else if constexpr (!std::is_same<TV, double>::value) {
     row_f64<MAXD, TV>(P, nl, ls, lv, o, xv, nlay, nx, deg, out, mass);
 #pragma unroll
     for (int q = 0; q < KMAX; ++q)
-      if (q < nl) out[q] = (double)f32_keep_side(out[q], P.theta);
+      if (q < nl) out[q] = round_keep<TV>(out[q], P.theta);
     outcome = ROW_REDONE;
   } else {
     row_f64<MAXD, TV>(P, nl, ls, lv, o, xv, nlay, nx, deg, out, mass);
@@ -291,7 +295,7 @@ __device__ __forceinline__ void update_rows(const Dev &d, const Params &P) {
       atomicAdd(&d.pmass[((int64_t)p * d.mslots + ls) * 2 + 1], mass.y);
     }
   }
-  if constexpr (sizeof(TV) == sizeof(float)) {
+  if constexpr (!std::is_same<TV, double>::value) {
     redo = __reduce_add_sync(0xffffffffu, redo);
     if ((threadIdx.x & 31) == 0 && redo) atomicAdd(&d.nrecheck[0], (unsigned long long)redo);
   }
@@ -674,7 +678,8 @@ cudaError_t build_initial_graph(Batch &b, cudaGraph_t *out) {
   GK(add_conditional(&w, g, nullptr, 0, cudaGraphCondTypeWhile, 1u, &H.loop, &body));
   GK(cudaGraphConditionalHandleCreate(&H.merge, body, 0u, cudaGraphCondAssignDefault));
   GK(cudaGraphConditionalHandleCreate(&H.split, body, 0u, cudaGraphCondAssignDefault));
-  GK(add_kernel(&n_upd, body, nullptr, 0, b.d.phif ? k_update<float> : k_update<double>, G(KK_UPDATE), T(KK_UPDATE),
+  GK(add_kernel(&n_upd, body, nullptr, 0, b.d.phih ? k_update<__nv_bfloat16> : b.d.phif ? k_update<float> : k_update<double>,
+                G(KK_UPDATE), T(KK_UPDATE),
                 b.d, b.prm));
   GK(add_kernel(&n_app, body, &n_upd, 1, k_apply, G(KK_APPLY), T(KK_APPLY), b.d, H));
   {
@@ -717,7 +722,8 @@ cudaError_t initial_step_host(Batch &b) {
   Handles H{};
   H.use = 0;
   long ps = b.prof.begin(st, KK_UPDATE);
-  if (d.phif) k_update<float><<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm);
+  if (d.phih) k_update<__nv_bfloat16><<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm);
+  else if (d.phif) k_update<float><<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm);
   else k_update<double><<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm);
   VLS_LAUNCH(b);
   b.prof.end(st, ps);
@@ -743,8 +749,10 @@ cudaError_t initial_step_host(Batch &b) {
 }
 
 void configure_initial(Batch &b) {
-  b.cfg[KK_UPDATE] = b.opt.precision == VLS_FP32_RECHECK ? row_cfg(b, k_update<float>, KK_UPDATE, 128)
-                                                           : row_cfg(b, k_update<double>, KK_UPDATE, 128); // thread per row
+  // one thread per frontier row
+  b.cfg[KK_UPDATE] = b.opt.precision == VLS_BF16_RECHECK   ? row_cfg(b, k_update<__nv_bfloat16>, KK_UPDATE, 128)
+                     : b.opt.precision == VLS_FP32_RECHECK ? row_cfg(b, k_update<float>, KK_UPDATE, 128)
+                                                           : row_cfg(b, k_update<double>, KK_UPDATE, 128);
   b.cfg[KK_APPLY] = row_cfg(b, k_apply, KK_APPLY, 128);
   b.cfg[KK_HOOK] = b.hook_variant == 1 ? row_cfg(b, k_band_hook_row, KK_HOOK, 128) : row_cfg(b, k_band_hook, KK_HOOK, 256);
   b.cfg[KK_COUNT] = row_cfg(b, k_band_count, KK_COUNT, 128);

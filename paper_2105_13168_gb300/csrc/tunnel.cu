@@ -14,6 +14,8 @@
 //            the handle loop by the shorter way to a crossing edge ending at b*.
 // Only rows whose closed neighbourhood holds both phases change, so each step updates the
 // frontier rows only (exact).
+#include <type_traits>
+
 #include "vls_batch.cuh"
 
 namespace vls {
@@ -53,10 +55,14 @@ __device__ __forceinline__ bool kept(const Dev &d, const TDev &T, int32_t q, int
 template <class TV> __device__ __forceinline__ const TV *tph_arr(const TDev &T);
 template <> __device__ __forceinline__ const double *tph_arr<double>(const TDev &T) { return T.phi; }
 template <> __device__ __forceinline__ const float *tph_arr<float>(const TDev &T) { return T.phif; }
-__device__ __forceinline__ double tph_ld(const TDev &T, int32_t i) { return T.phif ? (double)T.phif[i] : T.phi[i]; }
+template <> __device__ __forceinline__ const __nv_bfloat16 *tph_arr<__nv_bfloat16>(const TDev &T) { return T.phih; }
+__device__ __forceinline__ double tph_ld(const TDev &T, int32_t i) {
+  return T.phih ? to_f64(T.phih[i]) : T.phif ? (double)T.phif[i] : T.phi[i];
+}
 // a row output (exactly representable in float in the FP32 form) into the pass state
 __device__ __forceinline__ void tph_st(const TDev &T, int32_t i, double x) {
-  if (T.phif) T.phif[i] = (float)x;
+  if (T.phih) T.phih[i] = __double2bfloat16(x);
+  else if (T.phif) T.phif[i] = (float)x;
   else T.phi[i] = x;
 }
 
@@ -110,7 +116,7 @@ __device__ __forceinline__ int gather_kept(const Dev &d, const TDev &T, int32_t 
   for (int j = 0; j < MAXD; ++j) {
     const int32_t c = (j < deg) ? d.cover[nu[j]] : -1;
     const int8_t f = (j < deg) ? T.flag[base + (nu[j] - voff)] : (int8_t)0;
-    nx[j] = (j < deg) ? ph[base + (nu[j] - voff)] : (TV)0;
+    nx[j] = (j < deg) ? ph[base + (nu[j] - voff)] : TV(0.0f);
     bool k = j < deg && c >= 0 && c <= step;
     if (k && (((fl & F_SRC) && (f & F_TGT)) || ((fl & F_TGT) && (f & F_SRC)))) k = !is_cut(T, q, b + j);
     if (k) kp |= 1ull << j;
@@ -124,16 +130,16 @@ template <int MAXD, class TV>
 __device__ __forceinline__ double trow_f64(const Params &P, uint64_t kp, int dh, const TV *nx, TV xs) {
   const double Lv = dh > 0 ? P.lv[dh] : 0.0;
   const double diag = dh > 0 ? -P.s : 0.0;
-  const double x = (double)xs;
+  const double x = to_f64(xs);
   double acc = 0.0, accb = 0.0;
   // terms are >= 0 and the sums start at +0: zero terms are skipped (bit-identical)
 #pragma unroll
   for (int j = 0; j < MAXD; ++j)
-    if (((kp >> j) & 1ull) && val_pos(nx[j])) acc = dadd(acc, dmul(Lv, (double)nx[j]));
+    if (((kp >> j) & 1ull) && val_pos(nx[j])) acc = dadd(acc, dmul(Lv, to_f64(nx[j])));
   acc = dadd(acc, dmul(diag, x));
 #pragma unroll
   for (int j = 0; j < MAXD; ++j)
-    if (((kp >> j) & 1ull) && val_lt1(nx[j])) accb = dadd(accb, dmul(Lv, dsub(1.0, (double)nx[j])));
+    if (((kp >> j) & 1ull) && val_lt1(nx[j])) accb = dadd(accb, dmul(Lv, dsub(1.0, to_f64(nx[j]))));
   const double xb = dsub(1.0, x);
   accb = dadd(accb, dmul(diag, xb));
   double out;
@@ -141,22 +147,25 @@ __device__ __forceinline__ double trow_f64(const Params &P, uint64_t kp, int dh,
   return out;
 }
 
-// FP32 pass row; false when a decision lies within the recheck margin.
-template <int MAXD>
-__device__ __forceinline__ bool trow_f32(const Params &P, uint64_t kp, int dh, const float *nx, float x, double &out) {
+// FP32 pass row (values stored as float or bfloat16); false when a decision lies within the
+// recheck margin.
+template <int MAXD, class TN>
+__device__ __forceinline__ bool trow_f32(const Params &P, uint64_t kp, int dh, const TN *nx, TN xs, double &out) {
   if (dh == 0) return false;
   const float Lv = P.f_lv[dh];
+  const float x = to_f32(xs);
   float acc = 0.f, accb = 0.f;
 #pragma unroll
   for (int j = 0; j < MAXD; ++j)
     if ((kp >> j) & 1ull) {
-      acc = fmaf(Lv, nx[j], acc);
-      accb = fmaf(Lv, 1.f - nx[j], accb);
+      const float xj = to_f32(nx[j]);
+      acc = fmaf(Lv, xj, acc);
+      accb = fmaf(Lv, 1.f - xj, accb);
     }
   const float xb = 1.f - x;
   float y;
   if (!vertex_update_f32(P, x, fmaf(-P.f_s, x, acc), xb, fmaf(-P.f_s, xb, accb), y)) return false;
-  out = (double)y;
+  out = round_keep<TN>((double)y, P.theta); // exact for float storage
   return true;
 }
 
@@ -174,9 +183,9 @@ __device__ __forceinline__ bool tupdate_row(const Dev &d, const TDev &T, const P
   const TV x = tph_arr<TV>(T)[idx];
   double out;
   bool redo = false;
-  if constexpr (sizeof(TV) == sizeof(float)) {
+  if constexpr (!std::is_same<TV, double>::value) {
     if (!trow_f32<MAXD>(P, kp, dh, nx, x, out)) {
-      out = (double)f32_keep_side(trow_f64<MAXD, TV>(P, kp, dh, nx, x), P.theta);
+      out = round_keep<TV>(trow_f64<MAXD, TV>(P, kp, dh, nx, x), P.theta);
       redo = true;
     }
   } else {
@@ -202,11 +211,11 @@ __device__ __forceinline__ void tupdate_rows(const Dev &d, const TDev &T, const 
   FOR_ROWS(i, nF) {
     const int32_t v = fv[i], q = fq[i];
     const int32_t deg = d.rp[v + 1] - d.rp[v];
-    if (deg <= 16) redo += tupdate_row<16, TV>(d, T, P, i, q, v);
+    if (deg <= 12) redo += tupdate_row<12, TV>(d, T, P, i, q, v);
     else if (deg <= 64) redo += tupdate_row_wide<TV>(d, T, P, i, q, v);
     else T.onew[i] = tph_ld(T, T.pbase[q] + (v - d.voff[T.pprob[q]]));
   }
-  if constexpr (sizeof(TV) == sizeof(float)) {
+  if constexpr (!std::is_same<TV, double>::value) {
     redo = __reduce_add_sync(0xffffffffu, redo);
     if ((threadIdx.x & 31) == 0 && redo) atomicAdd(&d.nrecheck[1], (unsigned long long)redo);
   }
@@ -247,7 +256,7 @@ template <class TV> __device__ __forceinline__ uint32_t tgives(TV x) {
   return (val_pos(x) ? 1u : 0u) | (val_lt1(x) ? 2u : 0u);
 }
 __device__ __forceinline__ uint32_t tgives_at(const TDev &T, int32_t i) {
-  return T.phif ? tgives(T.phif[i]) : tgives(T.phi[i]);
+  return T.phih ? tgives(T.phih[i]) : T.phif ? tgives(T.phif[i]) : tgives(T.phi[i]);
 }
 
 // GL-lane groups per row, lane j takes the row's neighbour j (rows longer than GL loop).
@@ -412,7 +421,8 @@ __global__ void k_tctl_set(int32_t *ctl, int32_t idx, int32_t v) { ctl[idx] = v;
 }  // namespace
 
 void configure_tunnel(Batch &b) {
-  b.cfg[KK_TUPDATE] = b.opt.precision == VLS_FP32_RECHECK ? row_cfg(b, k_tupdate<float>, KK_TUPDATE, 128)
+  b.cfg[KK_TUPDATE] = b.opt.precision == VLS_BF16_RECHECK   ? row_cfg(b, k_tupdate<__nv_bfloat16>, KK_TUPDATE, 128)
+                      : b.opt.precision == VLS_FP32_RECHECK ? row_cfg(b, k_tupdate<float>, KK_TUPDATE, 128)
                                                             : row_cfg(b, k_tupdate<double>, KK_TUPDATE, 128);
   b.cfg[KK_TAPPLY] = row_cfg(b, k_tapply, KK_TAPPLY, 128);
   b.cfg[KK_TFRONTIER] = row_cfg(b, k_tfrontier, KK_TFRONTIER, 256);
@@ -440,7 +450,8 @@ cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out) {
     const int sync_every = b.opt.sync_interval > 0 ? b.opt.sync_interval : 16;
     for (int32_t tau = 1;; ++tau) {
       long ps = b.prof.begin(st, KK_TUPDATE);
-      if (T.phif) k_tupdate<float><<<b.cfg[KK_TUPDATE].grid, b.cfg[KK_TUPDATE].threads, 0, st>>>(d, T, b.prm);
+      if (T.phih) k_tupdate<__nv_bfloat16><<<b.cfg[KK_TUPDATE].grid, b.cfg[KK_TUPDATE].threads, 0, st>>>(d, T, b.prm);
+      else if (T.phif) k_tupdate<float><<<b.cfg[KK_TUPDATE].grid, b.cfg[KK_TUPDATE].threads, 0, st>>>(d, T, b.prm);
       else k_tupdate<double><<<b.cfg[KK_TUPDATE].grid, b.cfg[KK_TUPDATE].threads, 0, st>>>(d, T, b.prm);
       VLS_LAUNCH(b);
       b.prof.end(st, ps);
@@ -466,7 +477,7 @@ cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out) {
     H.use = 1;
     e = cudaGraphCreate(&g, 0);
     if (e == cudaSuccess) e = add_conditional(&w, g, nullptr, 0, cudaGraphCondTypeWhile, 1u, &H.loop, &body);
-    if (e == cudaSuccess) e = add_kernel(&n0, body, nullptr, 0, T.phif ? k_tupdate<float> : k_tupdate<double>, dim3(b.cfg[KK_TUPDATE].grid), dim3(b.cfg[KK_TUPDATE].threads), d, T, b.prm);
+    if (e == cudaSuccess) e = add_kernel(&n0, body, nullptr, 0, T.phih ? k_tupdate<__nv_bfloat16> : T.phif ? k_tupdate<float> : k_tupdate<double>, dim3(b.cfg[KK_TUPDATE].grid), dim3(b.cfg[KK_TUPDATE].threads), d, T, b.prm);
     if (e == cudaSuccess) e = add_kernel(&n1, body, &n0, 1, k_tapply, dim3(b.cfg[KK_TAPPLY].grid), dim3(b.cfg[KK_TAPPLY].threads), d, T, b.prm.theta);
     if (e == cudaSuccess)
       e = add_kernel(&n2, body, &n1, 1, k_tfrontier, dim3(b.cfg[KK_TFRONTIER].grid), dim3(b.cfg[KK_TFRONTIER].threads), d, T, H,

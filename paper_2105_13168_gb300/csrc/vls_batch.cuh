@@ -37,6 +37,7 @@ struct TDev {
   int8_t *flag;        // [pass-vertex] bit0 source, bit1 target
   double *phi;         // [pass-vertex] FP64 form
   float *phif;         // [pass-vertex] FP32 form (non-null selects it; phi unused)
+  __nv_bfloat16 *phih; // [pass-vertex] BF16 form (non-null selects it; phi, phif unused)
   int32_t *T;          // [pass-vertex] arrival step (-1 unreached)
   int32_t *stamp;      // [pass-vertex]
   int32_t *fv[2], *fq[2];  // frontier (vertex, pass)

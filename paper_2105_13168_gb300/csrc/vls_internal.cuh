@@ -18,6 +18,7 @@
 //   global - lbase[p] (1 = seed layer, then creation order).
 #pragma once
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -81,6 +82,7 @@ struct Dev {
   int32_t *lay;
   double *phi;       // FP64 form: layer values
   float *phif;       // FP32 form: layer values (non-null selects the FP32 form; phi unused)
+  __nv_bfloat16 *phih; // BF16 form: layer values (non-null selects the BF16 form; phi, phif unused)
   unsigned long long *nrecheck; // [2] rows redone in FP64: initial pass, tunnel passes
   double *pmass;     // [P][mslots][2] this step's sum over frontier rows of m_v (L base)_v, and of its
                      // terms' magnitudes, spread over mslots addresses per problem
@@ -225,6 +227,15 @@ __device__ __forceinline__ bool val_band(double x) { return val_pos(x) && val_lt
 __device__ __forceinline__ bool val_pos(float x) { return __float_as_int(x) > 0; }
 __device__ __forceinline__ bool val_lt1(float x) { return __float_as_int(x) < 0x3F800000; }
 __device__ __forceinline__ bool val_band(float x) { return val_pos(x) && val_lt1(x); }
+__device__ __forceinline__ bool val_pos(__nv_bfloat16 x) { return (int16_t)__bfloat16_as_ushort(x) > 0; }
+__device__ __forceinline__ bool val_lt1(__nv_bfloat16 x) { return (int16_t)__bfloat16_as_ushort(x) < 0x3F80; }
+__device__ __forceinline__ bool val_band(__nv_bfloat16 x) { return val_pos(x) && val_lt1(x); }
+// exact widening of a stored value
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return (double)x; }
+__device__ __forceinline__ double to_f64(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
 
 // ------------------------------------------------------------ row loops
 // Grid-stride loops over the n rows of a frontier list that spread warps over the whole grid:
@@ -249,16 +260,22 @@ __device__ __forceinline__ int32_t group_lane() { return (int32_t)(threadIdx.x &
 __device__ __forceinline__ unsigned group_mask() { return ((1u << GL) - 1u) << (threadIdx.x & (32 - GL)); }
 
 // ------------------------------------------------------------ stored values
-// The layer value of a vertex is stored as double (FP64 form) or float (FP32 form, d.phif
-// non-null).  Readers that only test a value use the bit tests above on the stored type.
-__device__ __forceinline__ double ph_ld(const Dev &d, int32_t v) { return d.phif ? (double)d.phif[v] : d.phi[v]; }
-__device__ __forceinline__ bool ph_lt1(const Dev &d, int32_t v) { return d.phif ? val_lt1(d.phif[v]) : val_lt1(d.phi[v]); }
+// The layer value of a vertex is stored as double (FP64 form), float (FP32 form, d.phif
+// non-null) or bfloat16 (BF16 form, d.phih non-null).  Readers that only test a value use the
+// bit tests above on the stored type.
+__device__ __forceinline__ double ph_ld(const Dev &d, int32_t v) {
+  return d.phih ? to_f64(d.phih[v]) : d.phif ? (double)d.phif[v] : d.phi[v];
+}
+__device__ __forceinline__ bool ph_lt1(const Dev &d, int32_t v) {
+  return d.phih ? val_lt1(d.phih[v]) : d.phif ? val_lt1(d.phif[v]) : val_lt1(d.phi[v]);
+}
 __device__ __forceinline__ bool ph_band(const Dev &d, int32_t v) {
-  return d.phif ? val_band(d.phif[v]) : val_band(d.phi[v]);
+  return d.phih ? val_band(d.phih[v]) : d.phif ? val_band(d.phif[v]) : val_band(d.phi[v]);
 }
 template <class TV> __device__ __forceinline__ const TV *ph_arr(const Dev &d);
 template <> __device__ __forceinline__ const double *ph_arr<double>(const Dev &d) { return d.phi; }
 template <> __device__ __forceinline__ const float *ph_arr<float>(const Dev &d) { return d.phif; }
+template <> __device__ __forceinline__ const __nv_bfloat16 *ph_arr<__nv_bfloat16>(const Dev &d) { return d.phih; }
 
 // FP32 storage of an FP64 value without moving it across any threshold that later steps test
 // on stored values: 0 < x, x < 1 and x >= theta keep their truth value (x in [0, 1]).  Only
@@ -273,14 +290,38 @@ __device__ __forceinline__ float f32_keep_side(double x, double theta) {
   else if (x >= theta && fd < theta) bits += 1;
   return __int_as_float(bits);
 }
-// a value of a row output (exactly representable in float in the FP32 form) into the state
+// The same for bfloat16 storage (8 significant bits): the nearest bfloat16, then one step
+// back towards x's side of 0, 1 or theta if the rounding crossed it.
+__device__ __forceinline__ __nv_bfloat16 bf16_keep_side(double x, double theta) {
+  const __nv_bfloat16 h = __double2bfloat16(x);
+  const double hd = to_f64(h);
+  uint16_t bits = __bfloat16_as_ushort(h);
+  if (x > 0.0 && !(hd > 0.0)) bits = 1;                   // smallest positive bfloat16
+  else if (x < 1.0 && !(hd < 1.0)) bits = 0x3F7F;         // largest bfloat16 below 1
+  else if (x < theta && hd >= theta) bits -= 1;
+  else if (x >= theta && hd < theta) bits += 1;
+  return __ushort_as_bfloat16(bits);
+}
+// Rounding of an FP64 value to the stored type keeping its side of every threshold (the FP64
+// form stores it as is).
+template <class TV> __device__ __forceinline__ double round_keep(double x, double theta);
+template <> __device__ __forceinline__ double round_keep<double>(double x, double) { return x; }
+template <> __device__ __forceinline__ double round_keep<float>(double x, double theta) {
+  return (double)f32_keep_side(x, theta);
+}
+template <> __device__ __forceinline__ double round_keep<__nv_bfloat16>(double x, double theta) {
+  return to_f64(bf16_keep_side(x, theta));
+}
+// a value of a row output (exactly representable in the stored type) into the state
 __device__ __forceinline__ void ph_st(const Dev &d, int32_t v, double x) {
-  if (d.phif) d.phif[v] = (float)x;
+  if (d.phih) d.phih[v] = __double2bfloat16(x);
+  else if (d.phif) d.phif[v] = (float)x;
   else d.phi[v] = x;
 }
-// any FP64 value into the state (FP32 form: rounded keeping its side of every threshold)
+// any FP64 value into the state (FP32 / BF16 forms: rounded keeping its side of every threshold)
 __device__ __forceinline__ void ph_st_round(const Dev &d, const Params &P, int32_t v, double x) {
-  if (d.phif) d.phif[v] = f32_keep_side(x, P.theta);
+  if (d.phih) d.phih[v] = bf16_keep_side(x, P.theta);
+  else if (d.phif) d.phif[v] = f32_keep_side(x, P.theta);
   else d.phi[v] = x;
 }
 

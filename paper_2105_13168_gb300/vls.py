@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libvls.so")
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOTMANIFOLD", 3: "ENONORIENTABLE", 4: "EDISCONNECTED",
           5: "EMAXSTEPS", 6: "ESLOTS", 7: "ELAYERS", 8: "ELOOPFAIL", 9: "ETIMEOUT", 10: "ENOMEM",
           11: "ECUDA", 12: "ESTALL", 13: "ETOOLARGE"}
-VLS_FP64, VLS_FP32_RECHECK = 0, 1
+VLS_FP64, VLS_FP32_RECHECK, VLS_BF16_RECHECK = 0, 1, 2
 
 
 class vls_options(ctypes.Structure):
@@ -113,13 +113,12 @@ def load(path: str = LIB_PATH):
 
 
 # ----------------------------------------------------------------- C-named wrappers
-VLS_FP64, VLS_FP32_RECHECK = 0, 1
-PRECISION = {"fp64": VLS_FP64, "fp32": VLS_FP32_RECHECK}
+PRECISION = {"fp64": VLS_FP64, "fp32": VLS_FP32_RECHECK, "bf16": VLS_BF16_RECHECK}
 
 
 def vls_default_options(**overrides) -> vls_options:
     """Defaults of the library with fields overridden by keyword; precision may be given as
-    "fp64" / "fp32" (VLS_FP32_RECHECK) or as the enum value."""
+    "fp64" / "fp32" (VLS_FP32_RECHECK) / "bf16" (VLS_BF16_RECHECK) or as the enum value."""
     o = vls_options()
     load().vls_default_options(ctypes.byref(o))
     for k, v in overrides.items():

@@ -1,0 +1,132 @@
+"""The BF16 form on the GPU: layer values stored as bfloat16 (8 significant bits), the step
+arithmetic of the FP32 form on the widened values, rows deciding near a threshold redone in FP64,
+every stored value rounded without crossing a threshold.
+
+Rounding every stored value to 8 bits moves the trajectory away from the FP64 one by far more
+than FP32 storage (about 3e-3 to 1e-2 against 4e-7 after 60 steps), so event steps and the
+geometry of the loops differ from the oracle's.  What the tests require is the topology, checked
+against the oracle and against the mathematics:
+  - the event kinds in order and the layer table (the Reeb graph's topology) equal the oracle's
+    (on the tori, chains, capsules, sphere and the small tube chain);
+  - as many handle loops and tunnel loops as the oracle finds (the genus from the Euler
+    characteristic where every handle is resolved), the Reeb graph's cycle rank equal to it;
+  - every loop a closed, non-contractible cycle whose cut leaves the surface connected, the
+    handle classes and the tunnel classes each of full rank;
+  - every stored value a bfloat16, the FP64 mass check at FP32 rounding level.
+"""
+import numpy as np
+import pytest
+
+import meshgen
+import oracle
+from topology import Topo, gf2_rank
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vls():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_13168_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_2105_13168_gb300 as v
+
+    v.load()
+    return v
+
+
+def check_loops(m, p, nloops):
+    """Counts, Reeb cycle rank and the homology of every loop (tree-cotree classes, cut tests)."""
+    assert p.status == 0, p.status_name
+    assert len(p.handles) == len(p.tunnels) == nloops
+    assert p.reeb_cycle_rank() == nloops
+    topo = Topo(m.F, m.nv)
+    ch, ct = [], []
+    for h, t in zip(p.handles, p.tunnels):
+        assert t.status == 0
+        x = topo.crossing_edges(h.edges)
+        z = topo.vertex_cycle_edges(t.verts)
+        assert topo.is_dual_cycle(x) and not topo.dual_is_null(x) and topo.cut_connected_dual(x)
+        assert topo.is_primal_cycle(z) and not topo.primal_is_null(z) and topo.cut_connected_primal(z)
+        ch.append(topo.class_dual(x))
+        ct.append(topo.class_primal(z))
+    if nloops:
+        assert gf2_rank(np.array(ch)) == nloops and gf2_rank(np.array(ct)) == nloops
+
+
+def check_storage(p):
+    """Every stored value is a bfloat16 in [0, 1] (the high half of a float)."""
+    f = p.phi.astype(np.float32)
+    assert np.array_equal(f.astype(np.float64), p.phi)
+    assert ((f.view(np.uint32) & 0xFFFF) == 0).all()
+    assert (p.phi >= 0).all() and (p.phi <= 1).all()
+
+
+SHAPES = {"torus": lambda: meshgen.torus(64, 32, 2.0, 0.7), "torus_small": lambda: meshgen.torus(24, 12),
+          "chain2": lambda: meshgen.tube_chain(2, 64), "chain3": lambda: meshgen.tube_chain(3, 80),
+          "capsules": lambda: meshgen.capsules(5, 60), "sphere": lambda: meshgen.sphere(28)}
+
+
+@pytest.mark.parametrize("name", sorted(SHAPES))
+def test_shapes_bf16_topology(vls, name):
+    m = SHAPES[name]()
+    seeds = [meshgen.seed_vertex(sd, m.nv) for sd in range(2)]
+    out = vls.detect([(m, seeds)], precision="bf16", keep_state=1, record_steps=1)
+    for s, g in zip(seeds, out):
+        o = oracle.detect(m, s)
+        assert o.status == 0 and g.genus == o.genus == m.genus()
+        assert [k for k, _ in g.events()] == [k for k, _ in o.events()]
+        assert np.array_equal(g.layers, o.layers)
+        check_loops(m, g, len(o.handles))
+        check_storage(g)
+        assert 0.0 < g.stats["mass_resid"] <= 1e-5
+        assert 0 < g.stats["rechecks"] < g.stats["row_updates"]
+
+
+def test_tube_chain_small_bf16_batch(vls):
+    """The tube-chain workload at grid scale 0.35 (8 tori, ~63k faces), 4 seeds in one batch."""
+    probs = meshgen.workload(2, 0.35)
+    m, seeds = probs[0]
+    out = vls.detect(probs, precision="bf16", keep_state=1)
+    for s, g in zip(seeds, out):
+        o = oracle.detect(m, s)
+        assert [k for k, _ in g.events()] == [k for k, _ in o.events()]
+        assert np.array_equal(g.layers, o.layers)
+        check_loops(m, g, m.genus())
+        check_storage(g)
+
+
+def test_gyroid_small_bf16(vls):
+    """A 2-period gyroid at the full gyroid workload's sampling density (BF16 is that workload's
+    form).  The diffuse band crosses the thinnest of its 27 handles without an event, and which of
+    those it resolves depends on the trajectory: the BF16 form may resolve a slightly different
+    set than the FP32 form (and its Reeb graph may differ by a short-lived split child).  Every
+    loop it finds must be a valid non-contractible cycle, with full rank."""
+    m = meshgen.jitter(meshgen.gyroid(2, 76), 0.05, 5)
+    s = meshgen.seed_vertex(0, m.nv)
+    g = vls.detect([(m, [s])], precision="bf16", keep_state=1)[0]
+    f = vls.detect([(m, [s])], precision="fp32")[0]
+    assert 10 < len(f.handles) <= m.genus() and 10 < len(g.handles) <= m.genus()
+    assert abs(len(g.handles) - len(f.handles)) <= 2
+    check_loops(m, g, len(g.handles))
+    check_storage(g)
+    print(f"gyroid 2 periods (genus {m.genus()}): {len(g.handles)} handle and tunnel loops in BF16, "
+          f"{len(f.handles)} in FP32")
+
+
+@pytest.mark.parametrize("name", ["torus", "chain3"])
+def test_bf16_values_mid_run(vls, name):
+    """After 60 steps the BF16 values lie within 2e-2 of the FP64 oracle's (8-bit storage,
+    rounded at every step); the FP32 form on the same problem within 2e-6."""
+    m = SHAPES[name]()
+    s = meshgen.seed_vertex(0, m.nv)
+    o = oracle.detect(m, s, max_steps=60, tunnels=0)
+    g = vls.detect([(m, [s])], precision="bf16", keep_state=1, max_steps=60, tunnels=0)[0]
+    f = vls.detect([(m, [s])], precision="fp32", keep_state=1, max_steps=60, tunnels=0)[0]
+    eb = float(np.abs(g.phi - o.phi).max())
+    ef = float(np.abs(f.phi - o.phi).max())
+    assert eb <= 2e-2 and ef <= 2e-6
+    print(f"{name} after 60 steps: max |phi - oracle| BF16 {eb:.2e}, FP32 {ef:.2e}")

@@ -158,12 +158,14 @@ def test_batch_full_size(vls, oracle_results):
 
 
 def test_gyroid_full_size(vls):
+    """The gyroid workload in its own form: BF16 values, FP32 arithmetic, FP64 recheck."""
     probs = meshgen.workload(5)
     m = probs[0][0]
     assert m.nf > 20_000_000
-    out = run(vls, probs, "fp32")
+    out = run(vls, probs, "bf16")
     check_properties(out, [m.genus()], exact_genus=False)
-    print(f"gyroid full size: {len(out[0].handles)} handle and tunnel loops of genus {m.genus()}")
+    assert out[0].stats["mass_resid"] <= 1e-5
+    print(f"gyroid full size (BF16): {len(out[0].handles)} handle and tunnel loops of genus {m.genus()}")
 
 
 def test_gyroid_oracle_parity(vls, oracle_results):
