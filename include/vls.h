@@ -102,6 +102,10 @@ typedef struct {
                                step loops as device-driven CUDA graphs (same results) */
   int32_t hook_variant;     /* band union-find: 1 one thread per band row, 2 a group of 8 lanes per
                                band row (one neighbour each), 0 autotuned or 2 (same results) */
+  int32_t rows_per_warp;    /* frontier rows a warp of the one-thread-per-row kernels takes per
+                               pass: 32, 16 or 8 (fewer rows per warp spread a small frontier over
+                               more warps and schedulers); 0 autotuned with the launch shape, or
+                               32 when the shape is given (same results) */
 } vls_options;
 
 /* A closed, oriented triangle mesh: X[nv][3] positions, F[nf][3] vertex ids (CCW). */

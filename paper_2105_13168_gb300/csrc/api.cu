@@ -97,6 +97,7 @@ extern "C" void vls_default_options(vls_options *o) {
   o->profile = 0;
   o->host_loop = 0;
   o->hook_variant = 0;
+  o->rows_per_warp = 0;
 }
 
 extern "C" void vls_constants(const vls_options *o, double out[4]) {
@@ -138,7 +139,9 @@ extern "C" vls_status vls_create(vls_ctx **ctx, const vls_options *o, void *stre
   if (o) c->opt = *o;
   else vls_default_options(&c->opt);
   if ((c->opt.precision != VLS_FP64 && c->opt.precision != VLS_FP32_RECHECK && c->opt.precision != VLS_BF16_RECHECK) ||
-      (c->opt.precision != VLS_FP64 && !(c->opt.recheck_margin > 0.0 && c->opt.recheck_margin < 0.25))) {
+      (c->opt.precision != VLS_FP64 && !(c->opt.recheck_margin > 0.0 && c->opt.recheck_margin < 0.25)) ||
+      (c->opt.rows_per_warp != 0 && c->opt.rows_per_warp != 8 && c->opt.rows_per_warp != 16 &&
+       c->opt.rows_per_warp != 32)) {
     delete c;
     return VLS_EINVAL;
   }
@@ -362,13 +365,16 @@ struct TuneEntry {
   int dev = -1, vclass = -1, prec = -1;
   Batch::Shape shape[KK_COUNT_KINDS];
   int hook_variant = 2;
+  int rpw = 32;
 };
 std::mutex g_tune_mu;
 std::vector<TuneEntry> g_tune;
 
 constexpr int TUNE_STEPS = 600;
-// (threads per block, blocks per SM (64: as many as fit), band union-find variant)
-const int kTuneCands[][3] = {{128, 64, 2}, {256, 64, 2}, {64, 64, 2}, {128, 64, 1}, {128, 4, 2}};
+// (threads per block, blocks per SM (64: as many as fit), band union-find variant, frontier
+// rows per warp of the one-thread-per-row kernels)
+const int kTuneCands[][4] = {{128, 64, 2, 32}, {256, 64, 2, 32}, {64, 64, 2, 32}, {128, 64, 1, 32}, {128, 4, 2, 32},
+                             {128, 64, 2, 16}, {128, 64, 2, 8},  {256, 64, 2, 8}, {64, 64, 2, 8}};
 
 // Each candidate launch shape / union-find variant runs the first TUNE_STEPS steps of this
 // batch's initial pass the way real calls run (device-driven graph, every kernel with that
@@ -385,6 +391,7 @@ void autotune(vls_ctx *ctx, int32_t n_mesh, const vls_mesh *meshes, const int32_
     o.threads = c[0];
     o.blocks_per_sm = c[1];
     o.hook_variant = c[2];
+    o.rows_per_warp = c[3];
     o.max_steps = TUNE_STEPS;
     o.tunnels = 0;
     o.profile = 0;
@@ -409,6 +416,7 @@ void autotune(vls_ctx *ctx, int32_t n_mesh, const vls_mesh *meshes, const int32_
         te.shape[k].bps = c[1];
       }
       te.hook_variant = c[2];
+      te.rpw = c[3];
     }
     if (r) vls_result_free(r);
     vls_destroy(t);
@@ -488,13 +496,16 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
   if (have_tuned) {
     for (int k = 0; k < KK_COUNT_KINDS; ++k) b.shape[k] = tuned.shape[k];
     b.hook_variant = tuned.hook_variant;
+    b.d.rpw = tuned.rpw;
   } else {
+    b.d.rpw = 32;
     for (int k = 0; k < KK_COUNT_KINDS; ++k) {
       b.shape[k].threads = ctx->opt.threads;
       b.shape[k].bps = ctx->opt.blocks_per_sm;
     }
   }
   if (ctx->opt.hook_variant == 1 || ctx->opt.hook_variant == 2) b.hook_variant = ctx->opt.hook_variant;
+  if (ctx->opt.rows_per_warp != 0) b.d.rpw = ctx->opt.rows_per_warp;
   configure_initial(b);
   configure_events(b);
   configure_tunnel(b);

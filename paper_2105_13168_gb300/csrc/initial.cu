@@ -260,11 +260,12 @@ __device__ __forceinline__ void update_rows(const Dev &d, const Params &P) {
   const int32_t nF = __ldcg(d.nfront + cur);
   uint32_t redo = 0;
   const int32_t lane = (int32_t)(threadIdx.x & 31);
-  VLS_WARP_LOOP(w, 32, nF) { // one row per lane (as FOR_ROWS), then the warp's mass sums
-    const int32_t i = w * 32 + lane;
+  const int32_t R = d.rpw;
+  VLS_WARP_LOOP(w, R, nF) { // one row per lane of the first R lanes (as FOR_ROWS_R), then the warp's mass sums
+    const int32_t i = w * R + lane;
     int32_t p = -1;
     double2 mass = make_double2(0.0, 0.0);
-    if (i < nF) {
+    if (lane < R && i < nF) {
       p = fp[i];
       redo += update_one<TV>(d, P, fv, i, p, mass) == ROW_REDONE;
     }
@@ -312,7 +313,7 @@ __device__ __forceinline__ void apply_phase(const Dev &d) {
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
   const int32_t nF = __ldcg(d.nfront + cur);
-  FOR_ROWS(i, nF) {
+  FOR_ROWS_R(i, nF, d.rpw) {
     const int32_t v = fv[i];
     d.uf[v] = v;
     const int32_t c = d.onl[i];
@@ -385,7 +386,7 @@ __global__ void k_band_hook_row(Dev d) {
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
   const int32_t nF = __ldcg(d.nfront + cur);
-  FOR_ROWS(i, nF) {
+  FOR_ROWS_R(i, nF, d.rpw) {
     if (__ldcg(d.pdone + fp[i])) continue;
     const int32_t v = fv[i];
     int32_t l;
@@ -425,7 +426,7 @@ __device__ __forceinline__ void count_phase(const Dev &d) {
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
   const int32_t nF = __ldcg(d.nfront + cur);
-  FOR_ROWS(i, nF) {
+  FOR_ROWS_R(i, nF, d.rpw) {
     const int32_t p = fp[i];
     if (__ldcg(d.pdone + p)) continue;
     const int32_t v = fv[i];

@@ -66,8 +66,29 @@ __device__ __forceinline__ void tph_st(const TDev &T, int32_t i, double x) {
   else T.phi[i] = x;
 }
 
+// Block-cooperative bitonic sort (ascending) of a[0, n2), n2 a power of two; a is shared or
+// block-private global memory (__syncthreads orders both).  Every thread of the block calls it.
+__device__ void block_bitonic_sort(int32_t *a, int32_t n2) {
+  for (int32_t k = 2; k <= n2; k <<= 1)
+    for (int32_t j = k >> 1; j > 0; j >>= 1) {
+      for (int32_t i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int32_t ixj = i ^ j;
+        if (ixj > i) {
+          const int32_t x = a[i], y = a[ixj];
+          if ((x > y) == ((i & k) == 0)) {
+            a[i] = y;
+            a[ixj] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+constexpr int32_t TINIT_SMEM_SORT = 4096; // cut slots sorted in shared memory up to this many
+
 // per pass: flags, sources at 1, cut slots sorted, F_0 = sources
-__global__ void k_tinit(Dev d, TDev T, int32_t *fv0, int32_t *fq0, int32_t *nF0) {
+__global__ void __launch_bounds__(256) k_tinit(Dev d, TDev T, int32_t *fv0, int32_t *fq0, int32_t *nF0) {
+  __shared__ int32_t sk[TINIT_SMEM_SORT];
   const int32_t q = blockIdx.x;
   if (q >= T.NP) return;
   const int32_t p = T.pprob[q];
@@ -91,8 +112,19 @@ __global__ void k_tinit(Dev d, TDev T, int32_t *fv0, int32_t *fq0, int32_t *nF0)
     fq0[s] = q;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const int32_t n = 2 * L;
+  // sort the 2L cut slots (padded with INT32_MAX to a power of two): in shared memory, or for a
+  // long loop in the pass's own stretch of the trace scratch (nvp entries, unused until the
+  // trace); a loop too long even for that (never seen) keeps a one-thread insertion sort
+  const int32_t n = 2 * L;
+  int32_t n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  int32_t *buf = n2 <= TINIT_SMEM_SORT ? sk : (n2 <= nvp ? T.path + base : nullptr);
+  if (buf != nullptr) {
+    for (int32_t i = threadIdx.x; i < n2; i += blockDim.x) buf[i] = i < n ? cut[i] : INT32_MAX;
+    __syncthreads();
+    block_bitonic_sort(buf, n2);
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) cut[i] = buf[i];
+  } else if (threadIdx.x == 0) {
     for (int32_t i = 1; i < n; ++i) {
       int32_t x = cut[i], j = i - 1;
       while (j >= 0 && cut[j] > x) { cut[j + 1] = cut[j]; --j; }
@@ -208,7 +240,7 @@ __device__ __forceinline__ void tupdate_rows(const Dev &d, const TDev &T, const 
   const int32_t *__restrict__ fq = T.fq[cur];
   const int32_t nF = __ldcg(T.nf + cur);
   uint32_t redo = 0;
-  FOR_ROWS(i, nF) {
+  FOR_ROWS_R(i, nF, d.rpw) {
     const int32_t v = fv[i], q = fq[i];
     const int32_t deg = d.rp[v + 1] - d.rp[v];
     if (deg <= 12) redo += tupdate_row<12, TV>(d, T, P, i, q, v);
@@ -231,7 +263,7 @@ __device__ __forceinline__ void tapply_phase(const Dev &d, const TDev &T, double
   const int32_t *__restrict__ fv = T.fv[cur];
   const int32_t *__restrict__ fq = T.fq[cur];
   const int32_t nF = __ldcg(T.nf + cur);
-  FOR_ROWS(i, nF) {
+  FOR_ROWS_R(i, nF, d.rpw) {
     const int32_t q = fq[i], v = fv[i];
     const int32_t p = T.pprob[q];
     const int32_t idx = T.pbase[q] + (v - d.voff[p]);

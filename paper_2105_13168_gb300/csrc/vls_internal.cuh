@@ -86,6 +86,7 @@ struct Dev {
   unsigned long long *nrecheck; // [2] rows redone in FP64: initial pass, tunnel passes
   double *pmass;     // [P][mslots][2] this step's sum over frontier rows of m_v (L base)_v, and of its
                      // terms' magnitudes, spread over mslots addresses per problem
+  int32_t rpw;       // frontier rows per warp of the one-thread-per-row kernels (8, 16 or 32)
   int32_t mslots;    // a power of two: MASS_SLOTS for batches of few problems (their rows share a few
                      // addresses), 1 for many (rows spread over many problems already)
   double *pmres;     // [P] largest relative residual |sum| / magnitude over the steps so far
@@ -249,9 +250,12 @@ constexpr int GL = 8; // lanes per row of the neighbour-parallel kernels (mesh d
 #define VLS_WARP_LOOP(w, rows_per_warp, n)                                                          \
   for (int32_t w = (int32_t)(blockIdx.x + gridDim.x * (threadIdx.x >> 5)); w * (rows_per_warp) < (n); \
        w += (int32_t)(gridDim.x * (blockDim.x >> 5)))
-#define FOR_ROWS(i, n)                                                                              \
-  VLS_WARP_LOOP(vls_w_, 32, n)                                                                      \
-  for (int32_t i = vls_w_ * 32 + (int32_t)(threadIdx.x & 31); i < (n); i = INT32_MAX)
+#define FOR_ROWS(i, n) FOR_ROWS_R(i, n, 32)
+// R rows per warp (R = 8, 16 or 32): lanes R..31 take no row
+#define FOR_ROWS_R(i, n, R)                                                                         \
+  VLS_WARP_LOOP(vls_w_, (R), n)                                                                     \
+  for (int32_t i = vls_w_ * (R) + (int32_t)(threadIdx.x & 31);                                      \
+       (int32_t)(threadIdx.x & 31) < (R) && i < (n); i = INT32_MAX)
 #define FOR_ROWS_G(i, n)                                                                            \
   VLS_WARP_LOOP(vls_w_, 32 / GL, n)                                                                 \
   for (int32_t i = vls_w_ * (32 / GL) + (int32_t)((threadIdx.x & 31) / GL); i < (n); i = INT32_MAX)

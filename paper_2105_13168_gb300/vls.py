@@ -28,7 +28,7 @@ class vls_options(ctypes.Structure):
                 ("keep_state", ctypes.c_int32), ("record_steps", ctypes.c_int32), ("sync_interval", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("host_loop", ctypes.c_int32),
-                ("hook_variant", ctypes.c_int32)]
+                ("hook_variant", ctypes.c_int32), ("rows_per_warp", ctypes.c_int32)]
 
 
 class vls_mesh(ctypes.Structure):

@@ -6,7 +6,7 @@ import pytest
 
 import meshgen
 import oracle
-from parity import assert_close, assert_parity
+from parity import assert_close, assert_fp32_parity, assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -135,14 +135,24 @@ def test_stats_are_consistent(vls):
     assert g.stats["steps"] == o.steps
 
 
-@pytest.mark.parametrize("threads,bps,variant", [(64, 1, 1), (256, 64, 2), (128, 2, 1), (128, 4, 2)])
-def test_launch_shapes_and_union_find_variants(vls, threads, bps, variant):
-    """Every launch shape and both band union-find variants give the oracle's results (the
-    autotuner may pick any of them)."""
+@pytest.mark.parametrize("threads,bps,variant,rpw", [(64, 1, 1, 32), (256, 64, 2, 32), (128, 2, 1, 16),
+                                                     (128, 4, 2, 8), (64, 64, 2, 8), (256, 1, 1, 16)])
+def test_launch_shapes_and_union_find_variants(vls, threads, bps, variant, rpw):
+    """Every launch shape, both band union-find variants and every rows-per-warp setting give the
+    oracle's results (the autotuner may pick any of them)."""
     m = meshgen.tube_chain(2, 64)
     s = meshgen.seed_vertex(1, m.nv)
-    g = run_gpu(vls, [(m, [s])], threads=threads, blocks_per_sm=bps, hook_variant=variant)[0]
+    g = run_gpu(vls, [(m, [s])], threads=threads, blocks_per_sm=bps, hook_variant=variant, rows_per_warp=rpw)[0]
     assert_parity(g, run_orc(m, s))
+    f = run_gpu(vls, [(m, [s])], precision="fp32", threads=threads, blocks_per_sm=bps, hook_variant=variant,
+                rows_per_warp=rpw)[0]
+    assert_fp32_parity(f, run_orc(m, s), m.X)
+
+
+def test_rows_per_warp_option_checked(vls):
+    for bad in (4, 12, 64, -1):
+        with pytest.raises(RuntimeError):
+            vls.vls_create(vls.vls_default_options(rows_per_warp=bad))
 
 
 def test_tunnel_passes_in_chunks(vls, monkeypatch):
