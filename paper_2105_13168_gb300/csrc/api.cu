@@ -84,7 +84,7 @@ extern "C" void vls_default_options(vls_options *o) {
   o->eps0 = 1e-3;
   o->theta_iso = 0.5;
   o->lbar = 0.0;
-  o->recheck_margin = 1e-4;
+  o->recheck_margin = 1e-5;
   o->max_steps = 200000;
   o->max_pass_steps = 200000;
   o->tunnels = 1;

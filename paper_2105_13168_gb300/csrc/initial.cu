@@ -235,6 +235,110 @@ __device__ __noinline__ int update_row_wide(const Dev &d, const Params &P, int32
                                             int32_t deg, double2 &mass) {
   return update_row<64, TV, false>(d, P, i, p, v, b, deg, mass);
 }
+// Rows the common-case path leaves (several layers, a frozen neighbour, a decision near its
+// threshold in the FP32 / BF16 forms): the general row, out of line.
+template <class TV>
+__device__ __noinline__ int update_row_general(const Dev &d, const Params &P, int32_t i, int32_t p, int32_t v,
+                                               int32_t b, int32_t deg, double2 &mass) {
+  return update_row<ROW_REG, TV, true>(d, P, i, p, v, b, deg, mass);
+}
+
+// FP64 row of the common case below (one live layer l0 and the base, no frozen neighbour): the
+// operations of the general row for this case, in the same order.
+template <class TV>
+__device__ __forceinline__ double row_one_f64(const Params &P, int32_t l0, int32_t lv, TV xv, const int32_t *nlay,
+                                              const TV *nx, int32_t deg, double2 &mass) {
+  const double Lv = P.lv[deg];
+  const double xvd = to_f64(xv);
+  const double xb = dsub(1.0, lv != 0 ? xvd : 0.0);
+  double acc = 0.0, accb = 0.0;
+#pragma unroll
+  for (int j = 0; j < ROW_REG; ++j)
+    if (j < deg) {
+      const double psi = nlay[j] == l0 ? to_f64(nx[j]) : 0.0;
+      if (val_pos(psi)) acc = dadd(acc, dmul(Lv, psi)); // zero terms skipped, as in the general row
+    }
+  const double x = lv == l0 ? xvd : 0.0;
+  acc = dadd(acc, dmul(-P.s, x));
+#pragma unroll
+  for (int j = 0; j < ROW_REG; ++j)
+    if (j < deg) {
+      if (nlay[j] == 0) accb = dadd(accb, Lv);
+      else if (val_lt1(nx[j])) accb = dadd(accb, dmul(Lv, dsub(1.0, to_f64(nx[j]))));
+    }
+  mass = make_double2(0.0, dadd(dmul(P.mv[deg], accb), dmul((double)deg, xb)));
+  accb = dadd(accb, dmul(-P.s, xb));
+  mass.x = dmul(P.mv[deg], accb);
+  double out;
+  if (!vertex_update(P, 1, &x, &acc, xb, accb, &out)) out = x;
+  return out;
+}
+// FP32 / BF16 forms: the FP64 redo of a common-case row from its gathered inputs, rounded to the
+// stored type keeping every threshold's side; out of line (rare: a decision within the margin).
+template <class TV>
+__device__ __noinline__ double row_one_redo(const Params &P, int32_t l0, int32_t lv, TV xv, const int32_t *nlay,
+                                            const TV *nx, int32_t deg, double2 &mass) {
+  return round_keep<TV>(row_one_f64<TV>(P, l0, lv, xv, nlay, nx, deg, mass), P.theta);
+}
+
+// The common case, kept short: every non-base entry of the closed neighbourhood belongs to one
+// live layer l0 (no collision, no frozen plateau next to the row), so Eq. (2) has n = 2 and the
+// layer's state is read once instead of once per neighbour.  The arithmetic is exactly that of
+// the general row for this case.  Returns ROW_GENERAL, having written nothing, for any other row.
+constexpr int ROW_GENERAL = 2;
+template <class TV>
+__device__ __forceinline__ int update_row_fast(const Dev &d, const Params &P, int32_t i, int32_t v, int32_t b,
+                                               int32_t deg, double2 &mass) {
+  const TV *__restrict__ ph = ph_arr<TV>(d);
+  int32_t nu[ROW_REG], nlay[ROW_REG];
+  TV nx[ROW_REG];
+#pragma unroll
+  for (int j = 0; j < ROW_REG; ++j) nu[j] = (j < deg) ? d.col[b + j] : v;
+  const int32_t lv = d.lay[v];
+  const TV xv = ph[v];
+#pragma unroll
+  for (int j = 0; j < ROW_REG; ++j) {
+    nlay[j] = (j < deg) ? d.lay[nu[j]] : 0;
+    nx[j] = (j < deg) ? ph[nu[j]] : TV(0.0f);
+  }
+  int32_t l0 = lv;
+  bool one = true, hb = lv == 0 || val_lt1(xv);
+#pragma unroll
+  for (int j = 0; j < ROW_REG; ++j)
+    if (j < deg) {
+      const int32_t lu = nlay[j];
+      if (lu == 0) hb = true;
+      else {
+        if (l0 == 0) l0 = lu;
+        one &= lu == l0;
+        hb |= val_lt1(nx[j]);
+      }
+    }
+  if (!one) return ROW_GENERAL;
+  if (l0 == 0) { d.onl[i] = -1; return ROW_DONE; } // the base alone: nothing changes
+  if (d.lstate[l0] != L_ALIVE) return ROW_GENERAL;
+  if (!hb) { d.onl[i] = -1; return ROW_DONE; }      // no base in the neighbourhood
+  double out;
+  int outcome = ROW_DONE;
+  if constexpr (std::is_same<TV, double>::value) {
+    out = row_one_f64<TV>(P, l0, lv, xv, nlay, nx, deg, mass);
+  } else if (!row_f32<ROW_REG>(P, l0, lv, lv, xv, nlay, nx, deg, out, mass)) {
+    int32_t cl[ROW_REG];
+    TV cx[ROW_REG];
+#pragma unroll
+    for (int j = 0; j < ROW_REG; ++j) { cl[j] = nlay[j]; cx[j] = nx[j]; }
+    out = row_one_redo<TV>(P, l0, lv, xv, cl, cx, deg, mass);
+    outcome = ROW_REDONE;
+  }
+  if (out > 0.0) {
+    d.olay[(int64_t)i * KMAX] = l0;
+    d.ophi[(int64_t)i * KMAX] = out;
+    d.onl[i] = 1;
+  } else {
+    d.onl[i] = 0;
+  }
+  return outcome;
+}
 
 template <class TV>
 __device__ __forceinline__ int update_one(const Dev &d, const Params &P, const int32_t *fv, int32_t i, int32_t p,
@@ -245,7 +349,10 @@ __device__ __forceinline__ int update_one(const Dev &d, const Params &P, const i
   const int32_t b = d.rp[v], e = d.rp[v + 1];
   if (!VCHK(d.err, e, d.nnz + 1, 102) || !VCHK(d.err, b, e + 1, 103)) { d.onl[i] = -1; return ROW_DONE; }
   const int32_t deg = e - b;
-  if (deg <= ROW_REG) return update_row<ROW_REG, TV, true>(d, P, i, p, v, b, deg, mass);
+  if (deg <= ROW_REG) {
+    const int oc = update_row_fast<TV>(d, P, i, v, b, deg, mass);
+    return oc != ROW_GENERAL ? oc : update_row_general<TV>(d, P, i, p, v, b, deg, mass);
+  }
   if (deg <= 64) return update_row_wide<TV>(d, P, i, p, v, b, deg, mass);
   atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_EINVAL);
   d.onl[i] = -1;
