@@ -59,6 +59,9 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=2, help="problems timed for the CPU baseline")
     ap.add_argument("--profile-case", action="store_true",
                     help="one detection of the workload bounded to --max-steps initial steps (for profilers)")
+    ap.add_argument("--shape", default="",
+                    help="profile case: fixed launch shape 'threads,blocks_per_sm,hook_variant,rows_per_warp' "
+                         "instead of the autotuner (keeps tuning runs out of a profiler's launch list)")
     ap.add_argument("--max-steps", type=int, default=400)
     ap.add_argument("--max-pass-steps", type=int, default=200)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
@@ -304,8 +307,12 @@ def run_profile_case(args):
     cfg, faces = workload_desc(probs)
     dev = torch.device("cuda", 0)
     meshes_dev = [(torch.from_numpy(m.X).to(dev), torch.from_numpy(m.F).to(dev)) for m, _ in probs]
+    shape = {}
+    if args.shape:
+        t, bps, hv, rpw = (int(x) for x in args.shape.split(","))
+        shape = dict(threads=t, blocks_per_sm=bps, hook_variant=hv, rows_per_warp=rpw)
     opts = vls.vls_default_options(max_steps=args.max_steps, max_pass_steps=args.max_pass_steps,
-                                   precision=args.precision)
+                                   precision=args.precision, **shape)
     ctx = vls.vls_create(opts, torch.cuda.current_stream().cuda_stream)
     res = vls.vls_detect_batch(ctx, meshes_dev, [s for _, s in probs], device=True)
     out = vls.read_result(res)

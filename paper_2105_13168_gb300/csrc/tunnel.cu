@@ -201,6 +201,14 @@ __device__ __forceinline__ bool trow_f32(const Params &P, uint64_t kp, int dh, c
   return true;
 }
 
+// FP32 / BF16 forms: the FP64 redo of a pass row from copies of its gathered inputs, rounded to
+// the stored type keeping every threshold's side; out of line (rare) so that the hot row keeps
+// few registers.
+template <int MAXD, class TV>
+__device__ __noinline__ double trow_redo(const Params &P, uint64_t kp, int dh, const TV *nx, TV x) {
+  return round_keep<TV>(trow_f64<MAXD, TV>(P, kp, dh, nx, x), P.theta);
+}
+
 template <int MAXD, class TV>
 __device__ __forceinline__ bool tupdate_row(const Dev &d, const TDev &T, const Params &P, int32_t i, int32_t q,
                                             int32_t v) {
@@ -217,7 +225,10 @@ __device__ __forceinline__ bool tupdate_row(const Dev &d, const TDev &T, const P
   bool redo = false;
   if constexpr (!std::is_same<TV, double>::value) {
     if (!trow_f32<MAXD>(P, kp, dh, nx, x, out)) {
-      out = round_keep<TV>(trow_f64<MAXD, TV>(P, kp, dh, nx, x), P.theta);
+      TV cx[MAXD];
+#pragma unroll
+      for (int j = 0; j < MAXD; ++j) cx[j] = nx[j];
+      out = trow_redo<MAXD, TV>(P, kp, dh, cx, x);
       redo = true;
     }
   } else {
