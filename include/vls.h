@@ -143,6 +143,10 @@ typedef struct {
    * magnitudes seen over the problem's steps.  Rounding alone gives about 1e-16 in the FP64
    * form and 1e-7 in the FP32 form; a wrong operator entry or a lost neighbour gives far more. */
   double mass_resid;
+  /* The same check in the tunnel passes: the kept-edge operator of a pass is symmetric in the same
+   * way, and the flux into the pass's sources (held at 1, never rows) is taken out; the largest
+   * residual over the steps of the problem's passes. */
+  double pass_mass_resid;
 } vls_stats;
 
 /* Fill *o with the defaults above. */

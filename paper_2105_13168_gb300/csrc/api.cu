@@ -313,6 +313,9 @@ void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut) {
   T.qstatus = L.take<int32_t>(NP);
   T.qbstar = L.take<int32_t>(NP);
   T.qcnt = L.take<int32_t>(2 * NP);
+  T.qslots = NP <= MASS_SPREAD_MAXP ? MASS_SLOTS : 1;
+  T.qmass = L.take<double>(2 * (size_t)T.qslots * NP);
+  T.qmres = L.take<double>(NP);
   T.qupd = L.take<long long>(NP);
   T.active = L.take<int32_t>(1);
   T.tvoff = L.take<int32_t>(NP);
@@ -836,6 +839,8 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       CK(cudaMemsetAsync(T.qstatus, 0xff, sizeof(int32_t) * NP, st));
       k_fill_i32<<<(NP + 255) / 256, 256, 0, st>>>(T.qbstar, NP, 0x7fffffff); VLS_LAUNCH(b);
       CK(cudaMemsetAsync(T.qcnt, 0, sizeof(int32_t) * 2 * NP, st));
+      CK(cudaMemsetAsync(T.qmass, 0, sizeof(double) * 2 * T.qslots * NP, st));
+      CK(cudaMemsetAsync(T.qmres, 0, sizeof(double) * NP, st));
       CK(cudaMemsetAsync(T.qupd, 0, sizeof(long long) * NP, st));
       CK(cudaMemsetAsync(T.ntverts, 0, sizeof(int32_t), st));
       CK(cudaMemsetAsync(T.tvn, 0, sizeof(int32_t) * NP, st));
@@ -844,6 +849,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       tunnel_tau += chunk_tau; // launch accounting: steps summed over chunks
       std::vector<int32_t> qs(NP), qst(NP), qb(NP), tvo(NP), tvn(NP);
       std::vector<long long> qupd(NP);
+      std::vector<double> qmres(NP);
       int32_t ntv = 0;
       CK(cudaMemcpyAsync(qs.data(), T.qstatus, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(qst.data(), T.qsteps, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
@@ -852,8 +858,9 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       CK(cudaMemcpyAsync(tvn.data(), T.tvn, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(&ntv, T.ntverts, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(qupd.data(), T.qupd, sizeof(long long) * NP, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(qmres.data(), T.qmres, sizeof(double) * NP, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      b.d2h += (int64_t)(5 * sizeof(int32_t) + sizeof(long long)) * NP + (int64_t)sizeof(int32_t);
+      b.d2h += (int64_t)(5 * sizeof(int32_t) + sizeof(long long) + sizeof(double)) * NP + (int64_t)sizeof(int32_t);
       ntv = std::min(ntv, T.tvcap);
       const size_t tv0 = h_tverts.size();
       h_tverts.resize(tv0 + (size_t)ntv);
@@ -870,6 +877,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
         // per-problem pass statistics
         ProbResult &r = res->p[dev_probs[pprob[q]]];
         r.stats.pass_updates += qupd[q];
+        r.stats.pass_mass_resid = std::max(r.stats.pass_mass_resid, qmres[q]);
         r.tunnel_steps = std::max(r.tunnel_steps, qst[q]);
       }
     }

@@ -376,32 +376,7 @@ __device__ __forceinline__ void update_rows(const Dev &d, const Params &P) {
       p = fp[i];
       redo += update_one<TV>(d, P, fv, i, p, mass) == ROW_REDONE;
     }
-    // mass check sums: FP64 atomics on per-problem slots spread over MASS_SLOTS addresses (the
-    // frontier list interleaves problems, and same-address atomics serialise).  A warp with few
-    // problems sums each problem's rows first: one pair of atomics per problem per warp.
-    const int32_t slot = (int32_t)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) & (d.mslots - 1));
-    const unsigned peers = __match_any_sync(0xffffffffu, p);
-    unsigned leaders = __ballot_sync(0xffffffffu, lane == __ffs(peers) - 1);
-    if (__popc(leaders) <= 4) {
-      while (leaders) {
-        const int32_t q = __shfl_sync(0xffffffffu, p, __ffs(leaders) - 1);
-        leaders &= leaders - 1;
-        double sx = p == q ? mass.x : 0.0, sy = p == q ? mass.y : 0.0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          sx += __shfl_xor_sync(0xffffffffu, sx, off);
-          sy += __shfl_xor_sync(0xffffffffu, sy, off);
-        }
-        if (lane == 0 && q >= 0 && sy != 0.0) {
-          atomicAdd(&d.pmass[((int64_t)q * d.mslots + slot) * 2], sx);
-          atomicAdd(&d.pmass[((int64_t)q * d.mslots + slot) * 2 + 1], sy);
-        }
-      }
-    } else if (mass.y != 0.0) {
-      const int32_t ls = (slot + lane) & (d.mslots - 1);
-      atomicAdd(&d.pmass[((int64_t)p * d.mslots + ls) * 2], mass.x);
-      atomicAdd(&d.pmass[((int64_t)p * d.mslots + ls) * 2 + 1], mass.y);
-    }
+    mass_sums(d.pmass, d.mslots, p, lane, mass);
   }
   if constexpr (!std::is_same<TV, double>::value) {
     redo = __reduce_add_sync(0xffffffffu, redo);
@@ -664,15 +639,7 @@ __device__ __forceinline__ void epilogue_phase(const Dev &d, const Handles &H, i
         // mass check of this step's diffusion: the base's Laplacian, weighted by the lumped
         // masses, sums to zero over the rows that can change (every other row has a uniform
         // closed neighbourhood); the FP64 residual relative to the terms' magnitude
-        double2 *pm = reinterpret_cast<double2 *>(d.pmass) + (int64_t)p * d.mslots;
-        double sm = 0.0, mag = 0.0;
-        for (int k = 0; k < d.mslots; ++k) {
-          const double2 a = __ldcg(pm + k);
-          sm += a.x;
-          mag += a.y;
-          pm[k] = make_double2(0.0, 0.0);
-        }
-        if (mag > 0.0) d.pmres[p] = fmax(d.pmres[p], fabs(sm) / mag);
+        d.pmres[p] = fmax(d.pmres[p], mass_fold(d.pmass, d.mslots, p));
       }
       if (__ldcg(d.pstatus + p) != 0) d.pdone[p] = 1;
       else if (__ldcg(pcount_next + p) == 0) d.pdone[p] = 1;

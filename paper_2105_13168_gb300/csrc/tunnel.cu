@@ -138,10 +138,11 @@ __global__ void __launch_bounds__(256) k_tinit(Dev d, TDev T, int32_t *fv0, int3
 template <int MAXD, class TV>
 __device__ __forceinline__ int gather_kept(const Dev &d, const TDev &T, int32_t q, int32_t step, int32_t base,
                                           int32_t voff, int8_t fl, int32_t v, int32_t b, int32_t deg, uint64_t &kp,
-                                          TV *nx) {
+                                          TV *nx, int &nsrc) {
   const TV *__restrict__ ph = tph_arr<TV>(T);
   int32_t nu[MAXD];
   kp = 0;
+  nsrc = 0;
 #pragma unroll
   for (int j = 0; j < MAXD; ++j) nu[j] = (j < deg) ? d.col[b + j] : v;
 #pragma unroll
@@ -152,6 +153,7 @@ __device__ __forceinline__ int gather_kept(const Dev &d, const TDev &T, int32_t 
     bool k = j < deg && c >= 0 && c <= step;
     if (k && (((fl & F_SRC) && (f & F_TGT)) || ((fl & F_TGT) && (f & F_SRC)))) k = !is_cut(T, q, b + j);
     if (k) kp |= 1ull << j;
+    nsrc += (k && (f & F_SRC)) ? 1 : 0;
   }
   return __popcll(kp);
 }
@@ -159,7 +161,8 @@ __device__ __forceinline__ int gather_kept(const Dev &d, const TDev &T, int32_t 
 // FP64 pass row (Eq. (2) with n = 2: the pass layer and its base) from the stored inputs
 // (FP32 values are widened exactly).
 template <int MAXD, class TV>
-__device__ __forceinline__ double trow_f64(const Params &P, uint64_t kp, int dh, const TV *nx, TV xs) {
+__device__ __forceinline__ double trow_f64(const Params &P, uint64_t kp, int dh, int nsrc, const TV *nx, TV xs,
+                                           double2 &mass) {
   const double Lv = dh > 0 ? P.lv[dh] : 0.0;
   const double diag = dh > 0 ? -P.s : 0.0;
   const double x = to_f64(xs);
@@ -173,7 +176,11 @@ __device__ __forceinline__ double trow_f64(const Params &P, uint64_t kp, int dh,
   for (int j = 0; j < MAXD; ++j)
     if (((kp >> j) & 1ull) && val_lt1(nx[j])) accb = dadd(accb, dmul(Lv, dsub(1.0, to_f64(nx[j]))));
   const double xb = dsub(1.0, x);
+  // mass check: m_v (L base)_v less the flux into the sources (held at 1, base 0; never rows), and
+  // the magnitude of its terms
+  mass = make_double2(0.0, dadd(dmul(P.mv[dh], accb), dmul((double)dh, xb)));
   accb = dadd(accb, dmul(diag, xb));
+  mass.x = dmul(P.mv[dh], accb) + (double)nsrc * xb;
   double out;
   if (!vertex_update(P, 1, &x, &acc, xb, accb, &out)) out = x;
   return out;
@@ -182,7 +189,8 @@ __device__ __forceinline__ double trow_f64(const Params &P, uint64_t kp, int dh,
 // FP32 pass row (values stored as float or bfloat16); false when a decision lies within the
 // recheck margin.
 template <int MAXD, class TN>
-__device__ __forceinline__ bool trow_f32(const Params &P, uint64_t kp, int dh, const TN *nx, TN xs, double &out) {
+__device__ __forceinline__ bool trow_f32(const Params &P, uint64_t kp, int dh, int nsrc, const TN *nx, TN xs,
+                                         double &out, double2 &mass) {
   if (dh == 0) return false;
   const float Lv = P.f_lv[dh];
   const float x = to_f32(xs);
@@ -195,8 +203,12 @@ __device__ __forceinline__ bool trow_f32(const Params &P, uint64_t kp, int dh, c
       accb = fmaf(Lv, 1.f - xj, accb);
     }
   const float xb = 1.f - x;
+  const float lapb = fmaf(-P.f_s, xb, accb);
+  // mass check (FP64 from the FP32 sums), as in the FP64 row
+  mass = make_double2(P.mv[dh] * (double)lapb + (double)nsrc * (double)xb,
+                      P.mv[dh] * (double)accb + (double)dh * (double)xb);
   float y;
-  if (!vertex_update_f32(P, x, fmaf(-P.f_s, x, acc), xb, fmaf(-P.f_s, xb, accb), y)) return false;
+  if (!vertex_update_f32(P, x, fmaf(-P.f_s, x, acc), xb, lapb, y)) return false;
   out = round_keep<TN>((double)y, P.theta); // exact for float storage
   return true;
 }
@@ -205,13 +217,14 @@ __device__ __forceinline__ bool trow_f32(const Params &P, uint64_t kp, int dh, c
 // the stored type keeping every threshold's side; out of line (rare) so that the hot row keeps
 // few registers.
 template <int MAXD, class TV>
-__device__ __noinline__ double trow_redo(const Params &P, uint64_t kp, int dh, const TV *nx, TV x) {
-  return round_keep<TV>(trow_f64<MAXD, TV>(P, kp, dh, nx, x), P.theta);
+__device__ __noinline__ double trow_redo(const Params &P, uint64_t kp, int dh, int nsrc, const TV *nx, TV x,
+                                         double2 &mass) {
+  return round_keep<TV>(trow_f64<MAXD, TV>(P, kp, dh, nsrc, nx, x, mass), P.theta);
 }
 
 template <int MAXD, class TV>
 __device__ __forceinline__ bool tupdate_row(const Dev &d, const TDev &T, const Params &P, int32_t i, int32_t q,
-                                            int32_t v) {
+                                            int32_t v, double2 &mass) {
   const int32_t p = T.pprob[q], base = T.pbase[q], voff = d.voff[p], step = T.pstep[q];
   const int32_t idx = base + (v - voff);
   if (!VCHK(T.err, idx, T.PV, 310)) { T.onew[i] = 0.0; return false; }
@@ -219,20 +232,21 @@ __device__ __forceinline__ bool tupdate_row(const Dev &d, const TDev &T, const P
   const int32_t b = d.rp[v], deg = d.rp[v + 1] - b;
   uint64_t kp;
   TV nx[MAXD];
-  const int dh = gather_kept<MAXD, TV>(d, T, q, step, base, voff, fl, v, b, deg, kp, nx);
+  int nsrc;
+  const int dh = gather_kept<MAXD, TV>(d, T, q, step, base, voff, fl, v, b, deg, kp, nx, nsrc);
   const TV x = tph_arr<TV>(T)[idx];
   double out;
   bool redo = false;
   if constexpr (!std::is_same<TV, double>::value) {
-    if (!trow_f32<MAXD>(P, kp, dh, nx, x, out)) {
+    if (!trow_f32<MAXD>(P, kp, dh, nsrc, nx, x, out, mass)) {
       TV cx[MAXD];
 #pragma unroll
       for (int j = 0; j < MAXD; ++j) cx[j] = nx[j];
-      out = trow_redo<MAXD, TV>(P, kp, dh, cx, x);
+      out = trow_redo<MAXD, TV>(P, kp, dh, nsrc, cx, x, mass);
       redo = true;
     }
   } else {
-    out = trow_f64<MAXD, TV>(P, kp, dh, nx, x);
+    out = trow_f64<MAXD, TV>(P, kp, dh, nsrc, nx, x, mass);
   }
   T.onew[i] = out;
   return redo;
@@ -240,8 +254,8 @@ __device__ __forceinline__ bool tupdate_row(const Dev &d, const TDev &T, const P
 
 template <class TV>
 __device__ __noinline__ bool tupdate_row_wide(const Dev &d, const TDev &T, const Params &P, int32_t i, int32_t q,
-                                              int32_t v) {
-  return tupdate_row<64, TV>(d, T, P, i, q, v);
+                                              int32_t v, double2 &mass) {
+  return tupdate_row<64, TV>(d, T, P, i, q, v, mass);
 }
 
 template <class TV>
@@ -251,12 +265,20 @@ __device__ __forceinline__ void tupdate_rows(const Dev &d, const TDev &T, const 
   const int32_t *__restrict__ fq = T.fq[cur];
   const int32_t nF = __ldcg(T.nf + cur);
   uint32_t redo = 0;
-  FOR_ROWS_R(i, nF, d.rpw) {
-    const int32_t v = fv[i], q = fq[i];
-    const int32_t deg = d.rp[v + 1] - d.rp[v];
-    if (deg <= 12) redo += tupdate_row<12, TV>(d, T, P, i, q, v);
-    else if (deg <= 64) redo += tupdate_row_wide<TV>(d, T, P, i, q, v);
-    else T.onew[i] = tph_ld(T, T.pbase[q] + (v - d.voff[T.pprob[q]]));
+  const int32_t R = d.rpw, lane = (int32_t)(threadIdx.x & 31);
+  VLS_WARP_LOOP(w, R, nF) { // one row per lane of the first R lanes, then the warp's mass sums
+    const int32_t i = w * R + lane;
+    int32_t q = -1;
+    double2 mass = make_double2(0.0, 0.0);
+    if (lane < R && i < nF) {
+      const int32_t v = fv[i];
+      q = fq[i];
+      const int32_t deg = d.rp[v + 1] - d.rp[v];
+      if (deg <= 12) redo += tupdate_row<12, TV>(d, T, P, i, q, v, mass);
+      else if (deg <= 64) redo += tupdate_row_wide<TV>(d, T, P, i, q, v, mass);
+      else T.onew[i] = tph_ld(T, T.pbase[q] + (v - d.voff[T.pprob[q]]));
+    }
+    mass_sums(T.qmass, T.qslots, q, lane, mass);
   }
   if constexpr (!std::is_same<TV, double>::value) {
     redo = __reduce_add_sync(0xffffffffu, redo);
@@ -367,6 +389,7 @@ __device__ __forceinline__ void tepilogue_phase(const Dev &d, const TDev &T, con
       else if (__ldcg(cnt_next + q) == 0) { T.qdone[q] = 1; T.qstatus[q] = VLS_ELOOPFAIL; }
       else if (tau >= max_steps) { T.qdone[q] = 1; T.qstatus[q] = VLS_EMAXSTEPS; }
       if (!T.qdone[q]) atomicAdd(&nact, 1);
+      T.qmres[q] = fmax(T.qmres[q], mass_fold(T.qmass, T.qslots, q));
     }
     cnt_cur[q] = 0;
   }

@@ -45,6 +45,9 @@ struct TDev {
   double *onew;        // [V] per frontier row
   int32_t *qdone, *qsteps, *qstatus, *qbstar;  // [NP]
   int32_t *qcnt;       // [NP] rows in the frontier being built
+  double *qmass;       // [NP][qslots][2] mass-check sums of the step (see mass_sums)
+  int32_t qslots;
+  double *qmres;       // [NP] largest mass-check residual of the pass
   long long *qupd;     // [NP]
   int32_t *active;
   // output: tunnel vertex cycles

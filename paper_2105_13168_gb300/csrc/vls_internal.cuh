@@ -445,6 +445,48 @@ __device__ __forceinline__ int32_t warp_append(int32_t *counter, int32_t *key_co
   return base;
 }
 
+// Mass-check sums of a warp's rows, keyed by problem (initial pass) or pass (tunnel passes):
+// FP64 atomics on `slots` addresses per key (a power of two), since a frontier list interleaves
+// keys and same-address atomics serialise.  A warp with few keys sums each key's rows first: one
+// pair of atomics per key per warp.  key < 0: the lane holds no row.  Every lane of the warp calls.
+__device__ __forceinline__ void mass_sums(double *acc, int32_t slots, int32_t key, int32_t lane, double2 m) {
+  const int32_t slot = (int32_t)((blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) & (slots - 1));
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  unsigned leaders = __ballot_sync(0xffffffffu, lane == __ffs(peers) - 1);
+  if (__popc(leaders) <= 4) {
+    while (leaders) {
+      const int32_t k = __shfl_sync(0xffffffffu, key, __ffs(leaders) - 1);
+      leaders &= leaders - 1;
+      double sx = key == k ? m.x : 0.0, sy = key == k ? m.y : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, off);
+        sy += __shfl_xor_sync(0xffffffffu, sy, off);
+      }
+      if (lane == 0 && k >= 0 && sy != 0.0) {
+        atomicAdd(&acc[((int64_t)k * slots + slot) * 2], sx);
+        atomicAdd(&acc[((int64_t)k * slots + slot) * 2 + 1], sy);
+      }
+    }
+  } else if (m.y != 0.0) {
+    const int32_t ls = (slot + lane) & (slots - 1);
+    atomicAdd(&acc[((int64_t)key * slots + ls) * 2], m.x);
+    atomicAdd(&acc[((int64_t)key * slots + ls) * 2 + 1], m.y);
+  }
+}
+// The relative residual |sum| / magnitude of one key's sums (0 when nothing was summed); clears them.
+__device__ __forceinline__ double mass_fold(double *acc, int32_t slots, int32_t key) {
+  double2 *pm = reinterpret_cast<double2 *>(acc) + (int64_t)key * slots;
+  double sm = 0.0, mag = 0.0;
+  for (int k = 0; k < slots; ++k) {
+    const double2 a = __ldcg(pm + k);
+    sm += a.x;
+    mag += a.y;
+    pm[k] = make_double2(0.0, 0.0);
+  }
+  return mag > 0.0 ? fabs(sm) / mag : 0.0;
+}
+
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;

@@ -44,7 +44,7 @@ class vls_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("ms_update", ctypes.c_double), ("ms_pass_update", ctypes.c_double),
                 ("n_update", ctypes.c_int64), ("n_pass_update", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64), ("rechecks", ctypes.c_int64), ("pass_rechecks", ctypes.c_int64),
-                ("mass_resid", ctypes.c_double)]
+                ("mass_resid", ctypes.c_double), ("pass_mass_resid", ctypes.c_double)]
 
 
 EXPORTS = ["vls_default_options", "vls_constants", "vls_create", "vls_destroy", "vls_detect", "vls_detect_batch",
