@@ -393,3 +393,53 @@ def test_tunnel_pass_leaves_a_separated_covered_area():
         z = topo.vertex_cycle_edges(t.verts)
         assert topo.is_primal_cycle(z) and not topo.primal_is_null(z) and topo.cut_connected_primal(z)
         assert int((x & z).sum()) % 2 == 1
+
+
+# ------------------------------------------------- the mass check's identity on oracle states
+def _edges(m):
+    F = m.F
+    E = np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]])
+    return E  # every undirected edge twice (once per orientation): a closed oriented mesh
+
+
+@pytest.mark.parametrize("which,seed", [("capsules", 0), ("chain2", 1), ("torus", 0)])
+def test_mass_check_identity_on_oracle_states(which, seed, torus, chain2):
+    """The GPU's FP64 mass check rests on a lemma about the rows a step updates (the frontier R of
+    the next step): every vertex next to a row that is neither a row nor frozen (a dead or ended
+    layer's plateau) holds the same base value as that row.  Then, with m_v L_vu = 1 symmetric,
+    sum over rows of m_v (L base)_v = sum over rows of the flux into frozen neighbours, exactly.
+    Checked on oracle states after many step counts (before and after splits and merges), with
+    the frontier taken from its definition; on the split-heavy capsules the frozen flux is
+    nonzero, so the correction is needed."""
+    m = {"capsules": meshgen.capsules(5, 60), "chain2": chain2, "torus": torus}[which]
+    s = meshgen.seed_vertex(seed, m.nv)
+    full = oracle.detect(m, s, tunnels=0)
+    E = _edges(m)
+    a, b = E[:, 0], E[:, 1]
+    frozen_flux_seen = False
+    split_steps = [st for k, st in full.events() if k == "SPLIT"]
+    steps = sorted(set(np.linspace(5, full.steps - 1, 8).astype(int).tolist()
+                       + [x + dt for x in split_steps[:3] for dt in (0, 1, 3)]))
+    for t in steps:
+        r = oracle.detect(m, s, max_steps=int(t), tunnels=0)
+        lay, phi = r.layer, r.phi
+        state = np.concatenate([[1], r.layers[:, 2]])  # layer id -> final state (1 alive)
+        frozen = (lay != 0) & np.isin(state[lay], (2, 4))
+        base = np.where(lay == 0, 1.0, 1.0 - phi)
+        gives = np.where(lay == 0, 1, np.where(frozen, 0, np.where(phi < 1.0, 3, 2)))
+        acc = gives.copy()
+        np.bitwise_or.at(acc, a, gives[b])
+        R = (~frozen) & (acc == 3)
+        # the lemma, edge by edge
+        cross = R[a] & ~R[b] & ~frozen[b]
+        assert np.array_equal(base[a[cross]], base[b[cross]]), (which, t)
+        # the identity: sum over rows of sum_u (base(u) - base(v)) minus the frozen flux is 0
+        rows = R[a]
+        tot = float(np.sum(base[b[rows]] - base[a[rows]]))
+        fz = rows & frozen[b]
+        flux = float(np.sum(base[b[fz]] - base[a[fz]]))
+        mag = float(np.sum(base[b[rows]] + base[a[rows]])) + 1.0
+        assert abs(tot - flux) <= 1e-12 * mag, (which, t, tot, flux)
+        frozen_flux_seen |= abs(flux) > 1e-6
+    if which == "capsules":
+        assert frozen_flux_seen
