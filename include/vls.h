@@ -74,7 +74,7 @@ typedef enum { VLS_FP64 = 0, VLS_FP32_RECHECK = 1, VLS_BF16_RECHECK = 2 } vls_pr
  * readings of what the paper leaves open: dt = dt_factor * lbar^2 / (4 mu a^2 / 2) with
  * dt_factor 0.5; lbar = eta / 4 with eta = pi a / sqrt(2 w) (band width of the
  * travelling wave of Eq. (2)); snap threshold eps0 = 1e-3; isoline / arrival level
- * theta_iso = 0.5.
+ * theta_iso = 0.5; recheck margin 1e-5 (ten times the worst-case rounding of the FP32 step).
  */
 typedef struct {
   double mu, e, a, w;       /* Eq. (2) coefficients */
