@@ -130,3 +130,18 @@ def test_bf16_values_mid_run(vls, name):
     ef = float(np.abs(f.phi - o.phi).max())
     assert eb <= 2e-2 and ef <= 2e-6
     print(f"{name} after 60 steps: max |phi - oracle| BF16 {eb:.2e}, FP32 {ef:.2e}")
+
+
+def test_tube_chain_full_size_bf16(vls):
+    """The tube-chain workload at full size (512k faces, 4 seeds) in the BF16 form: every problem
+    OK, as many handle and tunnel loops as the genus, Reeb cycle rank equal to it, and the mass
+    check of both passes at FP32 rounding level."""
+    probs = meshgen.workload(2)
+    m = probs[0][0]
+    out = vls.detect(probs, precision="bf16")
+    assert len(out) == 4
+    for p in out:
+        assert p.status == 0, p.status_name
+        assert len(p.handles) == len(p.tunnels) == m.genus() == p.reeb_cycle_rank()
+        assert all(t.status == 0 for t in p.tunnels)
+        assert 0.0 < p.stats["mass_resid"] <= 1e-5 and 0.0 < p.stats["pass_mass_resid"] <= 1e-5
