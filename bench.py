@@ -64,7 +64,7 @@ def parse_args():
                          "instead of the autotuner (keeps tuning runs out of a profiler's launch list)")
     ap.add_argument("--max-steps", type=int, default=400)
     ap.add_argument("--max-pass-steps", type=int, default=200)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"],
                     help="form of the timed batched path (fp32: FP32 values with FP64 near-threshold recheck)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison arm")
     ap.add_argument("--plain-steps", type=int, default=1, help="timed steps of the plain FP64 arm")
@@ -252,7 +252,7 @@ def measure_batch_workload(vls, torch, stream, flush, prec: str, steps: int = 2)
     n_upd, ms_upd = pout[0].stats["n_update"], pout[0].stats["ms_update"]
     rows = sum(p.stats["row_updates"] for p in pout)
     deg = sum(3 * m.nf * len(s) for m, s in probs) / sum(m.nv * len(s) for m, s in probs)
-    bpr = (44 if prec == "fp64" else 40) + 4 * deg
+    bpr = {"fp64": 44, "fp32": 40, "bf16": 38}[prec] + 4 * deg
     gbs = (rows / n_upd * bpr) / (ms_upd / n_upd * 1e-3) / 1e9 if n_upd else None
     peak, _ = measured_peaks()
     mean = sum(ms) / len(ms)
@@ -499,8 +499,8 @@ def main():
     # ---- roofline of the frontier update kernel
     peak, peak_kind = measured_peaks()
     deg = sum(3 * m.nf * len(s) for m, s in probs) / sum(m.nv * len(s) for m, s in probs)
-    # frontier entry 8, row bounds 8, columns 4d, own state (layer 4 + value 8 or 4), output 16
-    bytes_per_row = (44 if prec == "fp64" else 40) + 4 * deg
+    # frontier entry 8, row bounds 8, columns 4d, own state (layer 4 + value 8, 4 or 2), output 16
+    bytes_per_row = {"fp64": 44, "fp32": 40, "bf16": 38}[prec] + 4 * deg
     launch_s = (upd_ms / upd_n) / 1e3 if upd_n else None
     rows_per_launch = rows / upd_n if upd_n else 0
     achieved = (rows_per_launch * bytes_per_row / launch_s) / 1e9 if launch_s else None
@@ -511,12 +511,15 @@ def main():
             "launches": upd_n, "share_of_timed_step": (upd_ms / ms) if ms else None,
             "method": "CUDA events around each launch in a kernel-timing pass of the same workload "
                       "(host-driven launches); the timed steps run the device-driven graph"}
-    cfg = dict(cfg, precision=("fp32 values, fp64 near-threshold recheck" if prec == "fp32" else "fp64"), inputs="resident in HBM (device pointers) for value; pinned host for e2e",
+    cfg = dict(cfg, precision={"fp32": "fp32 values, fp64 near-threshold recheck",
+                               "bf16": "bf16 values, fp32 arithmetic, fp64 near-threshold recheck",
+                               "fp64": "fp64"}[prec], inputs="resident in HBM (device pointers) for value; pinned host for e2e",
                l2="flushed by a 256 MiB write before every timed step",
                parallelism=f"{world} GPU(s), each its own copy of the batch" if world > 1 else "1 GPU")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic", "config": cfg,
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[prec], "data": "synthetic",
+            "config": cfg,
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "clocks": clocks, "check_vs_oracle": check}
     if batch is not None:
