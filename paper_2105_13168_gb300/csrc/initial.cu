@@ -121,9 +121,9 @@ __device__ __forceinline__ bool row_f32(const Params &P, int32_t l, int32_t lv, 
   return true;
 }
 
-// FP32 form: the FP64 redo of a row from its gathered inputs (rounded to float keeping every
-// threshold's side), out of line so that the hot row keeps few registers.  Rare: a collision or
-// a decision within the margin.
+// FP32 / BF16 forms: the FP64 redo of a row from its gathered inputs (rounded to the stored type
+// keeping every threshold's side), out of line so that the hot row keeps few registers.  Rare: a
+// collision or a decision within the margin.
 template <int MAXD, class TN>
 __device__ __noinline__ void row_redo(const Params &P, int nl, const int32_t *ls, int32_t lv, int32_t o, TN xv,
                                       const int32_t *nlay, const TN *nx, int32_t deg, double *out, double2 &mass) {
@@ -636,9 +636,10 @@ __device__ __forceinline__ void epilogue_phase(const Dev &d, const Handles &H, i
       d.rband[p] = 0;
       d.rhash[p] = 0ull;
       {
-        // mass check of this step's diffusion: the base's Laplacian, weighted by the lumped
-        // masses, sums to zero over the rows that can change (every other row has a uniform
-        // closed neighbourhood); the FP64 residual relative to the terms' magnitude
+        // mass check of this step's diffusion: the base's Laplacian weighted by the lumped
+        // masses, less the flux into frozen neighbours, sums to zero over the rows that can
+        // change (every other non-frozen vertex next to a row holds that row's base value); the
+        // FP64 residual relative to the terms' magnitude
         d.pmres[p] = fmax(d.pmres[p], mass_fold(d.pmass, d.mslots, p));
       }
       if (__ldcg(d.pstatus + p) != 0) d.pdone[p] = 1;
