@@ -1,13 +1,14 @@
 """Full-size parity on the tube-chain workload (8 smooth-unioned tori, ~512k faces, 4 seeds),
 in the batched launch configuration the benchmark times, against the CPU oracle run on all
-four seeds (a spawn process pool, started before the first GPU call)."""
+four seeds (a spawn process pool, started before the first GPU call): the FP64 form bit for bit,
+and the FP32 form the benchmark times under its contract (identical events and handle loops)."""
 import concurrent.futures as cf
 import multiprocessing as mp
 
 import pytest
 
 import meshgen
-from parity import assert_parity
+from parity import assert_fp32_parity, assert_parity
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -47,3 +48,8 @@ def test_tube_chain_full_size_parity(workload2):
     for g, o in zip(gpu, orc):
         assert o.status == 0 and len(o.handles) == 8
         assert_parity(g, o)
+    g32 = vls.detect(probs, keep_state=1, record_steps=1, precision="fp32")
+    for g, o in zip(g32, orc):
+        err, rec_bad, cov_bad, tun_bad = assert_fp32_parity(g, o, m.X)
+        print(f"tube chain full size, FP32 form: records differing {rec_bad}, cover steps differing {cov_bad}, "
+              f"tunnel loops differing {tun_bad}, max |phi - oracle| {err}")
