@@ -49,6 +49,11 @@
  *     the smallest-id outside endpoint reached first, depth first over unvisited reached
  *     neighbours in the order (T larger than here, T, id), stepping back along the path
  *     from dead ends, down to a source; close along the loop.
+ *
+ * Parity unpinned: the FP64 coordinates of handle-loop points (isoline interpolation) and of
+ * Reeb-graph nodes (band means).  The paper prints no worked example and its meshes are not
+ * available; the pins cover the loops' crossing edges, vertex cycles and homology classes and
+ * the Reeb graph's topology, not these coordinates.
  */
 #include "vls_oracle.h"
 
