@@ -4,8 +4,9 @@
 // limits (inside a pre-sized memory pool or an allocation-free region of a larger
 // application) or where every device byte is budgeted up front.  vls_tunnel_pass_noalloc()
 // serves them: the caller passes device inputs and outputs, and every byte of scratch the
-// pass needs lives in g_noalloc_scratch, a fixed array of this library that every device
-// which loads the library holds until the process exits.
+// pass needs lives in g_noalloc_scratch, a fixed array of this library.  A device reserves the
+// array when this translation unit's CUDA module is loaded on it -- with lazy module loading
+// (the CUDA default) at the first call on that device -- and holds it until the process exits.
 //
 // The pass is the same computation as a tunnel pass of vls_detect (same operator, update,
 // frontier rule, stop rule, trace and closure), run by a single thread block.
@@ -147,8 +148,15 @@ __global__ void __launch_bounds__(NA_THREADS) k_tunnel_noalloc(unsigned char *sc
   for (int64_t i = tid; i < 3 * (int64_t)nf; i += nth) atomicAdd(&s.cnt[F[i]], 1);
   __syncthreads();
   na_scan(s.cnt, s.rp, nv);
+  // a row longer than the operator table (LV_MAX neighbours) is rejected, as vls_detect does
+  for (int32_t v = tid; v < nv; v += nth)
+    if (s.rp[v + 1] - s.rp[v] > LV_MAX) bad = 1;
   for (int32_t v = tid; v < nv; v += nth) s.cnt[v] = 0;
   __syncthreads();
+  if (bad) {
+    if (tid == 0) { out_info[0] = VLS_EINVAL; out_info[1] = 0; out_info[2] = -1; out_info[3] = 0; }
+    return;
+  }
   for (int64_t i = tid; i < 3 * (int64_t)nf; i += nth) {
     const int64_t f = i / 3;
     const int32_t v = F[i], nx = F[3 * f + (i - 3 * f + 1) % 3];
@@ -208,7 +216,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_tunnel_noalloc(unsigned char *sc
         const int32_t v = s.fv[cur][i];
         int32_t dh = 0;
         for (int32_t k = s.rp[v]; k < s.rp[v + 1]; ++k) dh += na_kept(s, cover, step, ncut, v, s.col[k], k);
-        const double Lv = dh > 0 ? P.lv[dh < LV_MAX ? dh : LV_MAX] : 0.0;
+        const double Lv = dh > 0 ? P.lv[dh] : 0.0; // dh <= degree <= LV_MAX (checked above)
         const double diag = dh > 0 ? -P.s : 0.0;
         const double x = s.phi[v];
         double acc = 0.0, accb = 0.0;

@@ -1,13 +1,16 @@
-"""vls_tunnel_pass_noalloc (tunnel pass with no device allocation, for callers that cannot
-allocate device memory) against the tunnel loops vls_detect reports for the same handles.
+"""vls_tunnel_pass_noalloc: the tunnel pass for callers that cannot allocate device memory (code
+confined to a pre-sized pool or an allocation-free region of a larger application), checked
+against the tunnel loops vls_detect reports for the same handles and against the CPU oracle.
 
 Collected last on purpose: the entry point keeps its scratch in one static device array of
 the library, so this file also checks that consecutive calls (and calls after every other
-GPU test of the session) see no leftovers of earlier calls."""
+GPU test of the session) see no leftovers of earlier calls, and that a call after the first
+one on the device takes no device memory."""
 import numpy as np
 import pytest
 
 import meshgen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -27,36 +30,83 @@ def lib():
     return v, vls, torch
 
 
-def test_noalloc_tunnel_pass_matches_detect(lib):
+def _pass(vls, torch, F, nv, cover, step, edges):
+    out = torch.full((nv,), -7, dtype=torch.int32, device="cuda")
+    info = torch.full((4,), -9, dtype=torch.int32, device="cuda")
+    assert vls.vls_tunnel_pass_noalloc(F, nv, cover, step, edges, out, info) == 0
+    torch.cuda.synchronize()
+    info = info.cpu().numpy()
+    return info, out[: max(0, int(info[3]))].cpu().numpy()
+
+
+def _check_problem(lib, m, s, rounds=2):
     v, vls, torch = lib
-    m = meshgen.tube_chain(2, 56)
-    s = meshgen.seed_vertex(4, m.nv)
     g = v.detect([(m, [s])], keep_state=1)[0]
-    assert g.status_name == "OK" and len(g.handles) == 2
+    o = oracle.detect(m, s)
+    assert g.status_name == "OK" and o.status == 0 and len(g.handles) == len(o.handles) == m.genus()
     F = torch.from_numpy(m.F).cuda()
     cover = torch.from_numpy(g.cover).cuda()
     edges = [torch.from_numpy(h.edges).cuda() for h in g.handles]
     calls = 0
-    for _ in range(2):  # two rounds over both handles: consecutive calls share the scratch
-        for h, t, e in zip(g.handles, g.tunnels, edges):
-            out = torch.full((m.nv,), -7, dtype=torch.int32, device="cuda")
-            info = torch.full((4,), -9, dtype=torch.int32, device="cuda")
-            assert vls.vls_tunnel_pass_noalloc(F, m.nv, cover, h.step, e, out, info) == 0
-            torch.cuda.synchronize()
-            info = info.cpu().numpy()
+    for _ in range(rounds):  # consecutive calls share the scratch
+        for h, t, to, e in zip(g.handles, g.tunnels, o.tunnels, edges):
+            info, verts = _pass(vls, torch, F, m.nv, cover, h.step, e)
             assert (info[0], info[1], info[2]) == (t.status, t.stop_step, t.bstar), (info, t.status, t.stop_step)
+            assert (info[0], info[1], info[2]) == (to.status, to.stop_step, to.bstar)
             assert info[0] == 0 and info[3] == len(t.verts)
-            assert np.array_equal(out[: info[3]].cpu().numpy(), t.verts)
+            assert np.array_equal(verts, t.verts) and np.array_equal(verts, to.verts)
             calls += 1
-    assert calls == 4
+    return calls
 
 
-def test_noalloc_rejects_sizes_beyond_the_limit(lib):
+def test_noalloc_tunnel_pass_matches_detect_and_oracle(lib):
+    m = meshgen.tube_chain(2, 56)
+    assert _check_problem(lib, m, meshgen.seed_vertex(4, m.nv)) == 4
+
+
+def test_noalloc_whole_surface_retry(lib):
+    """Batch mesh 44, seed 2: the loop kept at its step-226 merge separates the area covered by
+    then, so the pass cannot reach the far side there and runs again on the whole surface."""
+    m, seeds = meshgen.batch_problem(44)
+    assert m.nv <= 262144
+    assert _check_problem(lib, m, seeds[2], rounds=1) == 4
+
+
+def test_noalloc_rejects_bad_input(lib):
     v, vls, torch = lib
-    F = torch.zeros((8, 3), dtype=torch.int32, device="cuda")
-    cover = torch.zeros(8, dtype=torch.int32, device="cuda")
-    e = torch.zeros((1, 2), dtype=torch.int32, device="cuda")
+    m = meshgen.torus(24, 12)
+    g = v.detect([(m, [0])], keep_state=1)[0]
+    h = g.handles[0]
+    F = torch.from_numpy(m.F).cuda()
+    cover = torch.from_numpy(g.cover).cuda()
+    e = torch.from_numpy(h.edges).clone()
+    e[0, 1] = m.nv  # an edge endpoint out of range: rejected on the device before any scratch write
+    info, _ = _pass(vls, torch, F, m.nv, cover, h.step, e.cuda())
+    assert vls.STATUS[int(info[0])] == "EINVAL"
+    # sizes beyond the fixed limits: rejected on the host
     out = torch.zeros(8, dtype=torch.int32, device="cuda")
-    info = torch.zeros(4, dtype=torch.int32, device="cuda")
-    st = vls.vls_tunnel_pass_noalloc(F, 262145, cover, 0, e, out, info)
+    inf = torch.zeros(4, dtype=torch.int32, device="cuda")
+    st = vls.vls_tunnel_pass_noalloc(F, 262145, cover, 0, e.cuda(), out, inf)
     assert vls.STATUS[st] == "ETOOLARGE"
+
+
+def test_noalloc_takes_no_device_memory_after_the_first_call(lib):
+    v, vls, torch = lib
+    m = meshgen.torus(32, 16)
+    g = v.detect([(m, [3])], keep_state=1)[0]
+    h, t = g.handles[0], g.tunnels[0]
+    F = torch.from_numpy(m.F).cuda()
+    cover = torch.from_numpy(g.cover).cuda()
+    e = torch.from_numpy(h.edges).cuda()
+    out = torch.full((m.nv,), -7, dtype=torch.int32, device="cuda")
+    info = torch.full((4,), -9, dtype=torch.int32, device="cuda")
+    assert vls.vls_tunnel_pass_noalloc(F, m.nv, cover, h.step, e, out, info) == 0  # loads the array
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert vls.vls_tunnel_pass_noalloc(F, m.nv, cover, h.step, e, out, info) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    i = info.cpu().numpy()
+    assert i[0] == 0 and np.array_equal(out[: i[3]].cpu().numpy(), t.verts)
