@@ -31,7 +31,8 @@ class Options(ctypes.Structure):
                 ("theta_iso", ctypes.c_double), ("lbar", ctypes.c_double),
                 ("max_steps", ctypes.c_int32), ("max_pass_steps", ctypes.c_int32),
                 ("seed_ring", ctypes.c_int32), ("naive", ctypes.c_int32), ("tunnels", ctypes.c_int32),
-                ("record_steps", ctypes.c_int32)]
+                ("record_steps", ctypes.c_int32), ("refine", ctypes.c_int32), ("offset", ctypes.c_double),
+                ("max_passes", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -78,6 +79,12 @@ def _load():
                 getattr(L, name).argtypes = [vp, i32]
             L.orc_handle_length.restype = dbl
             L.orc_handle_length.argtypes = [vp, i32]
+            for name, rt in [("orc_refined_info", P(i32)), ("orc_refined_verts", P(i32)),
+                             ("orc_loop_offset_change", P(dbl))]:
+                getattr(L, name).restype = rt
+                getattr(L, name).argtypes = [vp, i32]
+            L.orc_mean_edge.restype = dbl
+            L.orc_mean_edge.argtypes = [vp]
             _lib = L
     return _lib
 
@@ -138,6 +145,9 @@ class Result:
     layers: np.ndarray         # [L, 3] birth, death, final state
     handles: list = field(default_factory=list)
     tunnels: list = field(default_factory=list)
+    refined: list = field(default_factory=list)   # Tunnel-shaped records of the refined handle loops
+    offset_change: np.ndarray | None = None       # [h, 3]: handle, tunnel, refined (Sec. 3.5)
+    mean_edge: float = 0.0
 
     @property
     def status_name(self) -> str:
@@ -192,6 +202,12 @@ def detect(mesh, seed: int, opts: Options | None = None, **kw) -> Result:
             res.tunnels.append(Tunnel(status=int(ti[0]), stop_step=int(ti[1]), bstar=int(ti[2]),
                                       verts=_arr(L.orc_tunnel_verts(h, i), max(int(ti[3]), 0), np.int32),
                                       arrival=_arr(arr, nv, np.int32) if arr else None))
+            ri = _arr(L.orc_refined_info(h, i), 4, np.int32)
+            res.refined.append(Tunnel(status=int(ri[0]), stop_step=int(ri[1]), bstar=int(ri[2]),
+                                      verts=_arr(L.orc_refined_verts(h, i), max(int(ri[3]), 0), np.int32)))
+        res.offset_change = np.array([_arr(L.orc_loop_offset_change(h, i), 3, np.float64) for i in range(nh)]
+                                     ).reshape(-1, 3)
+        res.mean_edge = float(L.orc_mean_edge(h))
         return res
     finally:
         L.orc_free(h)

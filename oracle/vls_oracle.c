@@ -78,6 +78,9 @@ typedef struct {
   int32_t tinfo[4];
   int32_t *tverts;
   int32_t *arrival;
+  int32_t rinfo[4];   /* refined handle (Sec. 3.3): status, stop step, first vertex reached, n verts */
+  int32_t *rverts;
+  double dlen[3];     /* length change under the normal offset (Sec. 3.5): handle, tunnel, refined */
 } handle_t;
 
 struct orc_run {
@@ -115,6 +118,9 @@ struct orc_run {
   /* scratch */
   int32_t *stamp;
   int32_t stamp_id;
+  /* loop classification (Sec. 3.5): unit vertex normals, mean edge length */
+  double *vn;
+  double mean_edge;
 };
 
 /* ------------------------------------------------------------------ utils */
@@ -134,6 +140,9 @@ void orc_default_options(orc_options *o) {
   o->naive = 0;
   o->tunnels = 1;
   o->record_steps = 0;
+  o->refine = 1;
+  o->offset = 0.5;
+  o->max_passes = 0;
 }
 
 void orc_constants(const orc_options *o, double out[4]) {
@@ -1059,6 +1068,154 @@ static int tunnel_pass(orc_run *R, handle_t *H, int32_t th_step) {
   return st;
 }
 
+/* -------------------------------------------------- handle refinement pass */
+/* The third vertex of the face left of half-edge c->u, i.e. the neighbour that follows u in
+   counter-clockwise order around c (faces are counter-clockwise); -1 if c->u is no half-edge. */
+static int32_t next_ccw(const orc_run *R, int32_t c, int32_t u) {
+  int64_t k = slot_of(R, c, u);
+  if (k < 0) return -1;
+  const int32_t *t = R->F + 3 * R->hface[k];
+  for (int q = 0; q < 3; ++q)
+    if (t[q] != c && t[q] != u) return t[q];
+  return -1;
+}
+
+/* Sec. 3.3: the refined handle loop comes from the same single-layer pass as the tunnel loop, now
+   started on one side of the tunnel loop, with the tunnel loop as the only border (no restriction
+   to a covered area); the trace from the first far-side vertex reached, closed along the tunnel
+   loop, is the refined handle.
+   The tunnel cycle is first made simple by erasing its closed sub-loops in order along it from its
+   first vertex: the cycle crosses the handle loop once, on its closing edge, which the erasure
+   keeps, and an erased sub-loop never crosses it, so the simple cycle lies in the same class
+   modulo loops that pair evenly with the handle loop.  Sources: the cycle's vertices.  Border: the
+   edges from a cycle vertex c_i to its neighbours on the right, those met counter-clockwise from
+   c_{i-1} to c_{i+1} around c_i (the surface is oriented by its counter-clockwise faces); those
+   neighbours are the far side.  Returns the pass status. */
+static int refine_pass(orc_run *R, handle_t *H) {
+  H->rinfo[0] = ST_ELOOPFAIL;
+  H->rinfo[1] = 0;
+  H->rinfo[2] = -1;
+  H->rinfo[3] = 0;
+  if (H->tinfo[0] != ST_OK || !H->tverts || H->tinfo[3] < 3) return ST_ELOOPFAIL;
+  int64_t k = H->tinfo[3];
+  int32_t *cyc = (int32_t *)malloc(sizeof(int32_t) * k);
+  int64_t n = 0;
+  for (int64_t i = 0; i < k; ++i) {
+    int32_t v = H->tverts[i];
+    int64_t j = 0;
+    while (j < n && cyc[j] != v) ++j;
+    if (j < n) n = j + 1; /* v closes a sub-loop: erase it */
+    else cyc[n++] = v;
+  }
+  if (n < 3) { free(cyc); return ST_ELOOPFAIL; }
+  int32_t sid = ++R->stamp_id;
+  for (int64_t i = 0; i < n; ++i) R->stamp[cyc[i]] = sid;
+  int64_t cap = 64, m = 0;
+  int32_t *xe = (int32_t *)malloc(sizeof(int32_t) * 2 * cap);
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t c = cyc[i], prv = cyc[(i + n - 1) % n], nxt = cyc[(i + 1) % n];
+    int64_t deg = R->rp[c + 1] - R->rp[c], guard = 0;
+    int32_t u = prv;
+    for (;;) {
+      u = next_ccw(R, c, u);
+      if (u < 0 || u == nxt || ++guard > deg) break;
+      if (R->stamp[u] == sid) continue; /* a chord to another cycle vertex */
+      if (m == cap) { cap *= 2; xe = (int32_t *)realloc(xe, sizeof(int32_t) * 2 * cap); }
+      xe[2 * m] = c;
+      xe[2 * m + 1] = u;
+      ++m;
+    }
+  }
+  free(cyc);
+  if (m == 0) { free(xe); return ST_ELOOPFAIL; }
+  handle_t T;
+  memset(&T, 0, sizeof(T));
+  T.edges = xe;
+  T.info[3] = (int32_t)m;
+  int st = tunnel_pass(R, &T, INT32_MAX);
+  for (int q = 0; q < 4; ++q) H->rinfo[q] = T.tinfo[q];
+  H->rinfo[0] = st;
+  H->rverts = T.tverts;
+  free(T.arrival);
+  free(xe);
+  return st;
+}
+
+/* ------------------------------------------------ loop classification */
+/* Sec. 3.5: a loop is offset slightly along the surface normals and its length compared: tunnel
+   loops sit in saddle-shaped parts and shrink, handle loops grow.  Normals: the unit vertex normal
+   is the sum of the (area-weighted) normals of the faces around the vertex, taken in the vertex's
+   CSR order; an isoline point on edge (a, b) takes the normalised sum of a's and b's.  Offset: the
+   option's fraction of the mean edge length.  Returns length(offset loop) - length(loop). */
+static void vertex_normals(orc_run *R) {
+  int64_t nv = R->nv, nf = R->nf;
+  double *fn = (double *)malloc(sizeof(double) * 3 * nf);
+  for (int64_t f = 0; f < nf; ++f) {
+    const double *a = R->X + 3 * R->F[3 * f], *b = R->X + 3 * R->F[3 * f + 1], *c = R->X + 3 * R->F[3 * f + 2];
+    double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, w[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    fn[3 * f] = u[1] * w[2] - u[2] * w[1];
+    fn[3 * f + 1] = u[2] * w[0] - u[0] * w[2];
+    fn[3 * f + 2] = u[0] * w[1] - u[1] * w[0];
+  }
+  R->vn = (double *)malloc(sizeof(double) * 3 * nv);
+  double esum = 0.0;
+  for (int64_t v = 0; v < nv; ++v) {
+    double n[3] = {0.0, 0.0, 0.0};
+    for (int64_t k = R->rp[v]; k < R->rp[v + 1]; ++k) {
+      const double *g = fn + 3 * R->hface[k];
+      for (int d = 0; d < 3; ++d) n[d] = n[d] + g[d];
+      int32_t u = R->col[k];
+      if (u > v) {
+        double dx = R->X[3 * u] - R->X[3 * v], dy = R->X[3 * u + 1] - R->X[3 * v + 1], dz = R->X[3 * u + 2] - R->X[3 * v + 2];
+        esum = esum + sqrt(dx * dx + dy * dy + dz * dz);
+      }
+    }
+    double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    for (int d = 0; d < 3; ++d) R->vn[3 * v + d] = len > 0.0 ? n[d] / len : 0.0;
+  }
+  R->mean_edge = esum / (double)(R->nnz / 2);
+  free(fn);
+}
+static double dist3(const double *p, const double *q) {
+  double dx = q[0] - p[0], dy = q[1] - p[1], dz = q[2] - p[2];
+  return sqrt(dx * dx + dy * dy + dz * dz);
+}
+/* points P[n][3] with unit normals N[n][3], closed polyline */
+static double offset_change(const orc_run *R, const double *P, const double *N, int64_t n) {
+  double del = R->opt.offset * R->mean_edge, l0 = 0.0, l1 = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t j = (i + 1) % n;
+    double p[3], q[3];
+    for (int d = 0; d < 3; ++d) { p[d] = P[3 * i + d] + del * N[3 * i + d]; q[d] = P[3 * j + d] + del * N[3 * j + d]; }
+    l0 = l0 + dist3(P + 3 * i, P + 3 * j);
+    l1 = l1 + dist3(p, q);
+  }
+  return l1 - l0;
+}
+static double cycle_offset_change(const orc_run *R, const int32_t *verts, int64_t n) {
+  if (n < 2) return NAN;
+  double *P = (double *)malloc(sizeof(double) * 3 * n), *N = (double *)malloc(sizeof(double) * 3 * n);
+  for (int64_t i = 0; i < n; ++i)
+    for (int d = 0; d < 3; ++d) { P[3 * i + d] = R->X[3 * verts[i] + d]; N[3 * i + d] = R->vn[3 * verts[i] + d]; }
+  double r = offset_change(R, P, N, n);
+  free(P); free(N);
+  return r;
+}
+static double isoline_offset_change(const orc_run *R, const handle_t *H) {
+  int64_t n = H->info[3];
+  if (n < 2) return NAN;
+  double *N = (double *)malloc(sizeof(double) * 3 * n);
+  for (int64_t i = 0; i < n; ++i) {
+    const double *na = R->vn + 3 * H->edges[2 * i], *nb = R->vn + 3 * H->edges[2 * i + 1];
+    double s[3] = {na[0] + nb[0], na[1] + nb[1], na[2] + nb[2]};
+    double len = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    for (int d = 0; d < 3; ++d) N[3 * i + d] = len > 0.0 ? s[d] / len : 0.0;
+  }
+  double r = offset_change(R, H->pts, N, n);
+  free(N);
+  return r;
+}
+
 /* ------------------------------------------------------------------ API */
 orc_run *orc_detect(const double *X, int64_t nv, const int32_t *F, int64_t nf, int32_t seed_vertex,
                     const orc_options *o) {
@@ -1076,8 +1233,11 @@ orc_run *orc_detect(const double *X, int64_t nv, const int32_t *F, int64_t nf, i
   if (R->status != ST_OK) return R;
   R->stamp = (int32_t *)calloc(nv, sizeof(int32_t));
   R->status = initial_pass(R, seed_vertex);
+  const int initial_ok = R->status == ST_OK;
+  const int32_t npass = o->max_passes > 0 && o->max_passes < R->nh ? o->max_passes : R->nh;
+  for (int32_t h = 0; h < R->nh; ++h) R->h[h].tinfo[0] = -1;
   if (R->status == ST_OK && o->tunnels)
-    for (int32_t h = 0; h < R->nh; ++h) {
+    for (int32_t h = 0; h < npass; ++h) {
       /* Sec. 3.2: the pass is restricted to the area covered when the handle was found.  When
          the kept handle loop separates that area (its far side cannot be reached), the pass
          runs again on the whole surface. */
@@ -1090,6 +1250,21 @@ orc_run *orc_detect(const double *X, int64_t nv, const int32_t *F, int64_t nf, i
       }
       if (st != ST_OK && R->status == ST_OK) R->status = st;
     }
+  /* Sec. 3.3: a refinement pass for every handle whose tunnel pass succeeded */
+  for (int32_t h = 0; h < R->nh; ++h) R->h[h].rinfo[0] = -1;
+  if (initial_ok && o->tunnels && o->refine)
+    for (int32_t h = 0; h < npass; ++h) {
+      if (R->h[h].tinfo[0] != ST_OK) continue;
+      int st = refine_pass(R, &R->h[h]);
+      if (st != ST_OK && R->status == ST_OK) R->status = st;
+    }
+  vertex_normals(R);
+  for (int32_t h = 0; h < R->nh; ++h) {
+    handle_t *H = &R->h[h];
+    H->dlen[0] = isoline_offset_change(R, H);
+    H->dlen[1] = H->tinfo[0] == ST_OK ? cycle_offset_change(R, H->tverts, H->tinfo[3]) : NAN;
+    H->dlen[2] = H->rinfo[0] == ST_OK ? cycle_offset_change(R, H->rverts, H->rinfo[3]) : NAN;
+  }
   /* outputs */
   R->out_layer = (int32_t *)malloc(sizeof(int32_t) * nv);
   R->out_phi = (double *)malloc(sizeof(double) * nv);
@@ -1114,7 +1289,9 @@ void orc_free(orc_run *R) {
   free(R->lst); free(R->lbirth); free(R->ldeath); free(R->nodes); free(R->npos);
   for (int32_t i = 0; i < R->nh; ++i) {
     free(R->h[i].edges); free(R->h[i].verts); free(R->h[i].pts); free(R->h[i].tverts); free(R->h[i].arrival);
+    free(R->h[i].rverts);
   }
+  free(R->vn);
   free(R->h); free(R->out_layer); free(R->out_phi); free(R->rec); free(R->layers_out); free(R->stamp);
   free(R);
 }
@@ -1141,3 +1318,7 @@ double orc_handle_length(const orc_run *r, int32_t h) { return r->h[h].len; }
 const int32_t *orc_tunnel_info(const orc_run *r, int32_t h) { return r->h[h].tinfo; }
 const int32_t *orc_tunnel_verts(const orc_run *r, int32_t h) { return r->h[h].tverts; }
 const int32_t *orc_tunnel_arrival(const orc_run *r, int32_t h) { return r->h[h].arrival; }
+const int32_t *orc_refined_info(const orc_run *r, int32_t h) { return r->h[h].rinfo; }
+const int32_t *orc_refined_verts(const orc_run *r, int32_t h) { return r->h[h].rverts; }
+const double *orc_loop_offset_change(const orc_run *r, int32_t h) { return r->h[h].dlen; }
+double orc_mean_edge(const orc_run *r) { return r->mean_edge; }

@@ -30,6 +30,9 @@ typedef struct {
   int32_t naive;          /* 1: update/scan every vertex each step (cross-check of the frontier restriction) */
   int32_t tunnels;        /* 1: run the tunnel passes */
   int32_t record_steps;   /* 1: keep per-step frontier size / band size / band hash */
+  int32_t refine;         /* 1: run the handle-refinement pass after each tunnel pass (Sec. 3.3) */
+  double offset;          /* loop classification: normal offset in mean edge lengths (Sec. 3.5) */
+  int32_t max_passes;     /* tunnel (and refinement) passes run: the first max_passes handles; 0: all */
 } orc_options;
 
 typedef struct orc_run orc_run;
@@ -78,6 +81,16 @@ const int32_t *orc_tunnel_info(const orc_run *r, int32_t h);
 const int32_t *orc_tunnel_verts(const orc_run *r, int32_t h);
 /* arrival steps of pass h (-1 unreached), kept only when record_steps is set */
 const int32_t *orc_tunnel_arrival(const orc_run *r, int32_t h);
+
+/* refined handle loops (Sec. 3.3), one per handle: info [0] status (-1: not run), [1] stop step,
+ * [2] first vertex reached, [3] n verts; verts = the vertex cycle */
+const int32_t *orc_refined_info(const orc_run *r, int32_t h);
+const int32_t *orc_refined_verts(const orc_run *r, int32_t h);
+/* loop classification (Sec. 3.5): length change of the handle loop, the tunnel loop and the refined
+ * handle loop of handle h when offset along the unit vertex normals by offset x mean edge length
+ * (NaN where the loop does not exist); > 0 reads as a handle, < 0 as a tunnel */
+const double *orc_loop_offset_change(const orc_run *r, int32_t h);
+double orc_mean_edge(const orc_run *r);
 
 #ifdef __cplusplus
 }
