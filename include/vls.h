@@ -106,6 +106,23 @@ typedef struct {
                                pass: 32, 16 or 8 (fewer rows per warp spread a small frontier over
                                more warps and schedulers); 0 autotuned with the launch shape, or
                                32 when the shape is given (same results) */
+  int32_t refine;           /* 1: after each tunnel pass, the handle-refinement pass of its handle
+                               (Sec. 3.3; needs tunnels = 1) */
+  double offset;            /* loop classification (Sec. 3.5): normal offset as a fraction of the
+                               mesh's mean edge length; > 0 */
+  int32_t K;                /* layers that may meet at one vertex within a step: 0 or 4 (fixed by
+                               the per-row output buffer; other values are VLS_EINVAL) */
+  int32_t laplacian;        /* operator: 0 = uniform scaled Laplacian L_vu = s / d_v, L_vv = -s (the
+                               only one built; other values are VLS_EINVAL) */
+  int32_t max_passes;       /* tunnel (and refinement) passes per problem, in handle order; 0: all */
+  int32_t autotune;         /* 1: tune the launch shapes when threads = blocks_per_sm = 0 (see
+                               blocks_per_sm); 0: default shapes without tuning runs */
+  double drift_bound;       /* FP32 / BF16 forms: a threshold decision (snap at eps0 or 1 - eps0,
+                               theta_iso) whose FP64 value from the stored inputs lies within this of
+                               its threshold is counted "uncertified": the low-precision trajectory
+                               may have drifted from the FP64 one by this much, so the decision could
+                               go the other way there.  0 selects 1e-6 (FP32) or 2e-2 (BF16), above
+                               the largest drift measured on the workloads */
 } vls_options;
 
 /* A closed, oriented triangle mesh: X[nv][3] positions, F[nf][3] vertex ids (CCW). */
@@ -147,6 +164,17 @@ typedef struct {
    * way, and the flux into the pass's sources (held at 1, never rows) is taken out; the largest
    * residual over the steps of the problem's passes. */
   double pass_mass_resid;
+  /* refinement passes (Sec. 3.3): rows updated, max steps over the problem's passes, phase time
+   * (batch-wide), largest mass-check residual */
+  int64_t refine_updates;
+  int32_t refine_steps;
+  double ms_refine;
+  double refine_mass_resid;
+  double mean_edge;        /* the mesh's mean edge length (the classification offset's unit) */
+  /* FP32 / BF16 forms: uncertified decisions (vls_options.drift_bound) of the initial pass, of the
+   * tunnel passes and of the refinement passes; 0 in the FP64 form.  A result can differ from the
+   * FP64 one only after such a decision. */
+  int64_t uncertified, pass_uncertified, refine_uncertified;
 } vls_stats;
 
 /* Fill *o with the defaults above. */
@@ -186,12 +214,13 @@ VLS_API vls_status vls_result_status(const vls_result *r, int32_t p);
 VLS_API int32_t vls_result_genus(const vls_result *r, int32_t p);      /* (2 - chi) / 2 */
 VLS_API vls_status vls_result_stats(const vls_result *r, int32_t p, vls_stats *s);
 
-/* kind 0: handle loops (Sec. 3.1), kind 1: tunnel loops (Sec. 3.2) */
+/* kind 0: handle loops (Sec. 3.1), kind 1: tunnel loops (Sec. 3.2), kind 2: refined handle loops
+ * (Sec. 3.3); kinds 1 and 2 have one entry per handle (status -1 where the pass did not run) */
 VLS_API int32_t vls_result_num_loops(const vls_result *r, int32_t p, int32_t kind);
 /*
  * Loop i of the given kind.  Handles: *verts = the collapsed inside-vertex cycle of the
  * theta-isoline, *pts = its FP64 isoline points (one per crossing edge, *npts of them).
- * Tunnels: *verts = the vertex cycle, *pts = NULL.
+ * Tunnels and refined handles: *verts = the vertex cycle, *pts = NULL.
  */
 VLS_API vls_status vls_result_loop(const vls_result *r, int32_t p, int32_t kind, int32_t i, const int32_t **verts,
                            int64_t *n, const double **pts, int64_t *npts);
@@ -201,6 +230,15 @@ VLS_API vls_status vls_result_handle(const vls_result *r, int32_t p, int32_t i, 
                              int32_t info[3], double *length);
 /* Tunnel i (one per handle): info[0] status, [1] step its pass stopped, [2] first vertex reached */
 VLS_API vls_status vls_result_tunnel(const vls_result *r, int32_t p, int32_t i, int32_t info[3]);
+/* Refined handle i (Sec. 3.3; one per handle): info as vls_result_tunnel.  Its pass starts on the
+ * tunnel loop (made simple by erasing its closed sub-loops) and spreads to the loop's left; the
+ * loop's right neighbours are the far side. */
+VLS_API vls_status vls_result_refined(const vls_result *r, int32_t p, int32_t i, int32_t info[3]);
+/* Loop classification (Sec. 3.5) of handle i's loops: out[0] handle loop, out[1] tunnel loop,
+ * out[2] refined handle loop: length of the loop offset along the unit vertex normals by
+ * offset x mean edge length, minus its length (NaN where the loop does not exist).  Tunnel loops
+ * tend to shrink (< 0), handle loops to grow (> 0). */
+VLS_API vls_status vls_result_offset_change(const vls_result *r, int32_t p, int32_t i, double out[3]);
 
 /* Reeb graph (Sec. 5): nodes [n][2] = (kind 0 SEED / 1 SPLIT / 2 MERGE / 3 END, step),
  * positions [n][3] (mean of the narrow band); arcs = layers [L][3] = (birth node, death
@@ -215,8 +253,8 @@ VLS_API vls_status vls_result_state(const vls_result *r, int32_t p, const int32_
  * (host-driven launches).  names[i] (static strings), launches[i], ms[i] for i < *n. */
 VLS_API vls_status vls_result_kernel_times(const vls_result *r, const char *const **names, const int64_t **launches,
                                            const double **ms, int32_t *n);
-/* Per-step records (record_steps = 1): [steps][4] = frontier rows, band vertices, band hash
- * low 32 bits, high 32 bits. */
+/* Per-step records (record_steps = 1): [steps][5] = frontier rows, band vertices, band hash
+ * low 32 bits, high 32 bits, uncertified decisions of the step (FP32 / BF16 forms). */
 VLS_API vls_status vls_result_records(const vls_result *r, int32_t p, const int64_t **rec, int32_t *steps);
 
 VLS_API void vls_result_free(vls_result *r);
@@ -233,13 +271,18 @@ VLS_API void vls_result_free(vls_result *r);
  * and writes, on the device, out_verts[0..n) (capacity nv) and out_info[4] = status, step the
  * pass stopped, first vertex reached, n.  Options o may be NULL (defaults); the pass always runs
  * in FP64 (o->precision is not used), so it matches the FP64 form of vls_detect.
- * Limits: nv <= 262144, nf <= 786432, n_edges <= 65536; larger inputs return VLS_ETOOLARGE.
- * All scratch (about 22 MB) lives in one static device array of the library, which every
- * device that loads the library holds until the process exits.  The call allocates nothing
- * and returns after queueing one kernel on cuda_stream (NULL: default stream).  The first
- * call on a device looks up the array's device address; make that first call before any
- * stream capture.  Calls share the array: calls that overlap on the GPU (different streams,
- * different host threads) race and must be serialised by the caller.
+ * Limits: nv <= 262144, nf <= 786432, n_edges <= 65536; larger inputs return VLS_ETOOLARGE.  A
+ * vertex with more than 64 neighbours gives out_info[0] = VLS_EINVAL, as in vls_detect.
+ * All scratch (about 22 MB) lives in one static device array of the library.  The array is
+ * reserved on a device when the CUDA module holding it is loaded there: under CUDA's default
+ * lazy module loading that is the first call of this function on that device (with
+ * CUDA_MODULE_LOADING=EAGER, the creation of the device's context); from then on the device
+ * holds it until the process exits.  That first call also looks up the array's device
+ * address, so it can fail with VLS_ECUDA when the device has no room left for the array:
+ * make it before entering any region where allocation is not allowed, and before any stream
+ * capture.  Later calls allocate nothing and return after queueing one kernel on cuda_stream
+ * (NULL: default stream).  Calls share the array: calls that overlap on the GPU (different
+ * streams, different host threads) race and must be serialised by the caller.
  */
 VLS_API vls_status vls_tunnel_pass_noalloc(const int32_t *F, int64_t nf, int64_t nv, const int32_t *cover,
                                            int32_t handle_step, const int32_t *edges, int64_t n_edges,

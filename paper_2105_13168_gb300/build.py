@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libvls.so")
-SOURCES = ["operator.cu", "initial.cu", "events.cu", "tunnel.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["operator.cu", "initial.cu", "events.cu", "tunnel.cu", "refine.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ([ "-DVLS_CHECKED"] if os.environ.get("VLS_CHECKED") == "1" else []) + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--default-stream", "per-thread", "-I", os.path.join(ROOT, "include")]

@@ -7,6 +7,7 @@
 // steps), tunnel passes, result download.  Nothing on the path runs on the host except
 // launch bookkeeping and the final repacking of downloaded results.
 #include <algorithm>
+#include <array>
 #include <climits>
 #include <cmath>
 #include <cstdlib>
@@ -41,6 +42,8 @@ struct ProbResult {
     std::vector<int32_t> verts;
   };
   std::vector<Tunnel> tunnels;
+  std::vector<Tunnel> refined;             // refined handle loops (Sec. 3.3), one per handle
+  std::vector<std::array<double, 3>> dlen; // offset length change: handle, tunnel, refined (Sec. 3.5)
   std::vector<int32_t> lay, cover;
   std::vector<double> phi;
   std::vector<int64_t> rec;
@@ -98,6 +101,13 @@ extern "C" void vls_default_options(vls_options *o) {
   o->host_loop = 0;
   o->hook_variant = 0;
   o->rows_per_warp = 0;
+  o->refine = 1;
+  o->offset = 0.5;
+  o->K = 4;
+  o->laplacian = 0;
+  o->max_passes = 0;
+  o->autotune = 1;
+  o->drift_bound = 0.0;
 }
 
 extern "C" void vls_constants(const vls_options *o, double out[4]) {
@@ -141,7 +151,9 @@ extern "C" vls_status vls_create(vls_ctx **ctx, const vls_options *o, void *stre
   if ((c->opt.precision != VLS_FP64 && c->opt.precision != VLS_FP32_RECHECK && c->opt.precision != VLS_BF16_RECHECK) ||
       (c->opt.precision != VLS_FP64 && !(c->opt.recheck_margin > 0.0 && c->opt.recheck_margin < 0.25)) ||
       (c->opt.rows_per_warp != 0 && c->opt.rows_per_warp != 8 && c->opt.rows_per_warp != 16 &&
-       c->opt.rows_per_warp != 32)) {
+       c->opt.rows_per_warp != 32) ||
+      (c->opt.K != 0 && c->opt.K != KMAX) || c->opt.laplacian != 0 || !(c->opt.offset > 0.0) ||
+      c->opt.max_passes < 0 || (c->opt.autotune != 0 && c->opt.autotune != 1) || c->opt.drift_bound < 0.0) {
     delete c;
     return VLS_EINVAL;
   }
@@ -206,6 +218,8 @@ void layout_batch(Layout &L, Batch &b) {
   d.phif = pr == VLS_FP32_RECHECK ? L.take<float>(V) : nullptr;
   d.phih = pr == VLS_BF16_RECHECK ? L.take<__nv_bfloat16>(V) : nullptr;
   d.nrecheck = L.take<unsigned long long>(2);
+  d.punc = L.take<unsigned long long>(P);
+  d.runc = L.take<int32_t>(P);
   d.mslots = P <= (size_t)MASS_SPREAD_MAXP ? MASS_SLOTS : 1;
   d.pmass = L.take<double>(2 * (size_t)d.mslots * P);
   d.pmres = L.take<double>(P);
@@ -274,16 +288,22 @@ void layout_batch(Layout &L, Batch &b) {
   d.hedge = L.take<int32_t>(2 * (size_t)d.ecap);
   d.hpts = L.take<double>(3 * (size_t)d.ecap);
   d.hverts = L.take<int32_t>(d.ecap);
-  d.rec = L.take<long long>(d.record ? (size_t)P * d.rcap * 4 : 1);
+  d.rec = L.take<long long>(d.record ? (size_t)P * d.rcap * 5 : 1);
   d.rhash = L.take<unsigned long long>(P);
   d.rband = L.take<int32_t>(P);
+  d.vn = L.take<double>(3 * V);
+  d.elen = L.take<double>(V);
+  d.pmedge = L.take<double>(P);
+  d.hdl = L.take<double>(d.hcap);
   d.err = L.take<int32_t>(4);
   d.ctl = L.take<int32_t>(CTL_SIZE);
   d.nalive = L.take<int32_t>(P);
   d.nbl = L.take<int32_t>(P);
 }
 
-void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut) {
+// nx > 0: a refinement chunk -- its own border-edge pool (nx edges) and the tunnel cycles it starts
+// from (ncyc vertex ids)
+void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut, int64_t nx, int64_t ncyc) {
   TDev &T = b.td;
   T.NP = NP;
   T.PV = (int32_t)PV;
@@ -316,6 +336,7 @@ void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut) {
   T.qslots = NP <= MASS_SPREAD_MAXP ? MASS_SLOTS : 1;
   T.qmass = L.take<double>(2 * (size_t)T.qslots * NP);
   T.qmres = L.take<double>(NP);
+  T.qunc = L.take<unsigned long long>(NP);
   T.qupd = L.take<long long>(NP);
   T.active = L.take<int32_t>(1);
   T.tvoff = L.take<int32_t>(NP);
@@ -324,6 +345,14 @@ void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut) {
   T.tverts = L.take<int32_t>(T.tvcap);
   T.ntverts = L.take<int32_t>(1);
   T.path = L.take<int32_t>(PV);
+  T.qdl = L.take<double>(NP);
+  if (nx > 0) {
+    T.xedge = L.take<int32_t>(2 * nx);
+    b.r_cyc = L.take<int32_t>(ncyc);
+    b.r_coff = L.take<int32_t>(NP);
+    b.r_clen = L.take<int32_t>(NP);
+    b.r_xcap = L.take<int32_t>(NP);
+  }
 }
 
 __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
@@ -353,6 +382,185 @@ template <class T> bool d2h(std::vector<T> &dst, const T *src, size_t n, cudaStr
   if (g_d2h_counter) *g_d2h_counter += (int64_t)(n * sizeof(T));
   return cudaMemcpyAsync(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, st) == cudaSuccess;
 }
+
+#define CKR(x)                                                                                    \
+  do {                                                                                            \
+    cudaError_t _e = (x);                                                                         \
+    if (_e != cudaSuccess) {                                                                      \
+      if (debug_on()) std::fprintf(stderr, "vls: %s failed at api.cu:%d: %s\n", #x, __LINE__,      \
+                                   cudaGetErrorString(_e));                                       \
+      return _e;                                                                                  \
+    }                                                                                             \
+  } while (0)
+
+// Results of single-layer passes (tunnel or refinement), per handle of the batch.  A pass that did
+// not run reports (status -1, stop step 0, first vertex 0).
+struct PassOut {
+  std::vector<int32_t> status, steps, bstar, voff, vn;
+  std::vector<int64_t> upd, unc;
+  std::vector<double> mres, dl;
+  std::vector<int32_t> verts; // vertex cycles (local ids), pool
+  explicit PassOut(int32_t nh)
+      : status(nh, -1), steps(nh, 0), bstar(nh, 0), voff(nh, 0), vn(nh, 0), upd(nh, 0), unc(nh, 0), mres(nh, 0.0),
+        dl(nh, std::nan("")) {}
+};
+enum PassKind : int { PASS_TUNNEL = 0, PASS_REFINE = 1 };
+
+// One chunk of passes: lay the pass state out after the batch state (keep_batch bytes), set the
+// passes up, run them (tunnel.cu), classify their loops (refine.cu) and download the results into
+// out.  Tunnel passes (Sec. 3.2) take handle h's crossing edges as the border and dom[h] as the
+// domain step; refinement passes (Sec. 3.3) take the border from tunnel loop h in tun.
+cudaError_t run_chunk(vls_ctx *ctx, Batch &b, size_t keep_batch, int kind, const std::vector<int32_t> &chunk,
+                      const std::vector<int32_t> &h_hprob, const std::vector<int32_t> &dom,
+                      const std::vector<int32_t> &h_hoff, const std::vector<int32_t> &h_hn, const PassOut *tun,
+                      PassOut &out, int32_t *tau_out) {
+  Dev &d = b.d;
+  cudaStream_t st = b.st;
+  const int32_t NP = (int32_t)chunk.size();
+  std::vector<int32_t> pbase(NP + 1), pprob(NP), pstep(NP), pcoff(NP), pcn(NP), heoff(NP), hen(NP);
+  std::vector<int32_t> rcyc, rcoff(NP), rclen(NP), xcap(NP);
+  int64_t PV = 0, ncut = 0, nx = 0;
+  for (int32_t q = 0; q < NP; ++q) {
+    const int32_t h = chunk[q], p = h_hprob[h];
+    pbase[q] = (int32_t)PV;
+    pprob[q] = p;
+    pstep[q] = dom[h];
+    if (kind == PASS_TUNNEL) {
+      heoff[q] = h_hoff[h];
+      hen[q] = h_hn[h];
+      pcn[q] = 2 * h_hn[h];
+      pcoff[q] = (int32_t)ncut;
+      ncut += 2 * h_hn[h];
+    } else {
+      const int32_t len = tun->vn[h];
+      rcoff[q] = (int32_t)rcyc.size();
+      rclen[q] = len;
+      for (int32_t i = 0; i < len; ++i) rcyc.push_back(tun->verts[tun->voff[h] + i] + b.voff[p]);
+      // a cycle vertex has at most degree - 2 neighbours on one side (degree <= LV_MAX, checked)
+      xcap[q] = (LV_MAX - 2) * std::max(len, 1);
+      heoff[q] = (int32_t)nx;
+      nx += xcap[q];
+      pcoff[q] = (int32_t)ncut;
+      ncut += 2 * (int64_t)xcap[q];
+    }
+    PV += b.voff[p + 1] - b.voff[p];
+  }
+  pbase[NP] = (int32_t)PV;
+  if (PV >= INT32_MAX / 2 || ncut >= INT32_MAX / 2) {
+    if (debug_on()) std::fprintf(stderr, "vls: pass chunk of %lld pass-vertices\n", (long long)PV);
+    return cudaErrorMemoryAllocation;
+  }
+  Layout L{&ctx->arena, true};
+  L.bytes = keep_batch;
+  layout_tunnels(L, b, NP, PV, ncut, nx, (int64_t)rcyc.size());
+  if (L.bytes > ctx->arena.cap) {
+    // grow: the batch state must survive, so copy it into the new arena
+    char *old = ctx->arena.base;
+    char *nb = nullptr;
+    CKR(cudaMalloc(&nb, L.bytes + L.bytes / 8));
+    CKR(cudaMemcpyAsync(nb, old, keep_batch, cudaMemcpyDeviceToDevice, st));
+    CKR(cudaStreamSynchronize(st));
+    // rebase every pointer of the batch: re-run the layout on the new base
+    ctx->arena.base = nb;
+    ctx->arena.cap = L.bytes + L.bytes / 8;
+    ctx->arena.reset();
+    Layout L2{&ctx->arena, false};
+    layout_batch(L2, b);
+    cudaFree(old);
+  }
+  ctx->arena.used = keep_batch;
+  Layout L3{&ctx->arena, false};
+  layout_tunnels(L3, b, NP, PV, ncut, nx, (int64_t)rcyc.size());
+  TDev &T = b.td;
+  T.err = d.err;
+  if (kind == PASS_TUNNEL) T.xedge = d.hedge;
+  auto up = [&](const int32_t *dst, const std::vector<int32_t> &src, size_t n) {
+    b.h2d += (int64_t)(sizeof(int32_t) * n);
+    return cudaMemcpyAsync(const_cast<int32_t *>(dst), src.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+  };
+  CKR(up(T.pbase, pbase, NP + 1));
+  CKR(up(T.pprob, pprob, NP));
+  CKR(up(T.pstep, pstep, NP));
+  CKR(up(T.pcoff, pcoff, NP));
+  CKR(up(T.heoff, heoff, NP));
+  if (kind == PASS_TUNNEL) {
+    CKR(up(T.pcn, pcn, NP));
+    CKR(up(T.hen, hen, NP));
+  }
+  CKR(cudaMemsetAsync(T.flag, 0, (size_t)PV, st));
+  if (T.phih) CKR(cudaMemsetAsync(T.phih, 0, sizeof(__nv_bfloat16) * PV, st));
+  else if (T.phif) CKR(cudaMemsetAsync(T.phif, 0, sizeof(float) * PV, st));
+  else CKR(cudaMemsetAsync(T.phi, 0, sizeof(double) * PV, st));
+  CKR(cudaMemsetAsync(T.T, 0xff, sizeof(int32_t) * PV, st));
+  CKR(cudaMemsetAsync(T.stamp, 0, sizeof(int32_t) * PV, st));
+  CKR(cudaMemsetAsync(T.nf, 0, sizeof(int32_t) * 2, st));
+  CKR(cudaMemsetAsync(T.qdone, 0, sizeof(int32_t) * NP, st));
+  CKR(cudaMemsetAsync(T.qsteps, 0, sizeof(int32_t) * NP, st));
+  CKR(cudaMemsetAsync(T.qstatus, 0xff, sizeof(int32_t) * NP, st));
+  k_fill_i32<<<(NP + 255) / 256, 256, 0, st>>>(T.qbstar, NP, 0x7fffffff); VLS_LAUNCH(b);
+  CKR(cudaMemsetAsync(T.qcnt, 0, sizeof(int32_t) * 2 * NP, st));
+  CKR(cudaMemsetAsync(T.qmass, 0, sizeof(double) * 2 * T.qslots * NP, st));
+  CKR(cudaMemsetAsync(T.qmres, 0, sizeof(double) * NP, st));
+  CKR(cudaMemsetAsync(T.qunc, 0, sizeof(unsigned long long) * NP, st));
+  CKR(cudaMemsetAsync(T.qupd, 0, sizeof(long long) * NP, st));
+  CKR(cudaMemsetAsync(T.ntverts, 0, sizeof(int32_t), st));
+  CKR(cudaMemsetAsync(T.tvn, 0, sizeof(int32_t) * NP, st));
+  if (kind == PASS_REFINE) {
+    CKR(up(b.r_cyc, rcyc, rcyc.size()));
+    CKR(up(b.r_coff, rcoff, NP));
+    CKR(up(b.r_clen, rclen, NP));
+    CKR(up(b.r_xcap, xcap, NP));
+    CKR(launch_refine_prep(b, b.r_cyc, b.r_coff, b.r_clen, const_cast<int32_t *>(T.xedge), b.r_xcap,
+                           const_cast<int32_t *>(T.hen), const_cast<int32_t *>(T.pcn)));
+  }
+  CKR(run_tunnels(b, tau_out));
+  CKR(launch_classify_passes(b, d.vn, d.pmedge));
+  std::vector<int32_t> qs(NP), qst(NP), qb(NP), tvo(NP), tvn(NP), qhen(NP);
+  std::vector<long long> qupd(NP);
+  std::vector<unsigned long long> qunc(NP);
+  std::vector<double> qmres(NP), qdl(NP);
+  int32_t ntv = 0;
+  CKR(cudaMemcpyAsync(qs.data(), T.qstatus, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
+  CKR(cudaMemcpyAsync(qst.data(), T.qsteps, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
+  CKR(cudaMemcpyAsync(qb.data(), T.qbstar, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
+  CKR(cudaMemcpyAsync(tvo.data(), T.tvoff, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
+  CKR(cudaMemcpyAsync(tvn.data(), T.tvn, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
+  CKR(cudaMemcpyAsync(qhen.data(), T.hen, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
+  CKR(cudaMemcpyAsync(&ntv, T.ntverts, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CKR(cudaMemcpyAsync(qupd.data(), T.qupd, sizeof(long long) * NP, cudaMemcpyDeviceToHost, st));
+  CKR(cudaMemcpyAsync(qmres.data(), T.qmres, sizeof(double) * NP, cudaMemcpyDeviceToHost, st));
+  CKR(cudaMemcpyAsync(qdl.data(), T.qdl, sizeof(double) * NP, cudaMemcpyDeviceToHost, st));
+  CKR(cudaMemcpyAsync(qunc.data(), T.qunc, sizeof(unsigned long long) * NP, cudaMemcpyDeviceToHost, st));
+  CKR(cudaStreamSynchronize(st));
+  b.d2h += (int64_t)(6 * sizeof(int32_t) + 2 * sizeof(long long) + 2 * sizeof(double)) * NP + (int64_t)sizeof(int32_t);
+  ntv = std::min(ntv, T.tvcap);
+  const size_t tv0 = out.verts.size();
+  out.verts.resize(tv0 + (size_t)ntv);
+  if (ntv) CKR(cudaMemcpyAsync(out.verts.data() + tv0, T.tverts, sizeof(int32_t) * ntv, cudaMemcpyDeviceToHost, st));
+  CKR(cudaStreamSynchronize(st));
+  b.d2h += (int64_t)sizeof(int32_t) * ntv;
+  for (int32_t q = 0; q < NP; ++q) {
+    const int32_t h = chunk[q];
+    out.status[h] = qs[q];
+    out.steps[h] = qst[q];
+    out.bstar[h] = qb[q] == 0x7fffffff ? -1 : qb[q];
+    out.voff[h] = (int32_t)tv0 + tvo[q];
+    out.vn[h] = tvn[q];
+    out.upd[h] = qupd[q];
+    out.mres[h] = qmres[q];
+    out.unc[h] = (int64_t)qunc[q];
+    out.dl[h] = qdl[q];
+    if (kind == PASS_REFINE && qhen[q] == 0) { // no border: a degenerate tunnel cycle
+      out.status[h] = VLS_ELOOPFAIL;
+      out.steps[h] = 0;
+      out.bstar[h] = -1;
+      out.vn[h] = 0;
+      out.dl[h] = std::nan("");
+    }
+  }
+  return cudaSuccess;
+}
+#undef CKR
 
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0;
@@ -437,7 +645,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
   // launch shapes: explicit options, else the autotuned table of this device / size class
   TuneEntry tuned;
   bool have_tuned = false;
-  if (ctx->opt.threads == 0 && ctx->opt.blocks_per_sm == 0) {
+  if (ctx->opt.threads == 0 && ctx->opt.blocks_per_sm == 0 && ctx->opt.autotune) {
     int dev = 0;
     cudaGetDevice(&dev);
     int64_t vt = 0;
@@ -532,6 +740,10 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     P.mun[0] = 0.0;
     for (int k = 1; k <= KMAX + 1; ++k) P.mun[k] = P.mu / (double)k;
     P.margin = ctx->opt.recheck_margin;
+    P.offset = ctx->opt.offset;
+    P.drift = ctx->opt.precision == VLS_FP64 ? 0.0
+              : ctx->opt.drift_bound > 0.0 ? ctx->opt.drift_bound
+              : ctx->opt.precision == VLS_BF16_RECHECK ? 2e-2 : 1e-6;
     P.f_e = (float)P.e;
     P.f_w = (float)P.w;
     P.f_ah = (float)P.ah;
@@ -541,6 +753,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     P.f_one_m_eps = (float)P.one_m_eps;
     P.f_theta = (float)P.theta;
     P.f_margin = (float)P.margin;
+    P.f_drift = (float)P.drift;
     for (int k = 0; k <= LV_MAX; ++k) P.f_lv[k] = (float)P.lv[k];
     for (int k = 0; k <= KMAX + 1; ++k) P.f_mun[k] = (float)P.mun[k];
   }
@@ -582,12 +795,12 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
 
   cudaError_t err = cudaSuccess;
   cudaStream_t st = b.st;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   std::vector<int32_t> stage, h_rpb, h_status, h_steps, h_nodes_cnt;
   int32_t h_nn = 0, h_nh = 0;
-  int32_t tunnel_tau = 0;
+  int32_t tunnel_tau = 0, refine_tau = 0;
   std::vector<int32_t> h_hprob, h_hstep, h_hlayer, h_hnode, h_hoff, h_hn, h_hvoff, h_hvn;
-  std::vector<double> h_hlen;
+  std::vector<double> h_hlen, h_hdl;
   {
     Layout L{&ctx->arena, true};
     layout_batch(L, b);
@@ -596,18 +809,32 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     Layout L2{&ctx->arena, false};
     layout_batch(L2, b);
   }
-  for (int i = 0; i < 5; ++i) CK(cudaEventCreate(&ev[i]));
+  for (int i = 0; i < 6; ++i) CK(cudaEventCreate(&ev[i]));
   if (const char *pz = std::getenv("VLS_POISON"))
     if (pz[0] == '1') CK(cudaMemsetAsync(ctx->arena.base, 0xab, ctx->arena.cap, st)); // debug: expose unset reads
   {
     Dev &d = b.d;
-    // inputs into the union graph
-    for (int32_t q = 0; q < b.P; ++q) {
-      const vls_mesh &m = meshes[b.mesh_of[q]];
-      const cudaMemcpyKind kx = m.device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-      if (!m.device) b.h2d += (int64_t)(sizeof(double) * 3 * m.nv + sizeof(int32_t) * 3 * m.nf);
-      CK(cudaMemcpyAsync(const_cast<double *>(d.X) + 3 * (int64_t)b.voff[q], m.X, sizeof(double) * 3 * m.nv, kx, st));
-      CK(cudaMemcpyAsync(const_cast<int32_t *>(d.F) + 3 * (int64_t)b.foff[q], m.F, sizeof(int32_t) * 3 * m.nf, kx, st));
+    // inputs into the union graph: a host mesh crosses to the device once, for its first problem;
+    // the mesh's other seeds copy that problem's slots on the device
+    {
+      std::vector<int32_t> first_of(n_mesh, -1);
+      for (int32_t q = 0; q < b.P; ++q) {
+        const int32_t mi = b.mesh_of[q];
+        const vls_mesh &m = meshes[mi];
+        const int32_t q0 = first_of[mi];
+        double *xq = const_cast<double *>(d.X) + 3 * (int64_t)b.voff[q];
+        int32_t *fq = const_cast<int32_t *>(d.F) + 3 * (int64_t)b.foff[q];
+        if (q0 >= 0 && !m.device) {
+          CK(cudaMemcpyAsync(xq, d.X + 3 * (int64_t)b.voff[q0], sizeof(double) * 3 * m.nv, cudaMemcpyDeviceToDevice, st));
+          CK(cudaMemcpyAsync(fq, d.F + 3 * (int64_t)b.foff[q0], sizeof(int32_t) * 3 * m.nf, cudaMemcpyDeviceToDevice, st));
+          continue;
+        }
+        first_of[mi] = q;
+        const cudaMemcpyKind kx = m.device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (!m.device) b.h2d += (int64_t)(sizeof(double) * 3 * m.nv + sizeof(int32_t) * 3 * m.nf);
+        CK(cudaMemcpyAsync(xq, m.X, sizeof(double) * 3 * m.nv, kx, st));
+        CK(cudaMemcpyAsync(fq, m.F, sizeof(int32_t) * 3 * m.nf, kx, st));
+      }
     }
     CK(cudaMemcpyAsync(const_cast<int32_t *>(d.voff), b.voff.data(), sizeof(int32_t) * (b.P + 1), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(const_cast<int32_t *>(d.foff), b.foff.data(), sizeof(int32_t) * (b.P + 1), cudaMemcpyHostToDevice, st));
@@ -620,6 +847,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     int32_t *stage_d = d.pev; // 5 * P ints needed: pev holds 4 * P, spill into pupd (2 * P ints)
     stage_d = reinterpret_cast<int32_t *>(d.ophi); // V * KMAX doubles: ample scratch before the first step
     CK(build_operator(b, stage_d));
+    CK(launch_vnormals(b, d.vn, d.elen, d.pmedge));
     stage.resize(5 * (size_t)b.P);
     CK(cudaMemcpyAsync(stage.data(), stage_d, sizeof(int32_t) * 5 * b.P, cudaMemcpyDeviceToHost, st));
     b.d2h += (int64_t)sizeof(int32_t) * (6 * b.P + 1);
@@ -649,6 +877,8 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     else if (d.phif) CK(cudaMemsetAsync(d.phif, 0, sizeof(float) * b.V, st));
     else CK(cudaMemsetAsync(d.phi, 0, sizeof(double) * b.V, st));
     CK(cudaMemsetAsync(d.nrecheck, 0, sizeof(unsigned long long) * 2, st));
+    CK(cudaMemsetAsync(d.punc, 0, sizeof(unsigned long long) * b.P, st));
+    CK(cudaMemsetAsync(d.runc, 0, sizeof(int32_t) * b.P, st));
     CK(cudaMemsetAsync(d.pmass, 0, sizeof(double) * 2 * d.mslots * b.P, st));
     CK(cudaMemsetAsync(d.pmres, 0, sizeof(double) * b.P, st));
     CK(cudaMemsetAsync(d.cover, 0xff, sizeof(int32_t) * b.V, st));
@@ -684,7 +914,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       CK(cudaMemcpyAsync(d.ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, st));
       b.h2d += (int64_t)sizeof(ctl);
     }
-    if (d.record) CK(cudaMemsetAsync(d.rec, 0, sizeof(long long) * 4 * (size_t)b.P * d.rcap, st));
+    if (d.record) CK(cudaMemsetAsync(d.rec, 0, sizeof(long long) * 5 * (size_t)b.P * d.rcap, st));
     CK(init_state(b));
     // ---- initial pass
     if (b.host_loop) {
@@ -727,14 +957,21 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       goto fail;
     }
     CK(cudaStreamSynchronize(st));
-    // passes: handles of problems whose initial pass succeeded
+    // classification of the handle (isoline) loops (Sec. 3.5)
+    CK(launch_classify_handles(b, d.vn, d.pmedge, d.hdl, h_nh));
+    if (!d2h(h_hdl, d.hdl, h_nh, st)) {
+      err = cudaErrorUnknown;
+      goto fail;
+    }
+    PassOut tun(h_nh), ref(h_nh);
+    // passes: handles of problems whose initial pass succeeded (at most max_passes per problem)
     std::vector<int32_t> pass_h;
-    if (ctx->opt.tunnels)
+    if (ctx->opt.tunnels) {
+      std::vector<int32_t> per_prob(b.P, 0);
       for (int32_t h = 0; h < h_nh; ++h)
-        if (h_status[h_hprob[h]] == VLS_OK) pass_h.push_back(h);
-    // a pass that did not run reports (status -1, stop step 0, first vertex 0)
-    std::vector<int32_t> h_tstatus(h_nh, -1), h_tsteps(h_nh, 0), h_tb(h_nh, 0), h_tvoff(h_nh, 0), h_tvn(h_nh, 0);
-    std::vector<int32_t> h_tverts;
+        if (h_status[h_hprob[h]] == VLS_OK && (ctx->opt.max_passes <= 0 || per_prob[h_hprob[h]]++ < ctx->opt.max_passes))
+          pass_h.push_back(h);
+    }
     // passes run in chunks whose dense per-pass state (one entry per vertex of the pass's
     // problem, about 45 B each) fits a bound set by the free device memory
     int64_t pv_cap = (int64_t(1) << 30) - (int64_t(1) << 20); // pass-vertex ids stay below INT32_MAX / 2
@@ -745,148 +982,72 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       if (const char *ev = std::getenv("VLS_PASS_VERTS")) pv_cap = std::atoll(ev);
       pv_cap = std::max<int64_t>(pv_cap, 1);
     }
+    const size_t keep_batch = ctx->arena.used;
+    auto run_all = [&](int kind, const std::vector<int32_t> &hs, const std::vector<int32_t> &dom, PassOut &out,
+                       int32_t *tau_sum) -> cudaError_t {
+      for (size_t c0 = 0; c0 < hs.size();) {
+        size_t c1 = c0;
+        int64_t pv_chunk = 0;
+        while (c1 < hs.size()) {
+          const int32_t p = h_hprob[hs[c1]];
+          const int64_t n = b.voff[p + 1] - b.voff[p];
+          if (c1 > c0 && pv_chunk + n > pv_cap) break;
+          pv_chunk += n;
+          ++c1;
+        }
+        const std::vector<int32_t> chunk(hs.begin() + (std::ptrdiff_t)c0, hs.begin() + (std::ptrdiff_t)c1);
+        c0 = c1;
+        int32_t chunk_tau = 0;
+        const cudaError_t e = run_chunk(ctx, b, keep_batch, kind, chunk, h_hprob, dom, h_hoff, h_hn, &tun, out,
+                                        &chunk_tau);
+        if (e != cudaSuccess) return e;
+        *tau_sum += chunk_tau; // launch accounting: steps summed over chunks
+      }
+      return cudaSuccess;
+    };
     // Sec. 3.2: a pass is restricted to the area covered when its handle was found.  A pass
     // that cannot reach the far side there (the kept handle loop separates that area) runs a
     // second time on the whole surface (domain step INT32_MAX).
     std::vector<int32_t> pass_dom(h_nh, 0);
-    const size_t keep_batch = ctx->arena.used;
     for (int32_t h : pass_h) pass_dom[h] = h_hstep[h];
-    for (int round = 0; round < 2 && !pass_h.empty(); ++round) {
-    if (round == 1) {
+    CK(run_all(PASS_TUNNEL, pass_h, pass_dom, tun, &tunnel_tau));
+    {
       std::vector<int32_t> again;
       for (int32_t h : pass_h)
-        if (h_tstatus[h] == VLS_ELOOPFAIL && h_tb[h] < 0 && h_hn[h] > 0) {
+        if (tun.status[h] == VLS_ELOOPFAIL && tun.bstar[h] < 0 && h_hn[h] > 0) {
           again.push_back(h);
           pass_dom[h] = INT32_MAX;
         }
-      pass_h.swap(again);
+      if (!again.empty()) CK(run_all(PASS_TUNNEL, again, pass_dom, tun, &tunnel_tau));
     }
-    for (size_t c0 = 0; c0 < pass_h.size();) {
-      size_t c1 = c0;
-      int64_t pv_chunk = 0;
-      while (c1 < pass_h.size()) {
-        const int32_t p = h_hprob[pass_h[c1]];
-        const int64_t n = b.voff[p + 1] - b.voff[p];
-        if (c1 > c0 && pv_chunk + n > pv_cap) break;
-        pv_chunk += n;
-        ++c1;
-      }
-      const std::vector<int32_t> chunk(pass_h.begin() + (std::ptrdiff_t)c0, pass_h.begin() + (std::ptrdiff_t)c1);
-      c0 = c1;
-      const int32_t NP = (int32_t)chunk.size();
-      std::vector<int32_t> pbase(NP + 1), pprob(NP), pstep(NP), pcoff(NP), pcn(NP), heoff(NP), hen(NP);
-      int64_t PV = 0, ncut = 0;
-      for (int32_t q = 0; q < NP; ++q) {
-        const int32_t h = chunk[q], p = h_hprob[h];
-        pbase[q] = (int32_t)PV;
-        pprob[q] = p;
-        pstep[q] = pass_dom[h];
-        heoff[q] = h_hoff[h];
-        hen[q] = h_hn[h];
-        pcoff[q] = (int32_t)ncut;
-        pcn[q] = 2 * h_hn[h];
-        ncut += 2 * h_hn[h];
-        PV += b.voff[p + 1] - b.voff[p];
-      }
-      pbase[NP] = (int32_t)PV;
-      if (PV >= INT32_MAX / 2) {
-        if (debug_on()) std::fprintf(stderr, "vls: tunnel chunk of %lld pass-vertices\n", (long long)PV);
-        err = cudaErrorMemoryAllocation;
-        goto fail;
-      }
-      // the tunnel state lives after the batch state in the arena
-      const size_t keep = keep_batch; // every chunk's tunnel state starts after the batch state
-      Layout L{&ctx->arena, true};
-      L.bytes = keep;
-      layout_tunnels(L, b, NP, PV, ncut);
-      if (L.bytes > ctx->arena.cap) {
-        // grow: the batch state must survive, so copy it into the new arena
-        char *old = ctx->arena.base;
-        char *nb = nullptr;
-        CK(cudaMalloc(&nb, L.bytes + L.bytes / 8));
-        CK(cudaMemcpyAsync(nb, old, keep, cudaMemcpyDeviceToDevice, st));
-        CK(cudaStreamSynchronize(st));
-        // rebase every pointer of the batch: re-run the layout on the new base
-        ctx->arena.base = nb;
-        ctx->arena.cap = L.bytes + L.bytes / 8;
-        ctx->arena.reset();
-        Layout L2{&ctx->arena, false};
-        layout_batch(L2, b);
-        cudaFree(old);
-      }
-      ctx->arena.used = keep;
-      Layout L3{&ctx->arena, false};
-      layout_tunnels(L3, b, NP, PV, ncut);
-      TDev &T = b.td;
-      T.err = d.err;
-      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.pbase), pbase.data(), sizeof(int32_t) * (NP + 1), cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.pprob), pprob.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.pstep), pstep.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.pcoff), pcoff.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.pcn), pcn.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.heoff), heoff.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(const_cast<int32_t *>(T.hen), hen.data(), sizeof(int32_t) * NP, cudaMemcpyHostToDevice, st));
-      b.h2d += (int64_t)sizeof(int32_t) * (7 * NP + 1);
-      CK(cudaMemsetAsync(T.flag, 0, (size_t)PV, st));
-      if (T.phih) CK(cudaMemsetAsync(T.phih, 0, sizeof(__nv_bfloat16) * PV, st));
-      else if (T.phif) CK(cudaMemsetAsync(T.phif, 0, sizeof(float) * PV, st));
-      else CK(cudaMemsetAsync(T.phi, 0, sizeof(double) * PV, st));
-      CK(cudaMemsetAsync(T.T, 0xff, sizeof(int32_t) * PV, st));
-      CK(cudaMemsetAsync(T.stamp, 0, sizeof(int32_t) * PV, st));
-      CK(cudaMemsetAsync(T.nf, 0, sizeof(int32_t) * 2, st));
-      CK(cudaMemsetAsync(T.qdone, 0, sizeof(int32_t) * NP, st));
-      CK(cudaMemsetAsync(T.qsteps, 0, sizeof(int32_t) * NP, st));
-      CK(cudaMemsetAsync(T.qstatus, 0xff, sizeof(int32_t) * NP, st));
-      k_fill_i32<<<(NP + 255) / 256, 256, 0, st>>>(T.qbstar, NP, 0x7fffffff); VLS_LAUNCH(b);
-      CK(cudaMemsetAsync(T.qcnt, 0, sizeof(int32_t) * 2 * NP, st));
-      CK(cudaMemsetAsync(T.qmass, 0, sizeof(double) * 2 * T.qslots * NP, st));
-      CK(cudaMemsetAsync(T.qmres, 0, sizeof(double) * NP, st));
-      CK(cudaMemsetAsync(T.qupd, 0, sizeof(long long) * NP, st));
-      CK(cudaMemsetAsync(T.ntverts, 0, sizeof(int32_t), st));
-      CK(cudaMemsetAsync(T.tvn, 0, sizeof(int32_t) * NP, st));
-      int32_t chunk_tau = 0;
-      CK(run_tunnels(b, &chunk_tau));
-      tunnel_tau += chunk_tau; // launch accounting: steps summed over chunks
-      std::vector<int32_t> qs(NP), qst(NP), qb(NP), tvo(NP), tvn(NP);
-      std::vector<long long> qupd(NP);
-      std::vector<double> qmres(NP);
-      int32_t ntv = 0;
-      CK(cudaMemcpyAsync(qs.data(), T.qstatus, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(qst.data(), T.qsteps, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(qb.data(), T.qbstar, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(tvo.data(), T.tvoff, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(tvn.data(), T.tvn, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(&ntv, T.ntverts, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(qupd.data(), T.qupd, sizeof(long long) * NP, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(qmres.data(), T.qmres, sizeof(double) * NP, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      b.d2h += (int64_t)(5 * sizeof(int32_t) + sizeof(long long) + sizeof(double)) * NP + (int64_t)sizeof(int32_t);
-      ntv = std::min(ntv, T.tvcap);
-      const size_t tv0 = h_tverts.size();
-      h_tverts.resize(tv0 + (size_t)ntv);
-      if (ntv) CK(cudaMemcpyAsync(h_tverts.data() + tv0, T.tverts, sizeof(int32_t) * ntv, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      b.d2h += (int64_t)sizeof(int32_t) * ntv;
-      for (int32_t q = 0; q < NP; ++q) {
-        const int32_t h = chunk[q];
-        h_tstatus[h] = qs[q];
-        h_tsteps[h] = qst[q];
-        h_tb[h] = qb[q] == 0x7fffffff ? -1 : qb[q];
-        h_tvoff[h] = (int32_t)tv0 + tvo[q];
-        h_tvn[h] = tvn[q];
-        // per-problem pass statistics
-        ProbResult &r = res->p[dev_probs[pprob[q]]];
-        r.stats.pass_updates += qupd[q];
-        r.stats.pass_mass_resid = std::max(r.stats.pass_mass_resid, qmres[q]);
-        r.tunnel_steps = std::max(r.tunnel_steps, qst[q]);
-      }
+    CK(cudaEventRecord(ev[5], st));
+    // Sec. 3.3: one handle-refinement pass per tunnel loop, on the whole surface
+    if (ctx->opt.tunnels && ctx->opt.refine) {
+      std::vector<int32_t> ref_h;
+      for (int32_t h : pass_h)
+        if (tun.status[h] == VLS_OK) ref_h.push_back(h);
+      const std::vector<int32_t> whole(h_nh, INT32_MAX);
+      CK(run_all(PASS_REFINE, ref_h, whole, ref, &refine_tau));
     }
+    for (int32_t h : pass_h) {
+      ProbResult &r = res->p[dev_probs[h_hprob[h]]];
+      r.stats.pass_updates += tun.upd[h];
+      r.stats.pass_uncertified += tun.unc[h];
+      r.stats.pass_mass_resid = std::max(r.stats.pass_mass_resid, tun.mres[h]);
+      r.tunnel_steps = std::max(r.tunnel_steps, tun.steps[h]);
+      if (ref.status[h] != -1) {
+        r.stats.refine_updates += ref.upd[h];
+        r.stats.refine_uncertified += ref.unc[h];
+        r.stats.refine_mass_resid = std::max(r.stats.refine_mass_resid, ref.mres[h]);
+        r.stats.refine_steps = std::max(r.stats.refine_steps, ref.steps[h]);
+      }
     }
     CK(cudaEventRecord(ev[3], st));
     // ---- download
     std::vector<int32_t> nkind, nstep, nprob, nlocal, lstate, lbirth, ldeath, lcount, psteps, pev, hedge, hverts;
     std::vector<double> npos, hpts;
     std::vector<int64_t> pupd;
+    std::vector<unsigned long long> punc;
     std::vector<double> pmres;
     int32_t ne = 0;
     CK(cudaMemcpyAsync(&ne, d.nhedge, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -896,7 +1057,8 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     if (!d2h(nkind, d.nkind, h_nn, st) || !d2h(nstep, d.nstep, h_nn, st) || !d2h(nprob, d.nprob, h_nn, st) ||
         !d2h(nlocal, d.nlocal, h_nn, st) || !d2h(npos, d.npos, 3 * (size_t)h_nn, st) ||
         !d2h(lcount, d.lcount, b.P, st) || !d2h(psteps, d.psteps, b.P, st) || !d2h(pev, d.pev, 3 * (size_t)b.P, st) ||
-        !d2h(pupd, reinterpret_cast<const int64_t *>(d.pupd), b.P, st) || !d2h(pmres, d.pmres, b.P, st) || !d2h(hedge, d.hedge, 2 * (size_t)ne, st) ||
+        !d2h(pupd, reinterpret_cast<const int64_t *>(d.pupd), b.P, st) || !d2h(pmres, d.pmres, b.P, st) ||
+        !d2h(punc, d.punc, b.P, st) || !d2h(hedge, d.hedge, 2 * (size_t)ne, st) ||
         !d2h(hverts, d.hverts, ne, st) || !d2h(hpts, d.hpts, 3 * (size_t)ne, st) ||
         !d2h(lstate, d.lstate, b.Lcap, st) || !d2h(lbirth, d.lbirth, b.Lcap, st) || !d2h(ldeath, d.ldeath, b.Lcap, st)) {
       err = cudaErrorUnknown;
@@ -938,7 +1100,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       }
     }
     if (d.record) {
-      if (!d2h(rec_all, d.rec, (size_t)b.P * d.rcap * 4, st)) { err = cudaErrorUnknown; goto fail; }
+      if (!d2h(rec_all, d.rec, (size_t)b.P * d.rcap * 5, st)) { err = cudaErrorUnknown; goto fail; }
     }
     int32_t h_ctl[CTL_SIZE] = {};
     CK(cudaMemcpyAsync(h_ctl, d.ctl, sizeof(h_ctl), cudaMemcpyDeviceToHost, st));
@@ -955,6 +1117,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       b.launches += 5 * steps;
       b.launches += 4 * (int64_t)h_ctl[CTL_NMERGE] + (int64_t)h_ctl[CTL_NSPLIT];
       if (tunnel_tau > 0) b.launches += 3 * (int64_t)tunnel_tau;
+      if (refine_tau > 0) b.launches += 3 * (int64_t)refine_tau;
     }
 #ifdef VLS_CHECKED
     {
@@ -967,8 +1130,13 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     }
 #endif
     // ---- repack per problem
-    const float ms_op = elapsed(ev[0], ev[1]), ms_init = elapsed(ev[1], ev[2]), ms_tun = elapsed(ev[2], ev[3]),
-                ms_dl = elapsed(ev[3], ev[4]);
+    const float ms_op = elapsed(ev[0], ev[1]), ms_init = elapsed(ev[1], ev[2]), ms_tun = elapsed(ev[2], ev[5]),
+                ms_ref = elapsed(ev[5], ev[3]), ms_dl = elapsed(ev[3], ev[4]);
+    std::vector<double> pmedge;
+    if (!d2h(pmedge, d.pmedge, b.P, st) || cudaStreamSynchronize(st) != cudaSuccess) {
+      err = cudaErrorUnknown;
+      goto fail;
+    }
     double ms_k[KK_COUNT_KINDS] = {};
     int64_t n_k[KK_COUNT_KINDS] = {};
     for (const auto &mk : b.prof.marks) {
@@ -991,6 +1159,8 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       r.stats.ms_operator = ms_op;
       r.stats.ms_initial = ms_init;
       r.stats.ms_tunnel = ms_tun;
+      r.stats.ms_refine = ms_ref;
+      r.stats.mean_edge = pmedge[q];
       r.stats.ms_download = ms_dl;
       r.stats.kernel_launches = b.launches;
       r.stats.ms_update = ms_k[KK_UPDATE];
@@ -1002,6 +1172,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       r.stats.rechecks = (int64_t)h_rechk[0];
       r.stats.pass_rechecks = (int64_t)h_rechk[1];
       r.stats.mass_resid = pmres[q];
+      r.stats.uncertified = (int64_t)punc[q];
       const int32_t nl = lcount[q];
       r.layers.resize(3 * (size_t)nl);
       for (int32_t l = 1; l <= nl; ++l) {
@@ -1019,8 +1190,8 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       }
       if (d.record) {
         const int32_t n = std::min(psteps[q], d.rcap);
-        r.rec.resize(4 * (size_t)n);
-        for (int32_t i = 0; i < 4 * n; ++i) r.rec[i] = rec_all[(size_t)q * d.rcap * 4 + i];
+        r.rec.resize(5 * (size_t)n);
+        for (int32_t i = 0; i < 5 * n; ++i) r.rec[i] = rec_all[(size_t)q * d.rcap * 5 + i];
       }
     }
     // nodes in local order
@@ -1060,31 +1231,35 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
       H.info[2] = h_hnode[h];
       H.len = h_hlen[h];
       r.handles.push_back(std::move(H));
-      {
+      for (int kind = 0; kind < 2; ++kind) {
+        const PassOut &o = kind == 0 ? tun : ref;
         ProbResult::Tunnel T;
-        T.info[0] = h_tstatus[h];
-        T.info[1] = h_tsteps[h];
-        T.info[2] = h_tb[h];
-        if (h_tstatus[h] == VLS_OK)
-          T.verts.assign(h_tverts.begin() + h_tvoff[h], h_tverts.begin() + h_tvoff[h] + h_tvn[h]);
-        r.tunnels.push_back(std::move(T));
+        T.info[0] = o.status[h];
+        T.info[1] = o.steps[h];
+        T.info[2] = o.bstar[h];
+        if (o.status[h] == VLS_OK) T.verts.assign(o.verts.begin() + o.voff[h], o.verts.begin() + o.voff[h] + o.vn[h]);
+        (kind == 0 ? r.tunnels : r.refined).push_back(std::move(T));
       }
+      r.dlen.push_back({h_hdl[h], tun.dl[h], ref.dl[h]});
     }
     for (int32_t q = 0; q < b.P; ++q) {
       ProbResult &r = res->p[dev_probs[q]];
       if (r.status == VLS_OK)
         for (auto &T : r.tunnels)
           if (T.info[0] > 0) { r.status = T.info[0]; break; } // -1: the pass did not run
+      if (r.status == VLS_OK)
+        for (auto &T : r.refined)
+          if (T.info[0] > 0) { r.status = T.info[0]; break; }
     }
   }
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < 6; ++i)
     if (ev[i]) cudaEventDestroy(ev[i]);
   g_d2h_counter = nullptr;
   *out = res;
   return VLS_OK;
 fail:
   g_d2h_counter = nullptr;
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < 6; ++i)
     if (ev[i]) cudaEventDestroy(ev[i]);
   cudaGetLastError();
   for (auto &r : res->p)
@@ -1121,7 +1296,10 @@ extern "C" vls_status vls_result_stats(const vls_result *r, int32_t p, vls_stats
 }
 extern "C" int32_t vls_result_num_loops(const vls_result *r, int32_t p, int32_t kind) {
   if (!r || p < 0 || p >= (int32_t)r->p.size()) return -1;
-  return kind == 0 ? (int32_t)r->p[p].handles.size() : (int32_t)r->p[p].tunnels.size();
+  return kind == 0   ? (int32_t)r->p[p].handles.size()
+         : kind == 1 ? (int32_t)r->p[p].tunnels.size()
+         : kind == 2 ? (int32_t)r->p[p].refined.size()
+                     : -1;
 }
 extern "C" vls_status vls_result_loop(const vls_result *r, int32_t p, int32_t kind, int32_t i, const int32_t **verts,
                                       int64_t *n, const double **pts, int64_t *npts) {
@@ -1135,8 +1313,10 @@ extern "C" vls_status vls_result_loop(const vls_result *r, int32_t p, int32_t ki
     if (npts) *npts = (int64_t)H.pts.size() / 3;
     return VLS_OK;
   }
-  if (i < 0 || i >= (int32_t)P_.tunnels.size()) return VLS_EINVAL;
-  const auto &T = P_.tunnels[i];
+  if (kind != 1 && kind != 2) return VLS_EINVAL;
+  const auto &L = kind == 1 ? P_.tunnels : P_.refined;
+  if (i < 0 || i >= (int32_t)L.size()) return VLS_EINVAL;
+  const auto &T = L[i];
   if (verts) *verts = T.verts.data();
   if (n) *n = (int64_t)T.verts.size();
   if (pts) *pts = nullptr;
@@ -1158,6 +1338,18 @@ extern "C" vls_status vls_result_tunnel(const vls_result *r, int32_t p, int32_t 
   GETP(r, p);
   if (i < 0 || i >= (int32_t)P_.tunnels.size() || !info) return VLS_EINVAL;
   std::memcpy(info, P_.tunnels[i].info, sizeof(int32_t) * 3);
+  return VLS_OK;
+}
+extern "C" vls_status vls_result_refined(const vls_result *r, int32_t p, int32_t i, int32_t info[3]) {
+  GETP(r, p);
+  if (i < 0 || i >= (int32_t)P_.refined.size() || !info) return VLS_EINVAL;
+  std::memcpy(info, P_.refined[i].info, sizeof(int32_t) * 3);
+  return VLS_OK;
+}
+extern "C" vls_status vls_result_offset_change(const vls_result *r, int32_t p, int32_t i, double out[3]) {
+  GETP(r, p);
+  if (i < 0 || i >= (int32_t)P_.dlen.size() || !out) return VLS_EINVAL;
+  for (int k = 0; k < 3; ++k) out[k] = P_.dlen[i][k];
   return VLS_OK;
 }
 extern "C" vls_status vls_result_reeb(const vls_result *r, int32_t p, const int32_t **nodes, const double **pos,
@@ -1183,7 +1375,7 @@ extern "C" vls_status vls_result_state(const vls_result *r, int32_t p, const int
 extern "C" vls_status vls_result_records(const vls_result *r, int32_t p, const int64_t **rec, int32_t *steps) {
   GETP(r, p);
   if (rec) *rec = P_.rec.data();
-  if (steps) *steps = (int32_t)(P_.rec.size() / 4);
+  if (steps) *steps = (int32_t)(P_.rec.size() / 5);
   return VLS_OK;
 }
 extern "C" vls_status vls_result_kernel_times(const vls_result *r, const char *const **names, const int64_t **launches,

@@ -106,13 +106,23 @@ __device__ int32_t new_layer(Dev &d, int32_t p, int32_t birth_local) {
 // ------------------------------------------------------------------ merge groups
 // One thread: the collision rows of a step are few.  `luf` is a union-find parent array over
 // global layer ids (-1 = untouched), reset to -1 for every layer it touched before returning.
-__global__ void k_merge_groups(Dev d, int32_t *luf, int32_t *touched) {
+// The groups of a step are resolved in rounds of at most MAX_TRACES traced layers, in the order
+// of their smallest member (the oracle's order): a round skips the ctl[CTL_MSKIP] groups of the
+// earlier rounds, takes groups while their traces fit, and asks for another round (H.mround)
+// when groups are left.  Groups are disjoint sets of layers, so resolving one does not change
+// another's traces, band or values.
+__global__ void k_merge_groups(Dev d, int32_t *luf, int32_t *touched, Handles H) {
   if (threadIdx.x != 0) return;
   const int32_t t = d.ctl[CTL_T];
   const int32_t nc = *d.ncoll;
+  const int32_t skip = d.ctl[CTL_MSKIP];
   *d.ngroups = 0;
   *d.ntrace = 0;
-  if (nc == 0) return;
+  if (nc == 0) {
+    d.ctl[CTL_MSKIP] = 0;
+    if (H.use) cudaGraphSetConditional(H.mround, 0u);
+    return;
+  }
   int32_t nt = 0;
   for (int32_t c = 0; c < nc; ++c) {
     const int32_t row = d.coll[c];
@@ -138,14 +148,16 @@ __global__ void k_merge_groups(Dev d, int32_t *luf, int32_t *touched) {
     while (j >= 0 && touched[j] > x) { touched[j + 1] = touched[j]; --j; }
     touched[j + 1] = x;
   }
-  int32_t ng = 0, ntr = 0;
+  int32_t ng = 0, ntr = 0, gi = 0;
+  bool more = false;
   for (int32_t i = 0; i < nt; ++i) {
     const int32_t r = touched[i];
     int32_t root = r;
     while (luf[root] != root) root = luf[root];
     if (root != r) continue; // groups are opened at their smallest member (the root)
+    if (gi++ < skip) continue; // resolved by an earlier round of this step
     const int32_t p = d.lprob[r];
-    if (ng >= MAX_TRACES) { atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_ELAYERS); continue; }
+    if (ng >= MAX_TRACES) { more = true; break; }
     int32_t nm = 0;
     for (int32_t j = i; j < nt; ++j) {
       int32_t x = touched[j];
@@ -155,7 +167,8 @@ __global__ void k_merge_groups(Dev d, int32_t *luf, int32_t *touched) {
         ++nm;
       }
     }
-    if (nm > MAX_GROUP || ntr + nm > MAX_TRACES) { atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_ELAYERS); continue; }
+    if (nm > MAX_GROUP) { atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_ELAYERS); continue; }
+    if (ntr + nm > MAX_TRACES) { more = true; break; } // the next round takes this group first
     d.gprob[ng] = p;
     d.gnmem[ng] = nm;
     d.gnode[ng] = new_node(d, p, N_MERGE, t);
@@ -171,6 +184,9 @@ __global__ void k_merge_groups(Dev d, int32_t *luf, int32_t *touched) {
   for (int32_t i = 0; i < nt; ++i) luf[touched[i]] = -1;
   *d.ngroups = ng;
   *d.ntrace = ntr;
+  // groups failed for size (more than MAX_GROUP layers) count as resolved
+  d.ctl[CTL_MSKIP] = more ? gi - 1 : 0;
+  if (H.use) cudaGraphSetConditional(H.mround, more ? 1u : 0u);
 }
 
 // ------------------------------------------------------------------ isoline trace
@@ -499,8 +515,9 @@ __global__ void __launch_bounds__(1024) k_merge_finish(Dev d, Params P) {
 // ranges of the problems that merged this step only.
 __global__ void k_relabel(Dev d) {
   const int32_t ng = *d.ngroups;
-  // collision rows are single-layer again
-  {
+  // collision rows are single-layer again once the last round of the step's merge phase is done
+  // (a later round still reads the rows of its groups)
+  if (d.ctl[CTL_MSKIP] == 0) {
     const int32_t *__restrict__ fv = d.front[d.ctl[CTL_T] & 1];
     const int32_t nc = *d.ncoll;
     for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) d.multi[fv[d.coll[c]]] = -1;
@@ -619,13 +636,17 @@ __global__ void __launch_bounds__(256) k_split(Dev d) {
 
 }  // namespace
 
-// IF(merge) body: groups -> traces (one block each) -> finish -> relabel
-cudaError_t add_merge_nodes(Batch &b, cudaGraph_t g) {
+// IF(merge) body: WHILE(groups left) { groups -> traces (one block each) -> finish -> relabel }
+cudaError_t add_merge_nodes(Batch &b, cudaGraph_t gif) {
   Dev &d = b.d;
   int32_t *luf = d.lcnt + b.Lcap;                  // [Lcap] layer union-find scratch (init -1)
   int32_t *touched = d.lcnt + 2 * (size_t)b.Lcap;  // [Lcap]
-  cudaGraphNode_t n0, n1, n2, n3;
-  cudaError_t e = add_kernel(&n0, g, nullptr, 0, k_merge_groups, dim3(1), dim3(32), d, luf, touched);
+  cudaGraphNode_t w, n0, n1, n2, n3;
+  Handles H{};
+  H.use = 1;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = add_conditional(&w, gif, nullptr, 0, cudaGraphCondTypeWhile, 1u, &H.mround, &g);
+  if (e == cudaSuccess) e = add_kernel(&n0, g, nullptr, 0, k_merge_groups, dim3(1), dim3(32), d, luf, touched, H);
   if (e == cudaSuccess) e = add_kernel(&n1, g, &n0, 1, k_trace, dim3(MAX_TRACES), dim3(1024), d, b.prm);
   if (e == cudaSuccess) e = add_kernel(&n2, g, &n1, 1, k_merge_finish, dim3(MAX_TRACES), dim3(1024), d, b.prm);
   if (e == cudaSuccess) e = add_kernel(&n3, g, &n2, 1, k_relabel, dim3(b.cfg[KK_RELABEL].grid), dim3(b.cfg[KK_RELABEL].threads), d);
@@ -645,18 +666,29 @@ cudaError_t merge_phase_host(Batch &b) {
   cudaStream_t st = b.st;
   int32_t *luf = d.lcnt + b.Lcap;
   int32_t *touched = d.lcnt + 2 * (size_t)b.Lcap;
-  long ps = b.prof.begin(st, KK_MERGE_GROUPS);
-  k_merge_groups<<<1, 32, 0, st>>>(d, luf, touched); VLS_LAUNCH(b);
-  b.prof.end(st, ps);
-  ps = b.prof.begin(st, KK_TRACE);
-  k_trace<<<MAX_TRACES, 1024, 0, st>>>(d, b.prm); VLS_LAUNCH(b);
-  b.prof.end(st, ps);
-  ps = b.prof.begin(st, KK_MERGE_FINISH);
-  k_merge_finish<<<MAX_TRACES, 1024, 0, st>>>(d, b.prm); VLS_LAUNCH(b);
-  b.prof.end(st, ps);
-  ps = b.prof.begin(st, KK_RELABEL);
-  k_relabel<<<b.cfg[KK_RELABEL].grid, b.cfg[KK_RELABEL].threads, 0, st>>>(d); VLS_LAUNCH(b);
-  b.prof.end(st, ps);
+  Handles H{};
+  H.use = 0;
+  for (;;) {
+    long ps = b.prof.begin(st, KK_MERGE_GROUPS);
+    k_merge_groups<<<1, 32, 0, st>>>(d, luf, touched, H); VLS_LAUNCH(b);
+    b.prof.end(st, ps);
+    ps = b.prof.begin(st, KK_TRACE);
+    k_trace<<<MAX_TRACES, 1024, 0, st>>>(d, b.prm); VLS_LAUNCH(b);
+    b.prof.end(st, ps);
+    ps = b.prof.begin(st, KK_MERGE_FINISH);
+    k_merge_finish<<<MAX_TRACES, 1024, 0, st>>>(d, b.prm); VLS_LAUNCH(b);
+    b.prof.end(st, ps);
+    ps = b.prof.begin(st, KK_RELABEL);
+    k_relabel<<<b.cfg[KK_RELABEL].grid, b.cfg[KK_RELABEL].threads, 0, st>>>(d); VLS_LAUNCH(b);
+    b.prof.end(st, ps);
+    // another round while groups of this step are left (rare: more traces than MAX_TRACES)
+    int32_t skip = 0;
+    cudaError_t e = cudaMemcpyAsync(&skip, d.ctl + CTL_MSKIP, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    b.d2h += (int64_t)sizeof(int32_t);
+    if (e != cudaSuccess) return e;
+    if (skip == 0) break;
+  }
   return cudaGetLastError();
 }
 

@@ -31,7 +31,8 @@ __device__ __forceinline__ int32_t append(int32_t *counter) { return atomicAdd(c
 // FP32 form are widened exactly, so the row is the FP64 step from the stored inputs.
 template <int MAXD, class TV>
 __device__ __forceinline__ void row_f64(const Params &P, int nl, const int32_t *ls, int32_t lv, int32_t o, TV xv,
-                                        const int32_t *nlay, const TV *nx, int32_t deg, double *out, double2 &mass) {
+                                        const int32_t *nlay, const TV *nx, int32_t deg, double *out, double2 &mass,
+                                        bool *unc = nullptr) {
   const double Lv = P.lv[deg];
   const double xvd = to_f64(xv);
   const double xb = dsub(1.0, lv != 0 ? xvd : 0.0);
@@ -74,7 +75,7 @@ __device__ __forceinline__ void row_f64(const Params &P, int nl, const int32_t *
   mass = make_double2(0.0, dadd(dmul(P.mv[deg], accb), dmul((double)deg, xb)));
   accb = dadd(accb, dmul(-P.s, xb));
   mass.x = dmul(P.mv[deg], accb) - bnd;
-  if (!vertex_update(P, nl, x, lap, xb, accb, out)) {
+  if (!vertex_update(P, nl, x, lap, xb, accb, out, unc)) {
 #pragma unroll
     for (int q = 0; q < KMAX; ++q)
       if (q < nl) out[q] = x[q];
@@ -86,7 +87,7 @@ __device__ __forceinline__ void row_f64(const Params &P, int nl, const int32_t *
 template <int MAXD, class TN>
 __device__ __forceinline__ bool row_f32(const Params &P, int32_t l, int32_t lv, int32_t o, TN xvs,
                                         const int32_t *nlay, const TN *nx, int32_t deg, double &out,
-                                        double2 &mass) {
+                                        double2 &mass, bool &unc) {
   const float Lv = P.f_lv[deg];
   const float plat = (o != 0 && l == o) ? 1.f : 0.f;
   const float xv = to_f32(xvs);
@@ -116,7 +117,7 @@ __device__ __forceinline__ bool row_f32(const Params &P, int32_t l, int32_t lv, 
   const double bnd = (double)fzb - (double)nfz * (double)xb;
   mass = make_double2(P.mv[deg] * (double)lapb - bnd, P.mv[deg] * (double)accb + (double)deg * (double)xb);
   float y;
-  if (!vertex_update_f32(P, x, lap, xb, lapb, y)) return false;
+  if (!vertex_update_f32(P, x, lap, xb, lapb, y, unc)) return false;
   out = round_keep<TN>((double)y, P.theta); // exact for float storage
   return true;
 }
@@ -126,8 +127,9 @@ __device__ __forceinline__ bool row_f32(const Params &P, int32_t l, int32_t lv, 
 // collision or a decision within the margin.
 template <int MAXD, class TN>
 __device__ __noinline__ void row_redo(const Params &P, int nl, const int32_t *ls, int32_t lv, int32_t o, TN xv,
-                                      const int32_t *nlay, const TN *nx, int32_t deg, double *out, double2 &mass) {
-  row_f64<MAXD, TN>(P, nl, ls, lv, o, xv, nlay, nx, deg, out, mass);
+                                      const int32_t *nlay, const TN *nx, int32_t deg, double *out, double2 &mass,
+                                      bool &unc) {
+  row_f64<MAXD, TN>(P, nl, ls, lv, o, xv, nlay, nx, deg, out, mass, &unc);
   for (int q = 0; q < nl; ++q) out[q] = round_keep<TN>(out[q], P.theta);
 }
 
@@ -136,7 +138,8 @@ __device__ __noinline__ void row_redo(const Params &P, int nl, const int32_t *ls
 // gathered inputs (FAST = true), or all in FP64 and rounded keeping every threshold's side
 // (FAST = false: the out-of-line path of rows longer than the register path).  FP64 form: the
 // FP64 row.
-enum RowOutcome : int { ROW_DONE = 0, ROW_REDONE = 1 };
+// Row outcome bits: redone in FP64, a decision within the drift bound of its threshold (uncertified).
+enum RowOutcome : int { ROW_DONE = 0, ROW_REDONE = 1, ROW_UNCERT = 4 };
 
 template <int MAXD, class TV, bool FAST>
 __device__ __forceinline__ int update_row(const Dev &d, const Params &P, int32_t i, int32_t p, int32_t v, int32_t b,
@@ -190,11 +193,12 @@ __device__ __forceinline__ int update_row(const Dev &d, const Params &P, int32_t
   if (!hb || nl == 0) { d.onl[i] = -1; return ROW_DONE; }
   double out[KMAX];
   int outcome = ROW_DONE;
+  bool unc = false;
   if constexpr (!std::is_same<TV, double>::value && FAST) {
     // FP32 / BF16 forms: one layer in FP32; several layers (a collision: merge arithmetic
     // follows) and rows near a decision are redone in FP64 from copies of the gathered inputs
     // (only the copies live in local memory)
-    if (nl != 1 || !row_f32<MAXD>(P, ls[0], lv, o, xv, nlay, nx, deg, out[0], mass)) {
+    if (nl != 1 || !row_f32<MAXD>(P, ls[0], lv, o, xv, nlay, nx, deg, out[0], mass, unc)) {
       int32_t cl[MAXD], cls[KMAX];
       TV cx[MAXD];
       double co[KMAX];
@@ -202,13 +206,14 @@ __device__ __forceinline__ int update_row(const Dev &d, const Params &P, int32_t
       for (int j = 0; j < MAXD; ++j) { cl[j] = nlay[j]; cx[j] = nx[j]; }
 #pragma unroll
       for (int q = 0; q < KMAX; ++q) cls[q] = ls[q];
-      row_redo<MAXD>(P, nl, cls, lv, o, xv, cl, cx, deg, co, mass);
+      unc = false;
+      row_redo<MAXD>(P, nl, cls, lv, o, xv, cl, cx, deg, co, mass, unc);
 #pragma unroll
       for (int q = 0; q < KMAX; ++q) out[q] = co[q];
       outcome = ROW_REDONE;
     }
   } else if constexpr (!std::is_same<TV, double>::value) {
-    row_f64<MAXD, TV>(P, nl, ls, lv, o, xv, nlay, nx, deg, out, mass);
+    row_f64<MAXD, TV>(P, nl, ls, lv, o, xv, nlay, nx, deg, out, mass, &unc);
 #pragma unroll
     for (int q = 0; q < KMAX; ++q)
       if (q < nl) out[q] = round_keep<TV>(out[q], P.theta);
@@ -225,7 +230,7 @@ __device__ __forceinline__ int update_row(const Dev &d, const Params &P, int32_t
       ++cnt;
     }
   d.onl[i] = cnt;
-  return outcome;
+  return outcome | (unc ? ROW_UNCERT : 0);
 }
 
 // Rows longer than the register path: out of line.
@@ -247,7 +252,7 @@ __device__ __noinline__ int update_row_general(const Dev &d, const Params &P, in
 // operations of the general row for this case, in the same order.
 template <class TV>
 __device__ __forceinline__ double row_one_f64(const Params &P, int32_t l0, int32_t lv, TV xv, const int32_t *nlay,
-                                              const TV *nx, int32_t deg, double2 &mass) {
+                                              const TV *nx, int32_t deg, double2 &mass, bool *unc = nullptr) {
   const double Lv = P.lv[deg];
   const double xvd = to_f64(xv);
   const double xb = dsub(1.0, lv != 0 ? xvd : 0.0);
@@ -270,15 +275,15 @@ __device__ __forceinline__ double row_one_f64(const Params &P, int32_t l0, int32
   accb = dadd(accb, dmul(-P.s, xb));
   mass.x = dmul(P.mv[deg], accb);
   double out;
-  if (!vertex_update(P, 1, &x, &acc, xb, accb, &out)) out = x;
+  if (!vertex_update(P, 1, &x, &acc, xb, accb, &out, unc)) out = x;
   return out;
 }
 // FP32 / BF16 forms: the FP64 redo of a common-case row from its gathered inputs, rounded to the
 // stored type keeping every threshold's side; out of line (rare: a decision within the margin).
 template <class TV>
 __device__ __noinline__ double row_one_redo(const Params &P, int32_t l0, int32_t lv, TV xv, const int32_t *nlay,
-                                            const TV *nx, int32_t deg, double2 &mass) {
-  return round_keep<TV>(row_one_f64<TV>(P, l0, lv, xv, nlay, nx, deg, mass), P.theta);
+                                            const TV *nx, int32_t deg, double2 &mass, bool &unc) {
+  return round_keep<TV>(row_one_f64<TV>(P, l0, lv, xv, nlay, nx, deg, mass, &unc), P.theta);
 }
 
 // The common case, kept short: every non-base entry of the closed neighbourhood belongs to one
@@ -320,16 +325,19 @@ __device__ __forceinline__ int update_row_fast(const Dev &d, const Params &P, in
   if (!hb) { d.onl[i] = -1; return ROW_DONE; }      // no base in the neighbourhood
   double out;
   int outcome = ROW_DONE;
+  bool unc = false;
   if constexpr (std::is_same<TV, double>::value) {
     out = row_one_f64<TV>(P, l0, lv, xv, nlay, nx, deg, mass);
-  } else if (!row_f32<ROW_REG>(P, l0, lv, lv, xv, nlay, nx, deg, out, mass)) {
+  } else if (!row_f32<ROW_REG>(P, l0, lv, lv, xv, nlay, nx, deg, out, mass, unc)) {
     int32_t cl[ROW_REG];
     TV cx[ROW_REG];
 #pragma unroll
     for (int j = 0; j < ROW_REG; ++j) { cl[j] = nlay[j]; cx[j] = nx[j]; }
-    out = row_one_redo<TV>(P, l0, lv, xv, cl, cx, deg, mass);
+    unc = false;
+    out = row_one_redo<TV>(P, l0, lv, xv, cl, cx, deg, mass, unc);
     outcome = ROW_REDONE;
   }
+  if (unc) outcome |= ROW_UNCERT;
   if (out > 0.0) {
     d.olay[(int64_t)i * KMAX] = l0;
     d.ophi[(int64_t)i * KMAX] = out;
@@ -372,11 +380,18 @@ __device__ __forceinline__ void update_rows(const Dev &d, const Params &P) {
     const int32_t i = w * R + lane;
     int32_t p = -1;
     double2 mass = make_double2(0.0, 0.0);
+    bool unc = false;
     if (lane < R && i < nF) {
       p = fp[i];
-      redo += update_one<TV>(d, P, fv, i, p, mass) == ROW_REDONE;
+      const int oc = update_one<TV>(d, P, fv, i, p, mass);
+      redo += (oc & ROW_REDONE) != 0;
+      unc = (oc & ROW_UNCERT) != 0;
     }
     mass_sums(d.pmass, d.mslots, p, lane, mass);
+    if constexpr (!std::is_same<TV, double>::value) {
+      count_keyed(d.punc, p, unc);
+      count_keyed(d.runc, p, unc);
+    }
   }
   if constexpr (!std::is_same<TV, double>::value) {
     redo = __reduce_add_sync(0xffffffffu, redo);
@@ -626,13 +641,15 @@ __device__ __forceinline__ void epilogue_phase(const Dev &d, const Handles &H, i
       d.psteps[p] = t;
       d.pupd[p] += __ldcg(pcount_cur + p);
       if (d.record && t - 1 < d.rcap) {
-        long long *r = d.rec + ((int64_t)p * d.rcap + (t - 1)) * 4;
+        long long *r = d.rec + ((int64_t)p * d.rcap + (t - 1)) * 5;
         const unsigned long long h = __ldcg(d.rhash + p);
         r[0] = __ldcg(pcount_cur + p);
         r[1] = __ldcg(d.rband + p);
         r[2] = (long long)(h & 0xffffffffull);
         r[3] = (long long)(h >> 32);
+        r[4] = __ldcg(d.runc + p);
       }
+      d.runc[p] = 0;
       d.rband[p] = 0;
       d.rhash[p] = 0ull;
       {

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) k_tinit(Dev d, TDev T, int32_t *fv0, int3
   const int32_t nvp = d.voff[p + 1] - voff;
   (void)nvp; // used by the checked build's guards
   for (int32_t i = threadIdx.x; i < L; i += blockDim.x) {
-    const int32_t a = d.hedge[2 * (int64_t)(eo + i)], b = d.hedge[2 * (int64_t)(eo + i) + 1];
+    const int32_t a = T.xedge[2 * (int64_t)(eo + i)], b = T.xedge[2 * (int64_t)(eo + i) + 1];
     if (!VCHK(T.err, a - voff, nvp, 301) || !VCHK(T.err, b - voff, nvp, 302)) continue;
     T.flag[base + (a - voff)] = F_SRC;
     T.flag[base + (b - voff)] = F_TGT;
@@ -162,7 +162,7 @@ __device__ __forceinline__ int gather_kept(const Dev &d, const TDev &T, int32_t 
 // (FP32 values are widened exactly).
 template <int MAXD, class TV>
 __device__ __forceinline__ double trow_f64(const Params &P, uint64_t kp, int dh, int nsrc, const TV *nx, TV xs,
-                                           double2 &mass) {
+                                           double2 &mass, bool *unc = nullptr) {
   const double Lv = dh > 0 ? P.lv[dh] : 0.0;
   const double diag = dh > 0 ? -P.s : 0.0;
   const double x = to_f64(xs);
@@ -182,7 +182,7 @@ __device__ __forceinline__ double trow_f64(const Params &P, uint64_t kp, int dh,
   accb = dadd(accb, dmul(diag, xb));
   mass.x = dmul(P.mv[dh], accb) + (double)nsrc * xb;
   double out;
-  if (!vertex_update(P, 1, &x, &acc, xb, accb, &out)) out = x;
+  if (!vertex_update(P, 1, &x, &acc, xb, accb, &out, unc)) out = x;
   return out;
 }
 
@@ -190,7 +190,7 @@ __device__ __forceinline__ double trow_f64(const Params &P, uint64_t kp, int dh,
 // recheck margin.
 template <int MAXD, class TN>
 __device__ __forceinline__ bool trow_f32(const Params &P, uint64_t kp, int dh, int nsrc, const TN *nx, TN xs,
-                                         double &out, double2 &mass) {
+                                         double &out, double2 &mass, bool &unc) {
   if (dh == 0) return false;
   const float Lv = P.f_lv[dh];
   const float x = to_f32(xs);
@@ -208,7 +208,7 @@ __device__ __forceinline__ bool trow_f32(const Params &P, uint64_t kp, int dh, i
   mass = make_double2(P.mv[dh] * (double)lapb + (double)nsrc * (double)xb,
                       P.mv[dh] * (double)accb + (double)dh * (double)xb);
   float y;
-  if (!vertex_update_f32(P, x, fmaf(-P.f_s, x, acc), xb, lapb, y)) return false;
+  if (!vertex_update_f32(P, x, fmaf(-P.f_s, x, acc), xb, lapb, y, unc)) return false;
   out = round_keep<TN>((double)y, P.theta); // exact for float storage
   return true;
 }
@@ -218,16 +218,17 @@ __device__ __forceinline__ bool trow_f32(const Params &P, uint64_t kp, int dh, i
 // few registers.
 template <int MAXD, class TV>
 __device__ __noinline__ double trow_redo(const Params &P, uint64_t kp, int dh, int nsrc, const TV *nx, TV x,
-                                         double2 &mass) {
-  return round_keep<TV>(trow_f64<MAXD, TV>(P, kp, dh, nsrc, nx, x, mass), P.theta);
+                                         double2 &mass, bool &unc) {
+  return round_keep<TV>(trow_f64<MAXD, TV>(P, kp, dh, nsrc, nx, x, mass, &unc), P.theta);
 }
 
+// Returns bit 0: redone in FP64; bit 2: a decision within the drift bound of its threshold.
 template <int MAXD, class TV>
-__device__ __forceinline__ bool tupdate_row(const Dev &d, const TDev &T, const Params &P, int32_t i, int32_t q,
-                                            int32_t v, double2 &mass) {
+__device__ __forceinline__ int tupdate_row(const Dev &d, const TDev &T, const Params &P, int32_t i, int32_t q,
+                                           int32_t v, double2 &mass) {
   const int32_t p = T.pprob[q], base = T.pbase[q], voff = d.voff[p], step = T.pstep[q];
   const int32_t idx = base + (v - voff);
-  if (!VCHK(T.err, idx, T.PV, 310)) { T.onew[i] = 0.0; return false; }
+  if (!VCHK(T.err, idx, T.PV, 310)) { T.onew[i] = 0.0; return 0; }
   const int8_t fl = T.flag[idx];
   const int32_t b = d.rp[v], deg = d.rp[v + 1] - b;
   uint64_t kp;
@@ -236,25 +237,26 @@ __device__ __forceinline__ bool tupdate_row(const Dev &d, const TDev &T, const P
   const int dh = gather_kept<MAXD, TV>(d, T, q, step, base, voff, fl, v, b, deg, kp, nx, nsrc);
   const TV x = tph_arr<TV>(T)[idx];
   double out;
-  bool redo = false;
+  bool redo = false, unc = false;
   if constexpr (!std::is_same<TV, double>::value) {
-    if (!trow_f32<MAXD>(P, kp, dh, nsrc, nx, x, out, mass)) {
+    if (!trow_f32<MAXD>(P, kp, dh, nsrc, nx, x, out, mass, unc)) {
       TV cx[MAXD];
 #pragma unroll
       for (int j = 0; j < MAXD; ++j) cx[j] = nx[j];
-      out = trow_redo<MAXD, TV>(P, kp, dh, nsrc, cx, x, mass);
+      unc = false;
+      out = trow_redo<MAXD, TV>(P, kp, dh, nsrc, cx, x, mass, unc);
       redo = true;
     }
   } else {
     out = trow_f64<MAXD, TV>(P, kp, dh, nsrc, nx, x, mass);
   }
   T.onew[i] = out;
-  return redo;
+  return (redo ? 1 : 0) | (unc ? 4 : 0);
 }
 
 template <class TV>
-__device__ __noinline__ bool tupdate_row_wide(const Dev &d, const TDev &T, const Params &P, int32_t i, int32_t q,
-                                              int32_t v, double2 &mass) {
+__device__ __noinline__ int tupdate_row_wide(const Dev &d, const TDev &T, const Params &P, int32_t i, int32_t q,
+                                             int32_t v, double2 &mass) {
   return tupdate_row<64, TV>(d, T, P, i, q, v, mass);
 }
 
@@ -270,15 +272,18 @@ __device__ __forceinline__ void tupdate_rows(const Dev &d, const TDev &T, const 
     const int32_t i = w * R + lane;
     int32_t q = -1;
     double2 mass = make_double2(0.0, 0.0);
+    int oc = 0;
     if (lane < R && i < nF) {
       const int32_t v = fv[i];
       q = fq[i];
       const int32_t deg = d.rp[v + 1] - d.rp[v];
-      if (deg <= 12) redo += tupdate_row<12, TV>(d, T, P, i, q, v, mass);
-      else if (deg <= 64) redo += tupdate_row_wide<TV>(d, T, P, i, q, v, mass);
+      if (deg <= 12) oc = tupdate_row<12, TV>(d, T, P, i, q, v, mass);
+      else if (deg <= 64) oc = tupdate_row_wide<TV>(d, T, P, i, q, v, mass);
       else T.onew[i] = tph_ld(T, T.pbase[q] + (v - d.voff[T.pprob[q]]));
+      redo += oc & 1;
     }
     mass_sums(T.qmass, T.qslots, q, lane, mass);
+    if constexpr (!std::is_same<TV, double>::value) count_keyed(T.qunc, q, (oc & 4) != 0);
   }
   if constexpr (!std::is_same<TV, double>::value) {
     redo = __reduce_add_sync(0xffffffffu, redo);
@@ -459,9 +464,9 @@ __global__ void k_ttrace(Dev d, TDev T) {
     int64_t bd = -1, bj = -1;
     int dir = 1;
     for (int32_t i = 0; i < m; ++i) {
-      if (d.hedge[2 * (int64_t)(eo + i) + 1] != bstar) continue;
+      if (T.xedge[2 * (int64_t)(eo + i) + 1] != bstar) continue;
       for (int32_t j = 0; j < m; ++j) {
-        if (d.hedge[2 * (int64_t)(eo + j)] != x) continue;
+        if (T.xedge[2 * (int64_t)(eo + j)] != x) continue;
         const int64_t fwd = ((int64_t)(i - j) % m + m) % m, bwd = ((int64_t)(j - i) % m + m) % m;
         const int64_t dd = fwd <= bwd ? fwd : bwd;
         if (bd < 0 || dd < bd) { bd = dd; bj = j; dir = fwd <= bwd ? 1 : -1; }
@@ -473,7 +478,7 @@ __global__ void k_ttrace(Dev d, TDev T) {
     for (int32_t i = 0; i < np; ++i) T.tverts[off + nc++] = path[i] - voff;
     for (int64_t s = 1; s <= bd; ++s) {
       const int64_t ix = ((bj + dir * s) % m + m) % m;
-      const int32_t a = d.hedge[2 * (int64_t)(eo + ix)] - voff;
+      const int32_t a = T.xedge[2 * (int64_t)(eo + ix)] - voff;
       if (T.tverts[off + nc - 1] != a) T.tverts[off + nc++] = a;
     }
     while (nc > 1 && T.tverts[off + nc - 1] == T.tverts[off]) --nc;

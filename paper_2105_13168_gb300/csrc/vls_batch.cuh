@@ -33,7 +33,10 @@ struct TDev {
   const int32_t *pstep;  // [NP] step of its handle (domain: cover <= step)
   const int32_t *pcoff, *pcn;  // [NP] cut half-edge slots (sorted) offset / count
   const int32_t *cut;          // global CSR slots of the loop's half-edges, both directions
-  const int32_t *heoff, *hen;  // [NP] the handle's crossing edges in the global pool
+  const int32_t *heoff, *hen;  // [NP] the pass's border edges (inside, outside) in the pool xedge
+  const int32_t *xedge;        // [..][2] border-edge pool (global vertex ids): the handle loops' crossing
+                               // edges (tunnel passes) or the tunnel loops' right-side edges (refinement)
+  double *qdl;                 // [NP] length change of the pass's loop under the normal offset (Sec. 3.5)
   int8_t *flag;        // [pass-vertex] bit0 source, bit1 target
   double *phi;         // [pass-vertex] FP64 form
   float *phif;         // [pass-vertex] FP32 form (non-null selects it; phi unused)
@@ -48,6 +51,7 @@ struct TDev {
   double *qmass;       // [NP][qslots][2] mass-check sums of the step (see mass_sums)
   int32_t qslots;
   double *qmres;       // [NP] largest mass-check residual of the pass
+  unsigned long long *qunc; // [NP] uncertified decisions of the pass (see Params::drift)
   long long *qupd;     // [NP]
   int32_t *active;
   // output: tunnel vertex cycles
@@ -119,6 +123,9 @@ struct Batch {
   int hook_variant = 2; // band union-find: 1 one thread per band row, 2 a lane group per row
   long long launches = 0;
   Arena *arena = nullptr;
+  // refinement chunks (Sec. 3.3): the tunnel cycles they start from, per pass offset / length, and
+  // the capacity of each pass's border-edge list
+  int32_t *r_cyc = nullptr, *r_coff = nullptr, *r_clen = nullptr, *r_xcap = nullptr;
   // host copies of problem tables
   std::vector<int32_t> voff, foff, lbase, lcap, seed, mesh_of;
   std::vector<int64_t> nv_local, nf_local;
@@ -199,5 +206,11 @@ cudaError_t merge_phase_host(Batch &b);
 cudaError_t split_phase_host(Batch &b);
 // tunnel.cu
 cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out);
+// refine.cu: vertex normals and mean edge lengths, loop classification, refinement set-up
+cudaError_t launch_vnormals(Batch &b, double *vn, double *elen, double *pmedge);
+cudaError_t launch_classify_handles(Batch &b, const double *vn, const double *pmedge, double *hdl, int32_t nh);
+cudaError_t launch_classify_passes(Batch &b, const double *vn, const double *pmedge);
+cudaError_t launch_refine_prep(Batch &b, int32_t *cyc_pool, const int32_t *coff, const int32_t *clen, int32_t *xedge,
+                               const int32_t *xcap, int32_t *hen, int32_t *pcn);
 
 }  // namespace vls

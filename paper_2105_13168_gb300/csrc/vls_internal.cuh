@@ -28,7 +28,7 @@ namespace vls {
 
 constexpr int KMAX = 4;            // non-base layers that may meet at one vertex in one step
 constexpr int MAX_GROUP = 32;      // layers in one merge group
-constexpr int MAX_TRACES = 64;     // isoline traces per step (all problems)
+constexpr int MAX_TRACES = 64;     // isoline traces per round of the merge phase (all problems)
 constexpr int TRACE_CAP = 1 << 16; // crossing edges per traced isoline
 constexpr int MASS_SLOTS = 16;     // accumulators per problem of the mass check (power of two)
 constexpr int MASS_SPREAD_MAXP = 64; // batches of at most this many problems spread them
@@ -52,7 +52,10 @@ struct Params {
   double mv[LV_MAX + 1];  // d / s: lumped mass of a row with d neighbours (m_v L_vu = 1, symmetric)
   // FP32 form: the same constants rounded to float, and the recheck margin
   double margin;
-  float f_e, f_w, f_ah, f_dt, f_s, f_eps0, f_one_m_eps, f_theta, f_margin;
+  double offset;          // loop classification: normal offset in mean edge lengths (Sec. 3.5)
+  double drift;           // FP32 / BF16 forms: a decision whose FP64 value lies within this of its
+                          // threshold is counted uncertified (0 in the FP64 form)
+  float f_e, f_w, f_ah, f_dt, f_s, f_eps0, f_one_m_eps, f_theta, f_margin, f_drift;
   float f_lv[LV_MAX + 1];
   float f_mun[KMAX + 2];
 };
@@ -84,6 +87,8 @@ struct Dev {
   float *phif;       // FP32 form: layer values (non-null selects the FP32 form; phi unused)
   __nv_bfloat16 *phih; // BF16 form: layer values (non-null selects the BF16 form; phi, phif unused)
   unsigned long long *nrecheck; // [2] rows redone in FP64: initial pass, tunnel passes
+  unsigned long long *punc;     // [P] uncertified decisions of the initial pass (see Params::drift)
+  int32_t *runc;                // [P] the same, this step (step records)
   double *pmass;     // [P][mslots][2] this step's sum over frontier rows of m_v (L base)_v, and of its
                      // terms' magnitudes, spread over mslots addresses per problem
   int32_t rpw;       // frontier rows per warp of the one-thread-per-row kernels (8, 16 or 32)
@@ -138,9 +143,12 @@ struct Dev {
   // records
   int32_t record;
   int32_t rcap;
-  long long *rec;   // [P][rcap][4]
+  long long *rec;   // [P][rcap][5]
   unsigned long long *rhash; // [P]
   int32_t *rband;   // [P]
+  // loop classification (Sec. 3.5): unit vertex normals [V][3], per-vertex sums of the lengths of
+  // the edges to larger ids [V], mean edge length per problem [P], handle-loop length change [hcap]
+  double *vn, *elen, *pmedge, *hdl;
   // error word
   int32_t *err;
   // device control block (see CTL_*), per-problem live layers and layers holding a band root
@@ -165,12 +173,14 @@ enum Ctl : int {
   CTL_NSPLIT = 11,    // split phases executed
   CTL_DONE_FRONT = 12, // last-block counter of the initial-pass frontier kernel
   CTL_DONE_TFRONT = 13, // last-block counter of the tunnel-pass frontier kernel
+  CTL_MSKIP = 14,     // merge groups of this step already resolved by earlier rounds of the phase
   CTL_SIZE = 16
 };
 
 // Conditional handles of the step graph; `use` = 0 when the kernels run from a host loop.
 struct Handles {
   cudaGraphConditionalHandle loop, merge, split;
+  cudaGraphConditionalHandle mround; // rounds of the merge phase (more groups than trace slots)
   int32_t use;
 };
 
@@ -334,9 +344,11 @@ __device__ __forceinline__ void ph_st_round(const Dev &d, const Params &P, int32
 // lapb).  Only pairs (layer, base) have mu_ij, e_ij != 0 (Sec. 2); e is antisymmetric so the
 // rates sum to zero; n = nl + 1 phases meet at the vertex.  Then clamp to [0,1], snap at
 // eps0 / 1 - eps0 and divide by the column sum (Sec. 2, normalisation).  Returns false if
-// the column sum vanished (values left unchanged).
+// the column sum vanished (values left unchanged).  unc (FP32 / BF16 forms): set when a decision of
+// the step -- a clamped value against eps0 or 1 - eps0, a new value against theta -- lies within
+// P.drift of its threshold, closer than the low-precision trajectory can be trusted to be.
 __device__ __forceinline__ bool vertex_update(const Params &P, int nl, const double *x, const double *lap,
-                                              double xb, double lapb, double *out) {
+                                              double xb, double lapb, double *out, bool *unc = nullptr) {
   const double mun = P.mun[nl + 1]; // = mu / n, rounded once on the host (same IEEE quotient)
   double y[KMAX];
   double sr = 0.0;
@@ -358,6 +370,7 @@ __device__ __forceinline__ bool vertex_update(const Params &P, int nl, const dou
       double v = (i < nl) ? y[i] : yb;
       if (v < 0.0) v = 0.0;
       if (v > 1.0) v = 1.0;
+      if (unc) *unc |= fabs(v - P.eps0) < P.drift || fabs(v - P.one_m_eps) < P.drift;
       if (v < P.eps0) v = 0.0;
       if (v > P.one_m_eps) v = 1.0;
       if (i < nl) y[i] = v;
@@ -371,16 +384,20 @@ __device__ __forceinline__ bool vertex_update(const Params &P, int nl, const dou
   if (S == 0.0) return false;
 #pragma unroll
   for (int i = 0; i < KMAX; ++i)
-    if (i < nl) out[i] = ddiv(y[i], S);
+    if (i < nl) {
+      out[i] = ddiv(y[i], S);
+      if (unc) *unc |= fabs(out[i] - P.theta) < P.drift;
+    }
   return true;
 }
 
 // FP32 form of vertex_update for one layer and the base (n = 2), the common case.  Returns
 // false when any decision of the step lies within the recheck margin: a clamped value near
 // eps0 or 1 - eps0 (snap), a new value near theta (isoline, arrival), or a vanishing column
-// sum; the caller then redoes the row in FP64.
+// sum; the caller then redoes the row in FP64.  unc: as in vertex_update, tested here only when the
+// drift bound exceeds the margin (the BF16 form; otherwise a row near a threshold is redone anyway).
 __device__ __forceinline__ bool vertex_update_f32(const Params &P, float x, float lap, float xb, float lapb,
-                                                  float &out) {
+                                                  float &out, bool &unc) {
   const float t1 = P.f_w * (x - xb);
   const float t2 = P.f_ah * (lap - lapb);
   const float t3 = P.f_e * sqrtf(x * xb);
@@ -389,9 +406,12 @@ __device__ __forceinline__ bool vertex_update_f32(const Params &P, float x, floa
   float yb = xb - P.f_dt * r;
   y = fminf(fmaxf(y, 0.f), 1.f);
   yb = fminf(fmaxf(yb, 0.f), 1.f);
-  const float m = P.f_margin;
+  const float m = P.f_margin, dr = P.f_drift;
   bool near = fabsf(y - P.f_eps0) < m || fabsf(y - P.f_one_m_eps) < m || fabsf(yb - P.f_eps0) < m ||
               fabsf(yb - P.f_one_m_eps) < m;
+  const bool wide = dr > m;
+  unc = wide && (fabsf(y - P.f_eps0) < dr || fabsf(y - P.f_one_m_eps) < dr || fabsf(yb - P.f_eps0) < dr ||
+                 fabsf(yb - P.f_one_m_eps) < dr);
   if (y < P.f_eps0) y = 0.f;
   if (y > P.f_one_m_eps) y = 1.f;
   if (yb < P.f_eps0) yb = 0.f;
@@ -400,7 +420,23 @@ __device__ __forceinline__ bool vertex_update_f32(const Params &P, float x, floa
   if (S == 0.f) return false;
   out = y / S;
   near |= fabsf(out - P.f_theta) < m;
+  unc |= wide && fabsf(out - P.f_theta) < dr;
   return !near;
+}
+
+// Count the lanes with `flag` into cnt[key] with one atomic per key present in the warp.  Every
+// lane of the warp calls (key of a lane without flag: anything).
+__device__ __forceinline__ void count_keyed(unsigned long long *cnt, int32_t key, bool flag) {
+  const unsigned fl = __ballot_sync(0xffffffffu, flag);
+  if (!fl) return;
+  const unsigned peers = __match_any_sync(0xffffffffu, flag ? key : -1) & fl;
+  if (flag && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[key], (unsigned long long)__popc(peers));
+}
+__device__ __forceinline__ void count_keyed(int32_t *cnt, int32_t key, bool flag) {
+  const unsigned fl = __ballot_sync(0xffffffffu, flag);
+  if (!fl) return;
+  const unsigned peers = __match_any_sync(0xffffffffu, flag ? key : -1) & fl;
+  if (flag && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[key], (int32_t)__popc(peers));
 }
 
 // ------------------------------------------------------------ union-find

@@ -28,7 +28,10 @@ class vls_options(ctypes.Structure):
                 ("keep_state", ctypes.c_int32), ("record_steps", ctypes.c_int32), ("sync_interval", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("host_loop", ctypes.c_int32),
-                ("hook_variant", ctypes.c_int32), ("rows_per_warp", ctypes.c_int32)]
+                ("hook_variant", ctypes.c_int32), ("rows_per_warp", ctypes.c_int32),
+                ("refine", ctypes.c_int32), ("offset", ctypes.c_double), ("K", ctypes.c_int32),
+                ("laplacian", ctypes.c_int32), ("max_passes", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("drift_bound", ctypes.c_double)]
 
 
 class vls_mesh(ctypes.Structure):
@@ -44,12 +47,17 @@ class vls_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("ms_update", ctypes.c_double), ("ms_pass_update", ctypes.c_double),
                 ("n_update", ctypes.c_int64), ("n_pass_update", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64), ("rechecks", ctypes.c_int64), ("pass_rechecks", ctypes.c_int64),
-                ("mass_resid", ctypes.c_double), ("pass_mass_resid", ctypes.c_double)]
+                ("mass_resid", ctypes.c_double), ("pass_mass_resid", ctypes.c_double),
+                ("refine_updates", ctypes.c_int64), ("refine_steps", ctypes.c_int32), ("ms_refine", ctypes.c_double),
+                ("refine_mass_resid", ctypes.c_double), ("mean_edge", ctypes.c_double),
+                ("uncertified", ctypes.c_int64), ("pass_uncertified", ctypes.c_int64),
+                ("refine_uncertified", ctypes.c_int64)]
 
 
 EXPORTS = ["vls_default_options", "vls_constants", "vls_create", "vls_destroy", "vls_detect", "vls_detect_batch",
            "vls_result_count", "vls_result_status", "vls_result_genus", "vls_result_stats", "vls_result_num_loops",
-           "vls_result_loop", "vls_result_handle", "vls_result_tunnel", "vls_result_reeb", "vls_result_state",
+           "vls_result_loop", "vls_result_handle", "vls_result_tunnel", "vls_result_refined",
+           "vls_result_offset_change", "vls_result_reeb", "vls_result_state",
            "vls_result_records", "vls_result_kernel_times", "vls_result_free", "vls_status_string",
            "vls_tunnel_pass_noalloc"]
 
@@ -94,6 +102,10 @@ def load(path: str = LIB_PATH):
     L.vls_result_handle.restype = i32
     L.vls_result_tunnel.argtypes = [vp, i32, i32, P(i32)]
     L.vls_result_tunnel.restype = i32
+    L.vls_result_refined.argtypes = [vp, i32, i32, P(i32)]
+    L.vls_result_refined.restype = i32
+    L.vls_result_offset_change.argtypes = [vp, i32, i32, P(dbl)]
+    L.vls_result_offset_change.restype = i32
     L.vls_result_reeb.argtypes = [vp, i32, P(P(i32)), P(P(dbl)), P(i32), P(P(i32)), P(i32)]
     L.vls_result_reeb.restype = i32
     L.vls_result_state.argtypes = [vp, i32, P(P(i32)), P(P(dbl)), P(P(i32)), P(i64)]
@@ -237,10 +249,13 @@ class Problem:
     layers: np.ndarray
     handles: list = field(default_factory=list)
     tunnels: list = field(default_factory=list)
+    refined: list = field(default_factory=list)      # refined handle loops (Tunnel-shaped), one per handle
+    offset_change: np.ndarray | None = None          # [h, 3] handle, tunnel, refined (Sec. 3.5)
     layer: np.ndarray | None = None
     phi: np.ndarray | None = None
     cover: np.ndarray | None = None
     records: np.ndarray | None = None
+    step_uncertified: np.ndarray | None = None      # per step: uncertified decisions (FP32 / BF16 forms)
 
     @property
     def status_name(self) -> str:
@@ -304,6 +319,18 @@ def read_result(res) -> list:
             v, nv_ = P(ctypes.c_int32)(), ctypes.c_int64()
             L.vls_result_loop(res, p, 1, i, ctypes.byref(v), ctypes.byref(nv_), None, None)
             pr.tunnels.append(Tunnel(status=info[0], stop_step=info[1], bstar=info[2], verts=_np(v, nv_.value, np.int32)))
+        for i in range(max(0, L.vls_result_num_loops(res, p, 2))):
+            info = (ctypes.c_int32 * 3)()
+            L.vls_result_refined(res, p, i, info)
+            v, nv_ = P(ctypes.c_int32)(), ctypes.c_int64()
+            L.vls_result_loop(res, p, 2, i, ctypes.byref(v), ctypes.byref(nv_), None, None)
+            pr.refined.append(Tunnel(status=info[0], stop_step=info[1], bstar=info[2], verts=_np(v, nv_.value, np.int32)))
+        dl = []
+        for i in range(len(pr.handles)):
+            out3 = (ctypes.c_double * 3)()
+            L.vls_result_offset_change(res, p, i, out3)
+            dl.append(list(out3))
+        pr.offset_change = np.array(dl, dtype=np.float64).reshape(-1, 3)
         la, ph, co, nvv = P(ctypes.c_int32)(), P(ctypes.c_double)(), P(ctypes.c_int32)(), ctypes.c_int64()
         if L.vls_result_state(res, p, ctypes.byref(la), ctypes.byref(ph), ctypes.byref(co), ctypes.byref(nvv)) == 0:
             pr.layer = _np(la, nvv.value, np.int32)
@@ -311,7 +338,9 @@ def read_result(res) -> list:
             pr.cover = _np(co, nvv.value, np.int32)
         rec, nr = P(ctypes.c_int64)(), ctypes.c_int32()
         L.vls_result_records(res, p, ctypes.byref(rec), ctypes.byref(nr))
-        pr.records = _np(rec, 4 * nr.value, np.int64).reshape(-1, 4)
+        rec5 = _np(rec, 5 * nr.value, np.int64).reshape(-1, 5)
+        pr.records = rec5[:, :4].copy()
+        pr.step_uncertified = rec5[:, 4].copy()
         out.append(pr)
     return out
 

@@ -129,7 +129,11 @@ def test_stats_are_consistent(vls):
     g = run_gpu(vls, [(m, [s])])[0]
     o = run_orc(m, s)
     assert g.stats["row_updates"] == o.counters[0]
-    assert g.stats["pass_updates"] == o.counters[2]
+    # the oracle counts the rows of tunnel and refinement passes together
+    assert g.stats["pass_updates"] + g.stats["refine_updates"] == o.counters[2]
+    assert g.stats["refine_updates"] > 0
+    t_only = run_orc(m, s, refine=0)
+    assert g.stats["pass_updates"] == t_only.counters[2]
     assert g.stats["merges"] == o.counters[3] and g.stats["splits"] == o.counters[4]
     assert g.stats["ends"] == o.counters[5] and g.stats["layers"] == o.counters[6]
     assert g.stats["steps"] == o.steps
@@ -208,3 +212,18 @@ def test_mass_check_of_the_diffusion_step(vls, precision, bound):
         assert 0.0 < rp <= bound, rp  # the tunnel passes, sources' flux taken out
     print(precision, "largest mass residual", max(p.stats["mass_resid"] for p in out),
           "tunnel passes", max(p.stats["pass_mass_resid"] for p in out))
+
+
+@pytest.mark.parametrize("host_loop", [0, 1])
+def test_merge_phase_in_rounds(vls, host_loop):
+    """More fronts meet in one step than the merge phase traces at once (64 isolines): 80 copies of
+    the same torus problem merge at the same step (160 isolines), resolved in rounds; every copy
+    gets exactly the oracle's result."""
+    m = meshgen.torus(24, 12)
+    s = meshgen.seed_vertex(1, m.nv)
+    out = run_gpu(vls, [(m, [s] * 80)], host_loop=host_loop)
+    o = run_orc(m, s)
+    assert o.status == 0 and len(o.handles) == 1
+    assert len(out) == 80
+    for g in out:
+        assert_parity(g, o)
