@@ -25,8 +25,10 @@ check_vs_oracle = those sampled problems' GPU results against the oracle's: inte
 
 --impl reference times the CPU oracle itself (the only reference implementation of this
 method available here) with the same metric and JSON layout.
-Multi-GPU (torchrun): every rank runs its own copy of the batch (weak scaling, no
-collective on the data path); value = all ranks' faces / the slowest rank's step time.
+Multi-GPU (torchrun, N ranks): the job is the tube chain with 4 N seed vertices; its problems are
+partitioned over the ranks by greedy LPT on face counts (each rank's share is the single-GPU
+batch's size: weak scaling), with no collective on the data path; value = every problem's faces /
+the slowest rank's step time; per-problem statuses are gathered on rank 0.
 """
 from __future__ import annotations
 
@@ -46,6 +48,7 @@ sys.path.insert(0, ROOT)
 METRIC = "faces/s full loop detection (batched FP32 vs plain FP64 GPU); SpMV HBM GB/s vs peak"
 UNIT = "faces/s"
 L2_FLUSH_BYTES = 256 << 20
+MIDRUN_STEPS = (100, 400, 1000)
 
 
 def parse_args():
@@ -67,7 +70,8 @@ def parse_args():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "bf16"],
                     help="form of the timed batched path (fp32: FP32 values with FP64 near-threshold recheck)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison arm")
-    ap.add_argument("--plain-steps", type=int, default=1, help="timed steps of the plain FP64 arm")
+    ap.add_argument("--plain-steps", type=int, default=5, help="timed steps of the plain FP64 arm")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the batched FP64 arm")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 1024-problem batch workload measured beside the headline")
     return ap.parse_args()
@@ -145,10 +149,105 @@ def max_over_ranks(x: float, dist=None, device=None) -> float:
     return float(t.item())
 
 
-def whole_job_value(faces_per_rank: float, world: int, ms_max: float) -> float:
-    """Whole-job faces/s: every rank detects its own copy of the batch (weak scaling) and the job
-    takes as long as its slowest rank."""
-    return faces_per_rank * world / (ms_max / 1e3)
+def whole_job_value(faces_all_ranks: float, ms_max: float) -> float:
+    """Whole-job faces/s: the faces of every problem of the job, over all ranks, in the time of the
+    slowest rank."""
+    return faces_all_ranks / (ms_max / 1e3)
+
+
+def job_problems(world: int, scale: float):
+    """The job at N GPUs: the tube-chain mesh with 4 N seed vertices (seed streams 0 .. 4N-1), so that
+    every rank's share is the single-GPU batch's size (weak scaling); N = 1 is the 4-seed batch."""
+    import meshgen
+
+    (m, seeds), = meshgen.workload(2, scale)
+    if world > 1:
+        seeds = [meshgen.seed_vertex(s, m.nv) for s in range(4 * world)]
+    return [(m, seeds)]
+
+
+def run_ranks(args, world: int, rank: int, local: int) -> int:
+    """N > 1: the job's problems partitioned over the ranks by greedy LPT on their face counts (no
+    collective on the data path); each rank times its own share; the job takes the slowest rank's
+    time; per-problem statuses are gathered on rank 0, which prints the line."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2105_13168_gb300 as vls
+    from paper_2105_13168_gb300 import partition
+
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    probs = job_problems(world, args.scale)
+    cfg, faces = workload_desc(probs)
+    sub, mine = partition.shard(probs, rank, world)
+    stream = torch.cuda.current_stream()
+    ctx = vls.vls_create(vls.vls_default_options(precision=args.precision), stream.cuda_stream)
+    meshes_dev = [(torch.from_numpy(m.X).to(dev), torch.from_numpy(m.F).to(dev)) for m, _ in sub]
+    pinned = [(torch.from_numpy(m.X).pin_memory(), torch.from_numpy(m.F).pin_memory()) for m, _ in sub]
+    meshes_host = [(x.numpy(), f.numpy()) for x, f in pinned]
+    seeds = [s for _, s in sub]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def one(host=False):
+        if not sub:
+            return []
+        res = vls.vls_detect_batch(ctx, meshes_host if host else meshes_dev, seeds, device=not host)
+        out = vls.read_result(res)
+        vls.vls_result_free(res)
+        return out
+
+    for _ in range(args.warmup):
+        one()
+    sampler = ClockSampler(local) if rank == 0 else None
+    dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    step_ms, launches, out = [], 0, []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = one()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        launches += out[0].stats["kernel_launches"] if out else 0
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    dist.barrier()
+    ms_max = max_over_ranks(sum(step_ms) / len(step_ms), dist, dev)
+    e2e_s, h2d, d2h = [], 0, 0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o2 = one(host=True)
+        e2e_s.append(time.perf_counter() - t0)
+        if o2:
+            h2d, d2h = o2[0].stats["h2d_bytes"], o2[0].stats["d2h_bytes"]
+    e2e_max = max_over_ranks(1e3 * sum(e2e_s) / len(e2e_s), dist, dev)
+    launches_all = max_over_ranks(float(launches), dist, dev)
+    status = partition.gather([p.status for p in out], mine, len(partition.flatten(probs)), dist)
+    if rank == 0:
+        assert all(st == 0 for st in status), status
+        cfg = dict(cfg, precision=args.precision, inputs="resident in HBM (device pointers) for value; pinned host for e2e",
+                   l2="flushed by a 256 MiB write before every timed step",
+                   parallelism=f"{world} GPUs, problems partitioned by greedy LPT on face counts")
+        line = {"metric": METRIC, "value": whole_job_value(faces, ms_max), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[args.precision], "data": "synthetic",
+                "config": cfg, "clocks": clocks,
+                "e2e": {"value": faces / (e2e_max / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": int(launches_all) * world}
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+    return 0
 
 
 def measured_peaks():
@@ -175,6 +274,26 @@ def update_kernel_traffic(rows_per_launch: float, prec: str):
     return float(d["dram_bytes_per_row"]) * rows_per_launch
 
 
+def host_cpu() -> dict:
+    """The host's core count and CPU model (the CPU baseline runs on these cores)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+                if key == "cpu part" and model is None:
+                    model = "cpu part " + ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine(),
+            "arch": platform.machine()}
+
+
 def cpu_baseline(probs, nsample: int) -> dict:
     import oracle
 
@@ -188,11 +307,12 @@ def cpu_baseline(probs, nsample: int) -> dict:
         faces += m.nf
         results.append(r)
     dt = time.perf_counter() - t0
-    # untimed: the same problems stopped at step 400 (front in flight), for the value check
-    midrun = [oracle.detect(m, s, max_steps=400, tunnels=0) for m, s in flat]
-    return {"value": faces / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": round(dt, 2),
-            "sample": f"{len(flat)} of {sum(len(s) for _, s in probs)} problems of the same workload, full detection "
-                      "(initial pass + tunnel passes), single-threaded FP64 oracle"}, results, midrun
+    # untimed: the same problems stopped mid-run (front in flight), for the value check
+    midrun = {k: [oracle.detect(m, s, max_steps=k, tunnels=0) for m, s in flat] for k in MIDRUN_STEPS}
+    return dict({"value": faces / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": round(dt, 2),
+                 "sample": f"{len(flat)} of {sum(len(s) for _, s in probs)} problems of the same workload, full "
+                           "detection (initial pass, tunnel passes, refinement passes), single-threaded FP64 oracle"},
+                **host_cpu()), results, midrun
 
 
 def compare_with_oracle(g, o) -> dict:
@@ -204,17 +324,30 @@ def compare_with_oracle(g, o) -> dict:
 
     same = (g.status == o.status and g.genus == o.genus and g.events() == o.events()
             and np.array_equal(g.layers, o.layers) and len(g.handles) == len(o.handles)
-            and len(g.tunnels) == len(o.tunnels))
+            and len(g.tunnels) == len(o.tunnels) and len(g.refined) == len(o.refined))
     if same:
         for hg, ho in zip(g.handles, o.handles):
             same &= (hg.step, hg.layer) == (ho.step, ho.layer) and np.array_equal(hg.edges, ho.edges) \
                 and np.array_equal(hg.verts, ho.verts)
     tun = sum((tg.status, tg.stop_step, tg.bstar) != (to.status, to.stop_step, to.bstar)
               or not np.array_equal(tg.verts, to.verts) for tg, to in zip(g.tunnels, o.tunnels))
+    ref = sum((tg.status, tg.stop_step, tg.bstar) != (to.status, to.stop_step, to.bstar)
+              or not np.array_equal(tg.verts, to.verts) for tg, to in zip(g.refined, o.refined))
     rec = int((g.records != o.records).any(axis=1).sum()) if len(g.records) == len(o.records) else -1
+    bad = np.nonzero((g.records != o.records).any(axis=1))[0] if rec > 0 else []
+    first = int(bad[0]) if len(bad) else None
+    # loop classification (Sec. 3.5): offset length change > 0 reads as a handle, < 0 as a tunnel
+    dl = np.asarray(g.offset_change)
     return {"identical": bool(same), "record_steps_differing": rec,
+            "first_differing_step": None if first is None else first + 1,
+            "uncertified_at_first_differing_step": None if first is None else int(g.step_uncertified[first]),
+            "uncertified": [int(g.stats["uncertified"]), int(g.stats["pass_uncertified"]),
+                            int(g.stats["refine_uncertified"])],
             "cover_steps_differing": int((g.cover != o.cover).sum()),
-            "final_layers_differing": int((g.layer != o.layer).sum()), "tunnel_loops_differing": int(tun)}
+            "final_layers_differing": int((g.layer != o.layer).sum()), "tunnel_loops_differing": int(tun),
+            "refined_loops_differing": int(ref),
+            "classified_as_handle": [int((dl[:, 0] > 0).sum()), int((dl[:, 2] > 0).sum())] if dl.size else [0, 0],
+            "classified_as_tunnel": int((dl[:, 1] < 0).sum()) if dl.size else 0, "loops": int(len(dl))}
 
 
 def measure_batch_workload(vls, torch, stream, flush, prec: str, steps: int = 2) -> dict:
@@ -340,14 +473,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
     if world > 1:
-        import torch.distributed as dist
-
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+        return run_ranks(args, world, rank, local)
+    dist = None
+    torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
 
     probs = meshgen.workload(2, args.scale)
@@ -401,7 +530,7 @@ def main():
         dist.barrier()
     ms = sum(step_ms) / len(step_ms)
     ms_max = max_over_ranks(ms, dist, dev)
-    value = whole_job_value(faces, world, ms_max)
+    value = whole_job_value(faces, ms_max)
     # ---- e2e: host buffers through the C ABI (pinned), copies inside the call
     pinned = [(torch.from_numpy(m.X).pin_memory(), torch.from_numpy(m.F).pin_memory()) for m, _ in probs]
     meshes_host = [(x.numpy(), f.numpy()) for x, f in pinned]
@@ -414,7 +543,7 @@ def main():
         out = one(device_inputs=False)
         e2e_s.append(time.perf_counter() - t0)
         h2d, d2h = out[0].stats["h2d_bytes"], out[0].stats["d2h_bytes"]
-    e2e_v = faces * world / (sum(e2e_s) / len(e2e_s))
+    e2e_v = faces / (sum(e2e_s) / len(e2e_s))
     vls.vls_destroy(ctx)
     # ---- kernel timing pass: the same workload with CUDA events around every launch of the
     # frontier update kernel (host-driven launches so that each launch can be bracketed)
@@ -434,6 +563,8 @@ def main():
     vls.vls_result_free(res)
     vls.vls_destroy(cctx)
     check = {"problems_checked": len(orc_results),
+             "uncertified_decisions": [[int(p.stats["uncertified"]), int(p.stats["pass_uncertified"]),
+                                        int(p.stats["refine_uncertified"])] for p in cout],
              "mass_check_max_resid": max(p.stats["mass_resid"] for p in cout),
              "rechecks": cout[0].stats["rechecks"],
              "pass_rechecks": cout[0].stats["pass_rechecks"], "row_updates": rows,
@@ -444,19 +575,22 @@ def main():
         for key in ("record_steps_differing", "cover_steps_differing", "final_layers_differing",
                     "tunnel_loops_differing"):
             check[key] = [c[key] for c in cmp]
-        # values mid-run (front in flight; at the end every value is 0 or 1)
-        mctx = vls.vls_create(vls.vls_default_options(precision=prec, keep_state=1, max_steps=400, tunnels=0),
-                              stream.cuda_stream)
+        # values mid-run (front in flight; at the end every value is 0 or 1): the max error against
+        # the FP64 oracle at a few steps
         nchk = len(orc_results)
         flat = [(x, f, s) for (x, f), ss in zip(meshes_dev, seeds) for s in ss][:nchk]
-        errs = []
-        for (x, f, s), om in zip(flat, orc_midrun):
-            r = vls.vls_detect(mctx, x, f, s, device=True)
-            gm = vls.read_result(r)[0]
-            vls.vls_result_free(r)
-            errs.append(float(np.abs(gm.phi - om.phi).max()))
-        vls.vls_destroy(mctx)
-        check["max_abs_err_phi_at_step_400"] = max(errs)
+        check["max_abs_err_phi_vs_oracle"] = {}
+        for k, oms in orc_midrun.items():
+            mctx = vls.vls_create(vls.vls_default_options(precision=prec, keep_state=1, max_steps=k, tunnels=0),
+                                  stream.cuda_stream)
+            errs = []
+            for (x, f, s), om in zip(flat, oms):
+                r = vls.vls_detect(mctx, x, f, s, device=True)
+                gm = vls.read_result(r)[0]
+                vls.vls_result_free(r)
+                errs.append(float(np.abs(gm.phi - om.phi).max()))
+            vls.vls_destroy(mctx)
+            check["max_abs_err_phi_vs_oracle"][f"step_{k}"] = max(errs)
     # ---- plain FP64 arm: the same problems one at a time (no batching), FP64, kernels launched
     # from the host (no graph)
     plain = None
@@ -489,6 +623,30 @@ def main():
         pm = sum(pms) / len(pms)
         plain = {"value": faces / (pm / 1e3), "unit": UNIT, "ms_per_step": pm, "steps": len(pms),
                  "form": "FP64, one problem per call (no batching), step kernels launched from the host (no graph)"}
+    # ---- batched FP64 arm: the headline's batch and graphs in the FP64 form (what the FP32 form
+    # itself buys, with batching and graphs held equal)
+    fp64b = None
+    if not args.no_plain and prec != "fp64":
+        bctx = vls.vls_create(vls.vls_default_options(precision="fp64"), stream.cuda_stream)
+        res = vls.vls_detect_batch(bctx, meshes_dev, seeds, device=True)  # warm-up (and tuning)
+        vls.vls_result_free(res)
+        bms = []
+        for _ in range(max(1, args.fp64_steps)):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = vls.vls_detect_batch(bctx, meshes_dev, seeds, device=True)
+            e1.record(stream)
+            e1.synchronize()
+            bouts = vls.read_result(res)
+            vls.vls_result_free(res)
+            bms.append(e0.elapsed_time(e1))
+            assert all(p.status == 0 for p in bouts)
+        vls.vls_destroy(bctx)
+        bm = sum(bms) / len(bms)
+        fp64b = {"value": faces / (bm / 1e3), "unit": UNIT, "ms_per_step": bm, "steps": len(bms),
+                 "form": "FP64, the same batch in one call per step, step loops as device-driven graphs"}
     batch = None
     if not args.no_batch and rank == 0:
         batch = measure_batch_workload(vls, torch, stream, flush, prec)
@@ -527,6 +685,9 @@ def main():
     if plain is not None:
         line["plain_fp64"] = plain
         line["speedup_vs_plain_fp64"] = value / world / plain["value"]
+    if fp64b is not None:
+        line["batched_fp64"] = fp64b
+        line["speedup_vs_batched_fp64"] = value / world / fp64b["value"]
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

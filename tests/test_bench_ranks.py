@@ -1,6 +1,7 @@
 """Host logic of the multi-GPU benchmark on CPU: world_size-2 gloo ranks (no GPU).  Each rank
 reports its own step time; the job's time is the slowest rank's and the whole-job value counts
-every rank's faces (weak scaling, no collective on the data path)."""
+the faces of every problem of the job (its problems partitioned over the ranks, weak scaling, no
+collective on the data path)."""
 import multiprocessing as mp
 import os
 import socket
@@ -28,7 +29,7 @@ def _rank(rank: int, world: int, port: int, q):
     try:
         ms = 100.0 + 50.0 * rank  # rank 1 is the slow one
         ms_max = bench.max_over_ranks(ms, dist, "cpu")
-        q.put((rank, ms_max, bench.whole_job_value(2_000_000, world, ms_max)))
+        q.put((rank, ms_max, bench.whole_job_value(2_000_000 * world, ms_max)))
     finally:
         dist.destroy_process_group()
 
@@ -56,4 +57,11 @@ def test_single_process_needs_no_group():
     import bench
 
     assert bench.max_over_ranks(12.5) == 12.5
-    assert bench.whole_job_value(1000, 1, 500.0) == pytest.approx(2000.0)
+    assert bench.whole_job_value(1000, 500.0) == pytest.approx(2000.0)
+    # the job at N GPUs: 4 N seeds of the tube chain, so each rank's LPT share is 4 problems
+    from paper_2105_13168_gb300 import partition
+
+    job = bench.job_problems(3, 0.1)
+    assert len(job[0][1]) == 12 and len(set(job[0][1])) == 12
+    assert [len(partition.shard(job, r, 3)[1]) for r in range(3)] == [4, 4, 4]
+    assert bench.job_problems(1, 0.1)[0][1] == job[0][1][:4]
