@@ -285,7 +285,9 @@ def host_cpu() -> dict:
                     model = ln.split(":", 1)[1].strip()
                     break
                 if key == "cpu part" and model is None:
-                    model = "cpu part " + ln.split(":", 1)[1].strip()
+                    part = ln.split(":", 1)[1].strip()
+                    model = {"0xd4f": "Arm Neoverse-V2", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1",
+                             "0xd8e": "Arm Neoverse-N2"}.get(part.lower(), "Arm cpu part " + part)
     except OSError:
         pass
     import platform

@@ -634,6 +634,12 @@ __global__ void __launch_bounds__(256) k_split(Dev d) {
   }
 }
 
+// The round loop of a merge phase is entered with its condition set: a handle's default value is
+// applied when the whole graph is launched, not each time the IF body runs.
+__global__ void k_mround_start(Handles H) {
+  if (threadIdx.x == 0 && H.use) cudaGraphSetConditional(H.mround, 1u);
+}
+
 }  // namespace
 
 // IF(merge) body: WHILE(groups left) { groups -> traces (one block each) -> finish -> relabel }
@@ -641,11 +647,21 @@ cudaError_t add_merge_nodes(Batch &b, cudaGraph_t gif) {
   Dev &d = b.d;
   int32_t *luf = d.lcnt + b.Lcap;                  // [Lcap] layer union-find scratch (init -1)
   int32_t *touched = d.lcnt + 2 * (size_t)b.Lcap;  // [Lcap]
-  cudaGraphNode_t w, n0, n1, n2, n3;
+  cudaGraphNode_t s0, w, n0, n1, n2, n3;
   Handles H{};
   H.use = 1;
   cudaGraph_t g = nullptr;
-  cudaError_t e = add_conditional(&w, gif, nullptr, 0, cudaGraphCondTypeWhile, 1u, &H.mround, &g);
+  cudaError_t e = cudaGraphConditionalHandleCreate(&H.mround, gif, 1u, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = add_kernel(&s0, gif, nullptr, 0, k_mround_start, dim3(1), dim3(32), H);
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = H.mround;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&w, gif, &s0, nullptr, 1, &np);
+    if (e == cudaSuccess) g = np.conditional.phGraph_out[0];
+  }
   if (e == cudaSuccess) e = add_kernel(&n0, g, nullptr, 0, k_merge_groups, dim3(1), dim3(32), d, luf, touched, H);
   if (e == cudaSuccess) e = add_kernel(&n1, g, &n0, 1, k_trace, dim3(MAX_TRACES), dim3(1024), d, b.prm);
   if (e == cudaSuccess) e = add_kernel(&n2, g, &n1, 1, k_merge_finish, dim3(MAX_TRACES), dim3(1024), d, b.prm);

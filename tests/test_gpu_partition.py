@@ -1,6 +1,7 @@
 """The multi-GPU partition on one GPU: a batch split over two ranks by greedy LPT, the two shards run
 in turn, and the gathered per-problem results equal the whole batch's bit for bit (problems are
-independent; their results do not depend on the batch they run in)."""
+independent; their results do not depend on the batch they run in) -- but for the Reeb node
+positions, band means summed in a batch-dependent order, equal to 1e-12."""
 import numpy as np
 import pytest
 
@@ -26,7 +27,9 @@ def vls():
 def same(a, b):
     assert a.status == b.status and a.events() == b.events()
     assert np.array_equal(a.records, b.records) and np.array_equal(a.layers, b.layers)
-    assert np.array_equal(a.node_pos, b.node_pos)
+    # a Reeb node position is a band mean summed in parallel in the order the step's frontier was
+    # built, which depends on the batch: equal up to rounding
+    assert np.allclose(a.node_pos, b.node_pos, rtol=1e-12, atol=1e-12)
     assert np.array_equal(a.phi, b.phi) and np.array_equal(a.layer, b.layer) and np.array_equal(a.cover, b.cover)
     for x, y in zip(a.handles, b.handles):
         assert np.array_equal(x.edges, y.edges) and np.array_equal(x.points, y.points)
