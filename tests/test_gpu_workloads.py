@@ -27,6 +27,17 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 BATCH_SAMPLE = list(range(0, 1024, 64))  # 16 problems spread over the batch
 
 
+# full-size oracle runs: the Schwarz-P workload's initial pass with the first FULL_PASSES tunnel and
+# refinement passes, and the initial pass of a 4-period gyroid at the full gyroid workload's grid
+# density (295 samples per 8 periods)
+FULL_PASSES = 4
+GYROID4_GRID = 148
+
+
+def gyroid4():
+    return meshgen.jitter(meshgen.gyroid(4, GYROID4_GRID), 0.05, 5)
+
+
 def _oracle_problem(args):
     import meshgen as mg
     import oracle as orc
@@ -38,6 +49,12 @@ def _oracle_problem(args):
     elif kind == "schwarz":
         m, ss = mg.workload(3, 0.35)[0]
         s = ss[0]
+    elif kind == "schwarz_full":
+        m, ss = mg.workload(3)[0]
+        return orc.detect(m, ss[0], record_steps=1, max_passes=FULL_PASSES)
+    elif kind == "gyroid4":
+        m = mg.jitter(mg.gyroid(4, GYROID4_GRID), 0.05, 5)
+        return orc.detect(m, mg.seed_vertex(0, m.nv), record_steps=1, tunnels=0)
     else:  # gyroid, 2 periods at the full workload's grid density
         m = mg.jitter(mg.gyroid(2, 76), 0.05, 5)
         s = mg.seed_vertex(0, m.nv)
@@ -46,10 +63,15 @@ def _oracle_problem(args):
 
 @pytest.fixture(scope="module")
 def oracle_results():
+    """Oracle runs in a spawn pool started before the module's first GPU call; the full-size runs
+    (minutes) keep going while the tests that do not need them run."""
+    ex = cf.ProcessPoolExecutor(max_workers=8, mp_context=mp.get_context("spawn"))
+    big = {k: ex.submit(_oracle_problem, (k, 0)) for k in ("schwarz_full", "gyroid4")}
     jobs = [("batch", i) for i in BATCH_SAMPLE] + [("schwarz", 0), ("gyroid", 0)]
-    with cf.ProcessPoolExecutor(max_workers=8, mp_context=mp.get_context("spawn")) as ex:
-        res = list(ex.map(_oracle_problem, jobs))
-    return {"batch": res[:len(BATCH_SAMPLE)], "schwarz": res[-2], "gyroid": res[-1]}
+    res = list(ex.map(_oracle_problem, jobs))
+    out = {"batch": res[:len(BATCH_SAMPLE)], "schwarz": res[-2], "gyroid": res[-1], "_big": big}
+    yield out
+    ex.shutdown(wait=True)
 
 
 @pytest.fixture(scope="module")
@@ -175,3 +197,41 @@ def test_gyroid_oracle_parity(vls, oracle_results):
     assert o.status == 0 and 10 < len(o.handles) <= m.genus()
     assert_parity(run(vls, [(m, [s])], "fp64", keep_state=1, record_steps=1)[0], o)
     assert_fp32_parity(run(vls, [(m, [s])], "fp32", keep_state=1, record_steps=1)[0], o, m.X)
+
+
+def test_schwarz_p_full_size_oracle_parity(vls, oracle_results):
+    """The Schwarz-P workload at full size (5.2M faces), one seed: the initial pass (every step
+    record, event, layer, handle loop, the final state) and the first tunnel and refinement passes
+    bit-exact in the FP64 form; the FP32 form under its certified contract."""
+    o = oracle_results["_big"]["schwarz_full"].result()
+    probs = meshgen.workload(3)
+    m = probs[0][0]
+    assert o.status == 0 and 0 < len(o.handles) <= m.genus()
+    g64 = run(vls, probs, "fp64", keep_state=1, record_steps=1, max_passes=FULL_PASSES)[0]
+    assert_parity(g64, o)
+    g32 = run(vls, probs, "fp32", keep_state=1, record_steps=1, max_passes=FULL_PASSES)[0]
+    err, rec_bad, cov_bad, tun_bad = assert_fp32_parity(g32, o, m.X)
+    print(f"Schwarz-P full size vs oracle: FP64 bit-exact; FP32: {rec_bad} record steps and {cov_bad} cover "
+          f"steps differ, {tun_bad} of {FULL_PASSES} tunnel loops differ, uncertified decisions "
+          f"{g32.stats['uncertified']} / {g32.stats['pass_uncertified']} / {g32.stats['refine_uncertified']}")
+
+
+def test_gyroid_4_periods_bf16_against_oracle(vls, oracle_results):
+    """A 4-period gyroid at the full gyroid workload's density (the largest the oracle runs in
+    minutes), BF16 form: the event kinds and the layer table equal the oracle's, and the first step
+    whose band differs from the oracle's took an uncertified decision; the FP64 form bit-exact."""
+    from parity import first_divergence
+
+    o = oracle_results["_big"]["gyroid4"].result()
+    m = gyroid4()
+    s = meshgen.seed_vertex(0, m.nv)
+    g64 = run(vls, [(m, [s])], "fp64", keep_state=1, record_steps=1, tunnels=0)[0]
+    assert_parity(g64, o)
+    g = run(vls, [(m, [s])], "bf16", keep_state=1, record_steps=1, tunnels=0)[0]
+    assert g.status == o.status == 0
+    assert [k for k, _ in g.events()] == [k for k, _ in o.events()]
+    assert np.array_equal(g.layers, o.layers)
+    i1 = first_divergence(g, o)
+    assert i1 is None or g.step_uncertified[i1] > 0
+    print(f"gyroid 4 periods ({m.nf} faces, genus {m.genus()}): {len(o.handles)} handles; BF16 first divergence "
+          f"at step {None if i1 is None else i1 + 1}, uncertified decisions {g.stats['uncertified']}")
