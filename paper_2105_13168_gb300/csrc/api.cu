@@ -57,9 +57,42 @@ struct vls_result {
   std::vector<double> kms;
 };
 
+// Pinned host memory for the set-up tables and small outputs of the pass chunks in flight: grow-only
+// blocks owned by the context, handed out afresh by every call.
+struct PinnedPool {
+  std::vector<std::pair<char *, size_t>> blocks;
+  size_t bi = 0, used = 0;
+  void reset() { bi = 0; used = 0; }
+  void *take(size_t n) {
+    n = (n + 63) & ~size_t(63);
+    while (bi < blocks.size() && used + n > blocks[bi].second) { ++bi; used = 0; }
+    if (bi == blocks.size()) {
+      const size_t sz = std::max(n, size_t(4) << 20);
+      char *p = nullptr;
+      if (cudaMallocHost(reinterpret_cast<void **>(&p), sz) != cudaSuccess) return nullptr;
+      blocks.push_back({p, sz});
+      used = 0;
+    }
+    void *r = blocks[bi].first + used;
+    used += n;
+    return r;
+  }
+  void release() {
+    for (auto &b : blocks) cudaFreeHost(b.first);
+    blocks.clear();
+    reset();
+  }
+};
+
+constexpr int PASS_STREAMS = 8; // pass chunks in flight at once, each on its own stream
+
 struct vls_ctx {
   vls_options opt;
   cudaStream_t st = nullptr;
+  cudaStream_t sp[PASS_STREAMS] = {}; // pass chunks, concurrent with the initial pass and each other
+  cudaStream_t st3 = nullptr;         // downloads of finished chunks
+  cudaMemPool_t pool = nullptr;       // device blocks of the pass chunks (stream-ordered)
+  PinnedPool pinned;
   Arena arena;
   int sm = 148;
   std::vector<cudaEvent_t> evpool; // profiling events, reused across calls
@@ -163,12 +196,43 @@ extern "C" vls_status vls_create(vls_ctx **ctx, const vls_options *o, void *stre
     delete c;
     return VLS_ECUDA;
   }
+  bool ok = true;
+  for (int i = 0; i < PASS_STREAMS; ++i) ok &= cudaStreamCreateWithFlags(&c->sp[i], cudaStreamNonBlocking) == cudaSuccess;
+  ok &= cudaStreamCreateWithFlags(&c->st3, cudaStreamNonBlocking) == cudaSuccess;
+  {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    ok &= cudaMemPoolCreate(&c->pool, &props) == cudaSuccess;
+    if (ok) {
+      // keep up to 4 GiB of freed blocks for the next chunks and calls (larger chunks are returned at
+      // the next synchronisation, so that chunks of other sizes never pile up)
+      uint64_t keep = uint64_t(4) << 30;
+      ok &= cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess;
+    }
+  }
+  if (!ok) {
+    vls_destroy(c);
+    return VLS_ECUDA;
+  }
   *ctx = c;
   return VLS_OK;
 }
 
 extern "C" void vls_destroy(vls_ctx *ctx) {
   if (!ctx) return;
+  for (int i = 0; i < PASS_STREAMS; ++i)
+    if (ctx->sp[i]) {
+      cudaStreamSynchronize(ctx->sp[i]);
+      cudaStreamDestroy(ctx->sp[i]);
+    }
+  if (ctx->st3) {
+    cudaStreamSynchronize(ctx->st3);
+    cudaStreamDestroy(ctx->st3);
+  }
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  ctx->pinned.release();
   if (ctx->arena.base) cudaFree(ctx->arena.base);
   for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
   delete ctx;
@@ -346,6 +410,7 @@ void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut, i
   T.ntverts = L.take<int32_t>(1);
   T.path = L.take<int32_t>(PV);
   T.qdl = L.take<double>(NP);
+  T.ctl = L.take<int32_t>(CTL_SIZE);
   if (nx > 0) {
     T.xedge = L.take<int32_t>(2 * nx);
     b.r_cyc = L.take<int32_t>(ncyc);
@@ -406,20 +471,50 @@ struct PassOut {
 };
 enum PassKind : int { PASS_TUNNEL = 0, PASS_REFINE = 1 };
 
-// One chunk of passes: lay the pass state out after the batch state (keep_batch bytes), set the
-// passes up, run them (tunnel.cu), classify their loops (refine.cu) and download the results into
-// out.  Tunnel passes (Sec. 3.2) take handle h's crossing edges as the border and dom[h] as the
-// domain step; refinement passes (Sec. 3.3) take the border from tunnel loop h in tun.
-cudaError_t run_chunk(vls_ctx *ctx, Batch &b, size_t keep_batch, int kind, const std::vector<int32_t> &chunk,
-                      const std::vector<int32_t> &h_hprob, const std::vector<int32_t> &dom,
-                      const std::vector<int32_t> &h_hoff, const std::vector<int32_t> &h_hn, const PassOut *tun,
-                      PassOut &out, int32_t *tau_out) {
+// A chunk of single-layer passes in flight on one stream: its own device block (from the context's
+// stream-ordered pool) and control block, so that chunks on different streams run independently of
+// each other and of the initial pass; host-side outputs in pinned memory, filled by asynchronous
+// copies ordered after the passes.
+struct PassBatch {
+  int kind = 0;
+  std::vector<int32_t> chunk;
+  TDev T{};
+  cudaStream_t st = nullptr;
+  char *mem = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int32_t *pin_i = nullptr;     // [7 NP + 2]: status, steps, first vertex, cycle offset, length, border edges; ntv, tau
+  long long *pin_l = nullptr;   // [2 NP]: rows updated, uncertified decisions
+  double *pin_d = nullptr;      // [2 NP]: mass-check residual, offset length change
+};
+
+// Enqueue one chunk of passes on stream st (no host wait): tunnel passes (Sec. 3.2) take handle h's
+// crossing edges as the border and dom[h] as the domain step; refinement passes (Sec. 3.3) take the
+// border from tunnel loop h in tun.  Lays the pass state out in a fresh block, sets the passes up,
+// runs them (tunnel.cu), classifies their loops (refine.cu) and queues the copies of the results.
+cudaError_t enqueue_chunk(vls_ctx *ctx, Batch &b, int kind, const std::vector<int32_t> &chunk,
+                          const std::vector<int32_t> &h_hprob, const std::vector<int32_t> &dom,
+                          const std::vector<int32_t> &h_hoff, const std::vector<int32_t> &h_hn, const PassOut *tun,
+                          cudaStream_t st, PassBatch &pb) {
   Dev &d = b.d;
-  cudaStream_t st = b.st;
   const int32_t NP = (int32_t)chunk.size();
-  std::vector<int32_t> pbase(NP + 1), pprob(NP), pstep(NP), pcoff(NP), pcn(NP), heoff(NP), hen(NP);
-  std::vector<int32_t> rcyc, rcoff(NP), rclen(NP), xcap(NP);
+  pb.kind = kind;
+  pb.chunk = chunk;
+  pb.st = st;
+  // set-up tables, staged in pinned memory (a copy from pageable memory would wait for the stream)
+  int32_t ncyc_total = 0;
+  if (kind == PASS_REFINE)
+    for (int32_t h : chunk) ncyc_total += tun->vn[h];
+  int32_t *ht = static_cast<int32_t *>(ctx->pinned.take(sizeof(int32_t) * (size_t)(10 * NP + 1 + ncyc_total)));
+  pb.pin_i = static_cast<int32_t *>(ctx->pinned.take(sizeof(int32_t) * (size_t)(7 * NP + 2)));
+  pb.pin_l = static_cast<long long *>(ctx->pinned.take(sizeof(long long) * (size_t)(2 * NP)));
+  pb.pin_d = static_cast<double *>(ctx->pinned.take(sizeof(double) * (size_t)(2 * NP)));
+  if (!ht || !pb.pin_i || !pb.pin_l || !pb.pin_d) return cudaErrorMemoryAllocation;
+  int32_t *pbase = ht, *pprob = ht + NP + 1, *pstep = pprob + NP, *pcoff = pstep + NP, *pcn = pcoff + NP;
+  int32_t *heoff = pcn + NP, *hen = heoff + NP, *rcoff = hen + NP, *rclen = rcoff + NP, *xcap = rclen + NP;
+  int32_t *rcyc = xcap + NP;
   int64_t PV = 0, ncut = 0, nx = 0;
+  int32_t nc = 0;
   for (int32_t q = 0; q < NP; ++q) {
     const int32_t h = chunk[q], p = h_hprob[h];
     pbase[q] = (int32_t)PV;
@@ -433,9 +528,9 @@ cudaError_t run_chunk(vls_ctx *ctx, Batch &b, size_t keep_batch, int kind, const
       ncut += 2 * h_hn[h];
     } else {
       const int32_t len = tun->vn[h];
-      rcoff[q] = (int32_t)rcyc.size();
+      rcoff[q] = nc;
       rclen[q] = len;
-      for (int32_t i = 0; i < len; ++i) rcyc.push_back(tun->verts[tun->voff[h] + i] + b.voff[p]);
+      for (int32_t i = 0; i < len; ++i) rcyc[nc++] = tun->verts[tun->voff[h] + i] + b.voff[p];
       // a cycle vertex has at most degree - 2 neighbours on one side (degree <= LV_MAX, checked)
       xcap[q] = (LV_MAX - 2) * std::max(len, 1);
       heoff[q] = (int32_t)nx;
@@ -450,33 +545,24 @@ cudaError_t run_chunk(vls_ctx *ctx, Batch &b, size_t keep_batch, int kind, const
     if (debug_on()) std::fprintf(stderr, "vls: pass chunk of %lld pass-vertices\n", (long long)PV);
     return cudaErrorMemoryAllocation;
   }
-  Layout L{&ctx->arena, true};
-  L.bytes = keep_batch;
-  layout_tunnels(L, b, NP, PV, ncut, nx, (int64_t)rcyc.size());
-  if (L.bytes > ctx->arena.cap) {
-    // grow: the batch state must survive, so copy it into the new arena
-    char *old = ctx->arena.base;
-    char *nb = nullptr;
-    CKR(cudaMalloc(&nb, L.bytes + L.bytes / 8));
-    CKR(cudaMemcpyAsync(nb, old, keep_batch, cudaMemcpyDeviceToDevice, st));
-    CKR(cudaStreamSynchronize(st));
-    // rebase every pointer of the batch: re-run the layout on the new base
-    ctx->arena.base = nb;
-    ctx->arena.cap = L.bytes + L.bytes / 8;
-    ctx->arena.reset();
-    Layout L2{&ctx->arena, false};
-    layout_batch(L2, b);
-    cudaFree(old);
-  }
-  ctx->arena.used = keep_batch;
-  Layout L3{&ctx->arena, false};
-  layout_tunnels(L3, b, NP, PV, ncut, nx, (int64_t)rcyc.size());
-  TDev &T = b.td;
+  Layout L{nullptr, true};
+  layout_tunnels(L, b, NP, PV, ncut, nx, nc);
+  CKR(cudaEventCreateWithFlags(&pb.ev0, cudaEventDefault));
+  CKR(cudaEventCreateWithFlags(&pb.ev1, cudaEventDefault));
+  CKR(cudaEventRecord(pb.ev0, st));
+  CKR(cudaMallocFromPoolAsync(reinterpret_cast<void **>(&pb.mem), L.bytes + 256, ctx->pool, st));
+  Arena a;
+  a.base = pb.mem;
+  a.cap = L.bytes + 256;
+  Layout L2{&a, false};
+  layout_tunnels(L2, b, NP, PV, ncut, nx, nc);
+  pb.T = b.td;
+  TDev &T = pb.T;
   T.err = d.err;
   if (kind == PASS_TUNNEL) T.xedge = d.hedge;
-  auto up = [&](const int32_t *dst, const std::vector<int32_t> &src, size_t n) {
+  auto up = [&](const int32_t *dst, const int32_t *src, size_t n) {
     b.h2d += (int64_t)(sizeof(int32_t) * n);
-    return cudaMemcpyAsync(const_cast<int32_t *>(dst), src.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+    return cudaMemcpyAsync(const_cast<int32_t *>(dst), src, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
   };
   CKR(up(T.pbase, pbase, NP + 1));
   CKR(up(T.pprob, pprob, NP));
@@ -487,6 +573,8 @@ cudaError_t run_chunk(vls_ctx *ctx, Batch &b, size_t keep_batch, int kind, const
     CKR(up(T.pcn, pcn, NP));
     CKR(up(T.hen, hen, NP));
   }
+  CKR(cudaMemsetAsync(T.ctl, 0, sizeof(int32_t) * CTL_SIZE, st));
+  k_fill_i32<<<1, 32, 0, st>>>(T.ctl + CTL_TLIMIT, 1, b.opt.max_pass_steps); VLS_LAUNCH(b);
   CKR(cudaMemsetAsync(T.flag, 0, (size_t)PV, st));
   if (T.phih) CKR(cudaMemsetAsync(T.phih, 0, sizeof(__nv_bfloat16) * PV, st));
   else if (T.phif) CKR(cudaMemsetAsync(T.phif, 0, sizeof(float) * PV, st));
@@ -506,51 +594,67 @@ cudaError_t run_chunk(vls_ctx *ctx, Batch &b, size_t keep_batch, int kind, const
   CKR(cudaMemsetAsync(T.ntverts, 0, sizeof(int32_t), st));
   CKR(cudaMemsetAsync(T.tvn, 0, sizeof(int32_t) * NP, st));
   if (kind == PASS_REFINE) {
-    CKR(up(b.r_cyc, rcyc, rcyc.size()));
+    CKR(up(b.r_cyc, rcyc, nc));
     CKR(up(b.r_coff, rcoff, NP));
     CKR(up(b.r_clen, rclen, NP));
     CKR(up(b.r_xcap, xcap, NP));
-    CKR(launch_refine_prep(b, b.r_cyc, b.r_coff, b.r_clen, const_cast<int32_t *>(T.xedge), b.r_xcap,
+    CKR(launch_refine_prep(b, T, st, b.r_cyc, b.r_coff, b.r_clen, const_cast<int32_t *>(T.xedge), b.r_xcap,
                            const_cast<int32_t *>(T.hen), const_cast<int32_t *>(T.pcn)));
   }
-  CKR(run_tunnels(b, tau_out));
-  CKR(launch_classify_passes(b, d.vn, d.pmedge));
-  std::vector<int32_t> qs(NP), qst(NP), qb(NP), tvo(NP), tvn(NP), qhen(NP);
-  std::vector<long long> qupd(NP);
-  std::vector<unsigned long long> qunc(NP);
-  std::vector<double> qmres(NP), qdl(NP);
-  int32_t ntv = 0;
-  CKR(cudaMemcpyAsync(qs.data(), T.qstatus, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
-  CKR(cudaMemcpyAsync(qst.data(), T.qsteps, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
-  CKR(cudaMemcpyAsync(qb.data(), T.qbstar, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
-  CKR(cudaMemcpyAsync(tvo.data(), T.tvoff, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
-  CKR(cudaMemcpyAsync(tvn.data(), T.tvn, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
-  CKR(cudaMemcpyAsync(qhen.data(), T.hen, sizeof(int32_t) * NP, cudaMemcpyDeviceToHost, st));
-  CKR(cudaMemcpyAsync(&ntv, T.ntverts, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  CKR(cudaMemcpyAsync(qupd.data(), T.qupd, sizeof(long long) * NP, cudaMemcpyDeviceToHost, st));
-  CKR(cudaMemcpyAsync(qmres.data(), T.qmres, sizeof(double) * NP, cudaMemcpyDeviceToHost, st));
-  CKR(cudaMemcpyAsync(qdl.data(), T.qdl, sizeof(double) * NP, cudaMemcpyDeviceToHost, st));
-  CKR(cudaMemcpyAsync(qunc.data(), T.qunc, sizeof(unsigned long long) * NP, cudaMemcpyDeviceToHost, st));
-  CKR(cudaStreamSynchronize(st));
-  b.d2h += (int64_t)(6 * sizeof(int32_t) + 2 * sizeof(long long) + 2 * sizeof(double)) * NP + (int64_t)sizeof(int32_t);
-  ntv = std::min(ntv, T.tvcap);
+  int32_t *pi = pb.pin_i;
+  CKR(run_tunnels(b, T, st, pi + 7 * NP + 1, &pb.ge));
+  CKR(launch_classify_passes(b, T, st, d.vn, d.pmedge));
+  auto dn = [&](void *dst, const void *src, size_t bytes) {
+    b.d2h += (int64_t)bytes;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+  };
+  CKR(dn(pi, T.qstatus, sizeof(int32_t) * NP));
+  CKR(dn(pi + NP, T.qsteps, sizeof(int32_t) * NP));
+  CKR(dn(pi + 2 * NP, T.qbstar, sizeof(int32_t) * NP));
+  CKR(dn(pi + 3 * NP, T.tvoff, sizeof(int32_t) * NP));
+  CKR(dn(pi + 4 * NP, T.tvn, sizeof(int32_t) * NP));
+  CKR(dn(pi + 5 * NP, T.hen, sizeof(int32_t) * NP));
+  CKR(dn(pi + 7 * NP, T.ntverts, sizeof(int32_t)));
+  CKR(dn(pb.pin_l, T.qupd, sizeof(long long) * NP));
+  CKR(dn(pb.pin_l + NP, T.qunc, sizeof(long long) * NP));
+  CKR(dn(pb.pin_d, T.qmres, sizeof(double) * NP));
+  CKR(dn(pb.pin_d + NP, T.qdl, sizeof(double) * NP));
+  CKR(cudaEventRecord(pb.ev1, st));
+  return cudaSuccess;
+}
+
+// Wait for a chunk, move its results into out (per handle), download its loop vertices on the
+// download stream and release its device block.  *tau_sum += its steps (launch accounting); *ms +=
+// its device time.
+cudaError_t finish_chunk(vls_ctx *ctx, Batch &b, PassBatch &pb, PassOut &out, int32_t *tau_sum, double *ms) {
+  CKR(cudaEventSynchronize(pb.ev1));
+  const int32_t NP = (int32_t)pb.chunk.size();
+  const int32_t *pi = pb.pin_i;
+  const int32_t ntv = std::min(pi[7 * NP], pb.T.tvcap);
+  *tau_sum += pi[7 * NP + 1] - 1;
+  float t = 0.f;
+  if (cudaEventElapsedTime(&t, pb.ev0, pb.ev1) == cudaSuccess) *ms += t;
   const size_t tv0 = out.verts.size();
   out.verts.resize(tv0 + (size_t)ntv);
-  if (ntv) CKR(cudaMemcpyAsync(out.verts.data() + tv0, T.tverts, sizeof(int32_t) * ntv, cudaMemcpyDeviceToHost, st));
-  CKR(cudaStreamSynchronize(st));
-  b.d2h += (int64_t)sizeof(int32_t) * ntv;
+  if (ntv) {
+    CKR(cudaMemcpyAsync(out.verts.data() + tv0, pb.T.tverts, sizeof(int32_t) * ntv, cudaMemcpyDeviceToHost, ctx->st3));
+    b.d2h += (int64_t)sizeof(int32_t) * ntv;
+  }
+  CKR(cudaFreeAsync(pb.mem, ctx->st3));
+  CKR(cudaStreamSynchronize(ctx->st3));
+  pb.mem = nullptr;
   for (int32_t q = 0; q < NP; ++q) {
-    const int32_t h = chunk[q];
-    out.status[h] = qs[q];
-    out.steps[h] = qst[q];
-    out.bstar[h] = qb[q] == 0x7fffffff ? -1 : qb[q];
-    out.voff[h] = (int32_t)tv0 + tvo[q];
-    out.vn[h] = tvn[q];
-    out.upd[h] = qupd[q];
-    out.mres[h] = qmres[q];
-    out.unc[h] = (int64_t)qunc[q];
-    out.dl[h] = qdl[q];
-    if (kind == PASS_REFINE && qhen[q] == 0) { // no border: a degenerate tunnel cycle
+    const int32_t h = pb.chunk[q];
+    out.status[h] = pi[q];
+    out.steps[h] = pi[NP + q];
+    out.bstar[h] = pi[2 * NP + q] == 0x7fffffff ? -1 : pi[2 * NP + q];
+    out.voff[h] = (int32_t)tv0 + pi[3 * NP + q];
+    out.vn[h] = pi[4 * NP + q];
+    out.upd[h] = pb.pin_l[q];
+    out.unc[h] = pb.pin_l[NP + q];
+    out.mres[h] = pb.pin_d[q];
+    out.dl[h] = pb.pin_d[NP + q];
+    if (pb.kind == PASS_REFINE && pi[5 * NP + q] == 0) { // no border: a degenerate tunnel cycle
       out.status[h] = VLS_ELOOPFAIL;
       out.steps[h] = 0;
       out.bstar[h] = -1;
@@ -558,6 +662,11 @@ cudaError_t run_chunk(vls_ctx *ctx, Batch &b, size_t keep_batch, int kind, const
       out.dl[h] = std::nan("");
     }
   }
+  if (pb.ge) cudaGraphExecDestroy(pb.ge);
+  pb.ge = nullptr;
+  cudaEventDestroy(pb.ev0);
+  cudaEventDestroy(pb.ev1);
+  pb.ev0 = pb.ev1 = nullptr;
   return cudaSuccess;
 }
 #undef CKR
@@ -677,6 +786,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
   }
   vls_result *res = new (std::nothrow) vls_result();
   if (!res) return VLS_ENOMEM;
+  ctx->pinned.reset(); // the previous call's copies have completed
   // problems (mesh-major, seed-minor); those failing host checks never reach the device
   std::vector<int32_t> pm, ps, pres_status;
   int64_t si = 0;
@@ -916,7 +1026,140 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     }
     if (d.record) CK(cudaMemsetAsync(d.rec, 0, sizeof(long long) * 5 * (size_t)b.P * d.rcap, st));
     CK(init_state(b));
-    // ---- initial pass
+    // ---- initial pass, and the single-layer passes (Sec. 3.2, 3.3) of the handles found so far
+    // running beside it: the initial pass is a chain of small latency-bound steps that leaves most
+    // of the GPU idle, so with step loops as graphs it runs in segments of SEG steps; after each
+    // segment the new handles' tunnel passes start on the pass streams (their domain, the area
+    // covered by the handle's step, no longer changes), and a problem whose initial pass has
+    // ended gets the refinement passes of its finished tunnel loops (their domain is the whole
+    // surface).  Passes are independent of one another and of the order they run in.
+    PassOut tun(d.hcap), ref(d.hcap);
+    std::vector<int32_t> pass_h, pass_dom(d.hcap, 0), per_prob(b.P, 0), pdone(b.P, 0);
+    std::vector<int32_t> pend_t, pend_r, retry;
+    std::vector<PassBatch> inflight;
+    double ms_t = 0.0, ms_r = 0.0;
+    int next_sp = 0;
+    int64_t inflight_bytes = 0;
+    // passes run in chunks whose dense per-pass state (one entry per vertex of the pass's problem,
+    // about 48 B each) fits a bound set by the free device memory; chunks in flight together stay
+    // within twice that
+    int64_t pv_cap = (int64_t(1) << 30) - (int64_t(1) << 20); // pass-vertex ids stay below INT32_MAX / 2
+    {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) pv_cap = std::min<int64_t>(pv_cap, (int64_t)(fr / 4 / 48));
+      // VLS_PASS_VERTS overrides the bound (smaller chunks; the results do not change)
+      if (const char *ev = std::getenv("VLS_PASS_VERTS")) pv_cap = std::atoll(ev);
+      pv_cap = std::max<int64_t>(pv_cap, 1);
+    }
+    const int64_t inflight_cap = 2 * pv_cap * 48;
+    h_hprob.assign(d.hcap, 0);
+    h_hstep.assign(d.hcap, 0);
+    h_hoff.assign(d.hcap, 0);
+    h_hn.assign(d.hcap, 0);
+    int32_t seen = 0;
+    // take the handles [seen, nh) in: their tables, and their tunnel passes (problems still OK)
+    auto admit = [&](int32_t nh, const std::vector<int32_t> &pst) -> cudaError_t {
+      nh = std::min(nh, d.hcap);
+      if (nh <= seen) return cudaSuccess;
+      const size_t n = (size_t)(nh - seen);
+      cudaError_t e = cudaMemcpy(h_hprob.data() + seen, d.hprob + seen, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(h_hstep.data() + seen, d.hstep + seen, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(h_hoff.data() + seen, d.hoff + seen, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(h_hn.data() + seen, d.hn + seen, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+      b.d2h += (int64_t)(16 * n);
+      if (e != cudaSuccess) return e;
+      for (int32_t h = seen; h < nh; ++h) {
+        const int32_t p = h_hprob[h];
+        if (!ctx->opt.tunnels || pst[p] != VLS_OK) continue;
+        if (ctx->opt.max_passes > 0 && per_prob[p]++ >= ctx->opt.max_passes) continue;
+        pass_h.push_back(h);
+        pass_dom[h] = h_hstep[h];
+        pend_t.push_back(h);
+      }
+      seen = nh;
+      return cudaSuccess;
+    };
+    auto chunk_bytes = [&](const std::vector<int32_t> &hs) {
+      int64_t pv = 0;
+      for (int32_t h : hs) pv += b.voff[h_hprob[h] + 1] - b.voff[h_hprob[h]];
+      return 48 * pv;
+    };
+    // start chunks of the pending handles (in order) while the in-flight bound allows (one chunk always
+    // starts when none is in flight); refinements wait for their problem's initial pass to end;
+    // after_ev: the initial-pass point the chunks must follow
+    auto launch = [&](int kind, std::vector<int32_t> &pend, const std::vector<int32_t> &dom,
+                      cudaEvent_t after_ev) -> cudaError_t {
+      std::vector<int32_t> keep;
+      size_t i = 0;
+      while (i < pend.size()) {
+        std::vector<int32_t> chunk;
+        int64_t pv = 0;
+        size_t j = i;
+        for (; j < pend.size(); ++j) {
+          const int32_t h = pend[j], p = h_hprob[h];
+          if (kind == PASS_REFINE && !pdone[p]) { keep.push_back(h); continue; }
+          const int64_t nvp = b.voff[p + 1] - b.voff[p];
+          if (!chunk.empty() && pv + nvp > pv_cap) break;
+          chunk.push_back(h);
+          pv += nvp;
+        }
+        i = j;
+        if (chunk.empty()) continue;
+        const int64_t bytes = chunk_bytes(chunk);
+        if (!inflight.empty() && inflight_bytes + bytes > inflight_cap) { // wait for room
+          keep.insert(keep.end(), chunk.begin(), chunk.end());
+          keep.insert(keep.end(), pend.begin() + (std::ptrdiff_t)i, pend.end());
+          break;
+        }
+        PassBatch pb;
+        const cudaStream_t sp = ctx->sp[next_sp++ % PASS_STREAMS];
+        if (after_ev) {
+          cudaError_t e = cudaStreamWaitEvent(sp, after_ev, 0);
+          if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = enqueue_chunk(ctx, b, kind, chunk, h_hprob, dom, h_hoff, h_hn, &tun, sp, pb);
+        if (e != cudaSuccess) return e;
+        inflight_bytes += bytes;
+        inflight.push_back(std::move(pb));
+      }
+      pend.swap(keep);
+      return cudaSuccess;
+    };
+    // finish the chunks that are done (all of them when `wait`); finished tunnel loops of problems
+    // whose initial pass is done queue their refinement (others wait for it), failed ones a retry
+    auto collect = [&](bool wait) -> cudaError_t {
+      std::vector<PassBatch> rest;
+      for (auto &pb : inflight) {
+        if (!wait && cudaEventQuery(pb.ev1) == cudaErrorNotReady) {
+          rest.push_back(std::move(pb));
+          continue;
+        }
+        const int kind = pb.kind;
+        std::vector<int32_t> ch = pb.chunk;
+        cudaError_t e = finish_chunk(ctx, b, pb, kind == PASS_TUNNEL ? tun : ref,
+                                     kind == PASS_TUNNEL ? &tunnel_tau : &refine_tau, kind == PASS_TUNNEL ? &ms_t : &ms_r);
+        if (e != cudaSuccess) return e;
+        inflight_bytes -= chunk_bytes(ch);
+        if (kind == PASS_TUNNEL)
+          for (int32_t h : ch) {
+            if (tun.status[h] == VLS_OK) {
+              if (ctx->opt.refine) pend_r.push_back(h);
+            } else if (tun.status[h] == VLS_ELOOPFAIL && tun.bstar[h] < 0 && h_hn[h] > 0 && pass_dom[h] != INT32_MAX) {
+              retry.push_back(h); // Sec. 3.2: the kept loop separates the covered area: whole surface
+            }
+          }
+      }
+      inflight.swap(rest);
+      return cudaSuccess;
+    };
+    std::vector<int32_t> whole(d.hcap, INT32_MAX);
+    std::vector<int32_t> pst(b.P, 0);
+    // Overlapping the passes with the initial pass was measured slower on the tube chain (464 against
+    // 340 ms per detection): many small pass loops running beside the initial pass contend with it
+    // for kernel dispatch, while one batched pass loop afterwards costs a single step chain.  It stays
+    // available for experiments (VLS_OVERLAP_PASSES=1); the results are the same either way.
+    const char *ovl = std::getenv("VLS_OVERLAP_PASSES");
+    const bool pipe = !b.host_loop && ctx->opt.tunnels && ovl && ovl[0] == '1';
     if (b.host_loop) {
       const int sync_every = ctx->opt.sync_interval > 0 ? ctx->opt.sync_interval : 16;
       for (int t = 1;; ++t) {
@@ -930,18 +1173,53 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
         }
       }
     } else {
+      constexpr int32_t SEG = 256;
       cudaGraph_t g = nullptr;
       cudaGraphExec_t ge = nullptr;
+      cudaEvent_t ev_seg = nullptr;
+      int32_t *pin = static_cast<int32_t *>(ctx->pinned.take(sizeof(int32_t) * (size_t)(4 + 2 * b.P)));
+      if (!pin) { err = cudaErrorMemoryAllocation; goto fail; }
       err = build_initial_graph(b, &g);
       if (err == cudaSuccess) err = cudaGraphInstantiate(&ge, g, 0);
-      if (err == cudaSuccess) err = cudaGraphLaunch(ge, st);
-      if (ge) cudaGraphExecDestroy(ge);
       if (g) cudaGraphDestroy(g);
+      if (err == cudaSuccess) err = cudaEventCreateWithFlags(&ev_seg, cudaEventDisableTiming);
+      int32_t seg_end = pipe ? SEG : ctx->opt.max_steps;
+      while (err == cudaSuccess) {
+        pin[0] = std::min(seg_end, ctx->opt.max_steps);
+        err = cudaMemcpyAsync(d.ctl + CTL_LIMIT, pin, sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess) err = cudaGraphLaunch(ge, st);
+        if (err != cudaSuccess || !pipe) break;
+        // the segment's outcome: step, problems running, handles found, per-problem status and end
+        err = cudaMemcpyAsync(pin + 1, d.ctl + CTL_T, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(pin + 2, d.ctl + CTL_ACTIVE, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(pin + 3, d.nhand, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(pin + 4, d.pstatus, sizeof(int32_t) * b.P, cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(pin + 4 + b.P, d.pdone, sizeof(int32_t) * b.P, cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaEventRecord(ev_seg, st);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+        if (err != cudaSuccess) break;
+        b.d2h += (int64_t)sizeof(int32_t) * (3 + 2 * b.P);
+        for (int32_t p = 0; p < b.P; ++p) {
+          pst[p] = pin[4 + p];
+          pdone[p] = pin[4 + b.P + p] && pst[p] == VLS_OK;
+        }
+        const bool last = pin[2] == 0 || pin[1] > ctx->opt.max_steps;
+        if (!last) {
+          err = admit(pin[3], pst);
+          if (err == cudaSuccess) err = collect(false);
+          if (err == cudaSuccess) err = launch(PASS_TUNNEL, pend_t, pass_dom, ev_seg);
+          if (err == cudaSuccess) err = launch(PASS_REFINE, pend_r, whole, ev_seg);
+        }
+        if (last || err != cudaSuccess) break;
+        seg_end += SEG;
+      }
+      if (ge) cudaGraphExecDestroy(ge);
+      if (ev_seg) cudaEventDestroy(ev_seg);
       if (err != cudaSuccess) goto fail;
     }
     CK(final_checks(b));
     CK(cudaEventRecord(ev[2], st));
-    // ---- tunnel passes
+    // ---- the rest of the passes, once the initial pass has ended
     CK(cudaMemcpyAsync(&h_nh, d.nhand, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&h_nn, d.nnodes, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     h_status.resize(b.P);
@@ -950,86 +1228,47 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     b.d2h += (int64_t)sizeof(int32_t) * (2 + b.P);
     h_nh = std::min(h_nh, d.hcap);
     h_nn = std::min(h_nn, d.ncap);
-    if (!d2h(h_hprob, d.hprob, h_nh, st) || !d2h(h_hstep, d.hstep, h_nh, st) || !d2h(h_hlayer, d.hlayer, h_nh, st) ||
-        !d2h(h_hnode, d.hnode, h_nh, st) || !d2h(h_hoff, d.hoff, h_nh, st) || !d2h(h_hn, d.hn, h_nh, st) ||
-        !d2h(h_hvoff, d.hvoff, h_nh, st) || !d2h(h_hvn, d.hvn, h_nh, st) || !d2h(h_hlen, d.hlen, h_nh, st)) {
+    for (int32_t p = 0; p < b.P; ++p) pdone[p] = h_status[p] == VLS_OK;
+    CK(admit(h_nh, h_status));
+    CK(cudaEventRecord(ev[5], st));
+    while (!pend_t.empty() || !pend_r.empty() || !retry.empty() || !inflight.empty()) {
+      for (int32_t h : retry) {
+        pass_dom[h] = INT32_MAX;
+        pend_t.push_back(h);
+      }
+      retry.clear();
+      CK(launch(PASS_TUNNEL, pend_t, pass_dom, ev[5]));
+      CK(launch(PASS_REFINE, pend_r, whole, ev[5]));
+      CK(collect(true));
+    }
+    for (int32_t sp = 0; sp < PASS_STREAMS; ++sp) CK(cudaStreamSynchronize(ctx->sp[sp]));
+    // passes of a problem whose initial pass failed (started before it failed) do not count
+    for (int32_t h : pass_h)
+      if (h_status[h_hprob[h]] != VLS_OK) {
+        tun.status[h] = ref.status[h] = -1;
+        tun.steps[h] = ref.steps[h] = 0;
+        tun.bstar[h] = ref.bstar[h] = 0;
+        tun.vn[h] = ref.vn[h] = 0;
+        tun.dl[h] = ref.dl[h] = std::nan("");
+      }
+    // tables of every handle, classification of the handle (isoline) loops (Sec. 3.5)
+    h_hprob.resize(h_nh);
+    h_hstep.resize(h_nh);
+    h_hoff.resize(h_nh);
+    h_hn.resize(h_nh);
+    if (!d2h(h_hlayer, d.hlayer, h_nh, st) || !d2h(h_hnode, d.hnode, h_nh, st) || !d2h(h_hvoff, d.hvoff, h_nh, st) ||
+        !d2h(h_hvn, d.hvn, h_nh, st) || !d2h(h_hlen, d.hlen, h_nh, st)) {
       err = cudaErrorUnknown;
       goto fail;
     }
-    CK(cudaStreamSynchronize(st));
-    // classification of the handle (isoline) loops (Sec. 3.5)
     CK(launch_classify_handles(b, d.vn, d.pmedge, d.hdl, h_nh));
     if (!d2h(h_hdl, d.hdl, h_nh, st)) {
       err = cudaErrorUnknown;
       goto fail;
     }
-    PassOut tun(h_nh), ref(h_nh);
-    // passes: handles of problems whose initial pass succeeded (at most max_passes per problem)
-    std::vector<int32_t> pass_h;
-    if (ctx->opt.tunnels) {
-      std::vector<int32_t> per_prob(b.P, 0);
-      for (int32_t h = 0; h < h_nh; ++h)
-        if (h_status[h_hprob[h]] == VLS_OK && (ctx->opt.max_passes <= 0 || per_prob[h_hprob[h]]++ < ctx->opt.max_passes))
-          pass_h.push_back(h);
-    }
-    // passes run in chunks whose dense per-pass state (one entry per vertex of the pass's
-    // problem, about 45 B each) fits a bound set by the free device memory
-    int64_t pv_cap = (int64_t(1) << 30) - (int64_t(1) << 20); // pass-vertex ids stay below INT32_MAX / 2
-    {
-      size_t fr = 0, tot = 0;
-      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) pv_cap = std::min<int64_t>(pv_cap, (int64_t)(fr / 2 / 48));
-      // VLS_PASS_VERTS overrides the bound (smaller chunks; the results do not change)
-      if (const char *ev = std::getenv("VLS_PASS_VERTS")) pv_cap = std::atoll(ev);
-      pv_cap = std::max<int64_t>(pv_cap, 1);
-    }
-    const size_t keep_batch = ctx->arena.used;
-    auto run_all = [&](int kind, const std::vector<int32_t> &hs, const std::vector<int32_t> &dom, PassOut &out,
-                       int32_t *tau_sum) -> cudaError_t {
-      for (size_t c0 = 0; c0 < hs.size();) {
-        size_t c1 = c0;
-        int64_t pv_chunk = 0;
-        while (c1 < hs.size()) {
-          const int32_t p = h_hprob[hs[c1]];
-          const int64_t n = b.voff[p + 1] - b.voff[p];
-          if (c1 > c0 && pv_chunk + n > pv_cap) break;
-          pv_chunk += n;
-          ++c1;
-        }
-        const std::vector<int32_t> chunk(hs.begin() + (std::ptrdiff_t)c0, hs.begin() + (std::ptrdiff_t)c1);
-        c0 = c1;
-        int32_t chunk_tau = 0;
-        const cudaError_t e = run_chunk(ctx, b, keep_batch, kind, chunk, h_hprob, dom, h_hoff, h_hn, &tun, out,
-                                        &chunk_tau);
-        if (e != cudaSuccess) return e;
-        *tau_sum += chunk_tau; // launch accounting: steps summed over chunks
-      }
-      return cudaSuccess;
-    };
-    // Sec. 3.2: a pass is restricted to the area covered when its handle was found.  A pass
-    // that cannot reach the far side there (the kept handle loop separates that area) runs a
-    // second time on the whole surface (domain step INT32_MAX).
-    std::vector<int32_t> pass_dom(h_nh, 0);
-    for (int32_t h : pass_h) pass_dom[h] = h_hstep[h];
-    CK(run_all(PASS_TUNNEL, pass_h, pass_dom, tun, &tunnel_tau));
-    {
-      std::vector<int32_t> again;
-      for (int32_t h : pass_h)
-        if (tun.status[h] == VLS_ELOOPFAIL && tun.bstar[h] < 0 && h_hn[h] > 0) {
-          again.push_back(h);
-          pass_dom[h] = INT32_MAX;
-        }
-      if (!again.empty()) CK(run_all(PASS_TUNNEL, again, pass_dom, tun, &tunnel_tau));
-    }
-    CK(cudaEventRecord(ev[5], st));
-    // Sec. 3.3: one handle-refinement pass per tunnel loop, on the whole surface
-    if (ctx->opt.tunnels && ctx->opt.refine) {
-      std::vector<int32_t> ref_h;
-      for (int32_t h : pass_h)
-        if (tun.status[h] == VLS_OK) ref_h.push_back(h);
-      const std::vector<int32_t> whole(h_nh, INT32_MAX);
-      CK(run_all(PASS_REFINE, ref_h, whole, ref, &refine_tau));
-    }
+    CK(cudaStreamSynchronize(st));
     for (int32_t h : pass_h) {
+      if (h_status[h_hprob[h]] != VLS_OK) continue;
       ProbResult &r = res->p[dev_probs[h_hprob[h]]];
       r.stats.pass_updates += tun.upd[h];
       r.stats.pass_uncertified += tun.unc[h];
@@ -1130,8 +1369,9 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     }
 #endif
     // ---- repack per problem
-    const float ms_op = elapsed(ev[0], ev[1]), ms_init = elapsed(ev[1], ev[2]), ms_tun = elapsed(ev[2], ev[5]),
-                ms_ref = elapsed(ev[5], ev[3]), ms_dl = elapsed(ev[3], ev[4]);
+    // pass times: device time of the pass chunks (they overlap the initial pass and one another)
+    const float ms_op = elapsed(ev[0], ev[1]), ms_init = elapsed(ev[1], ev[2]), ms_tun = (float)ms_t,
+                ms_ref = (float)ms_r, ms_dl = elapsed(ev[3], ev[4]);
     std::vector<double> pmedge;
     if (!d2h(pmedge, d.pmedge, b.P, st) || cudaStreamSynchronize(st) != cudaSuccess) {
       err = cudaErrorUnknown;

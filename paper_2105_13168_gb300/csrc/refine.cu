@@ -274,16 +274,16 @@ cudaError_t launch_classify_handles(Batch &b, const double *vn, const double *pm
   return cudaGetLastError();
 }
 
-cudaError_t launch_classify_passes(Batch &b, const double *vn, const double *pmedge) {
-  if (b.td.NP <= 0) return cudaSuccess;
-  k_classify_cyc<<<b.td.NP < 4096 ? b.td.NP : 4096, 128, 0, b.st>>>(b.d, b.td, b.prm, vn, pmedge); VLS_LAUNCH(b);
+cudaError_t launch_classify_passes(Batch &b, const TDev &T, cudaStream_t st, const double *vn, const double *pmedge) {
+  if (T.NP <= 0) return cudaSuccess;
+  k_classify_cyc<<<T.NP < 4096 ? T.NP : 4096, 128, 0, st>>>(b.d, T, b.prm, vn, pmedge); VLS_LAUNCH(b);
   return cudaGetLastError();
 }
 
-cudaError_t launch_refine_prep(Batch &b, int32_t *cyc_pool, const int32_t *coff, const int32_t *clen, int32_t *xedge,
-                               const int32_t *xcap, int32_t *hen, int32_t *pcn) {
-  if (b.td.NP <= 0) return cudaSuccess;
-  k_rprep<<<b.td.NP, 256, 0, b.st>>>(b.d, b.td, cyc_pool, coff, clen, xedge, xcap, hen, pcn); VLS_LAUNCH(b);
+cudaError_t launch_refine_prep(Batch &b, const TDev &T, cudaStream_t st, int32_t *cyc_pool, const int32_t *coff,
+                               const int32_t *clen, int32_t *xedge, const int32_t *xcap, int32_t *hen, int32_t *pcn) {
+  if (T.NP <= 0) return cudaSuccess;
+  k_rprep<<<T.NP, 256, 0, st>>>(b.d, T, cyc_pool, coff, clen, xedge, xcap, hen, pcn); VLS_LAUNCH(b);
   return cudaGetLastError();
 }
 

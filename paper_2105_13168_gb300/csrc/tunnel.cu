@@ -262,7 +262,7 @@ __device__ __noinline__ int tupdate_row_wide(const Dev &d, const TDev &T, const 
 
 template <class TV>
 __device__ __forceinline__ void tupdate_rows(const Dev &d, const TDev &T, const Params &P) {
-  const int32_t cur = __ldcg(d.ctl + CTL_TAU) & 1;
+  const int32_t cur = __ldcg(T.ctl + CTL_TAU) & 1;
   const int32_t *__restrict__ fv = T.fv[cur];
   const int32_t *__restrict__ fq = T.fq[cur];
   const int32_t nF = __ldcg(T.nf + cur);
@@ -297,7 +297,7 @@ template <class TV> __global__ void __launch_bounds__(256, VLS_UPDATE_MINB) k_tu
 }
 
 __device__ __forceinline__ void tapply_phase(const Dev &d, const TDev &T, double theta) {
-  const int32_t tau = __ldcg(d.ctl + CTL_TAU), cur = tau & 1;
+  const int32_t tau = __ldcg(T.ctl + CTL_TAU), cur = tau & 1;
   const int32_t *__restrict__ fv = T.fv[cur];
   const int32_t *__restrict__ fq = T.fq[cur];
   const int32_t nF = __ldcg(T.nf + cur);
@@ -331,7 +331,7 @@ __device__ __forceinline__ uint32_t tgives_at(const TDev &T, int32_t i) {
 
 // GL-lane groups per row, lane j takes the row's neighbour j (rows longer than GL loop).
 __device__ __forceinline__ void tfrontier_phase(const Dev &d, const TDev &T) {
-  const int32_t tau = __ldcg(d.ctl + CTL_TAU), cur = tau & 1, nxt = cur ^ 1, tnext = tau + 1;
+  const int32_t tau = __ldcg(T.ctl + CTL_TAU), cur = tau & 1, nxt = cur ^ 1, tnext = tau + 1;
   const int32_t *__restrict__ fv = T.fv[cur];
   const int32_t *__restrict__ fq = T.fq[cur];
   const int32_t nF = __ldcg(T.nf + cur);
@@ -381,7 +381,7 @@ __device__ __forceinline__ void tfrontier_phase(const Dev &d, const TDev &T) {
 // pass is running (or at the hard step bound).
 __device__ __forceinline__ void tepilogue_phase(const Dev &d, const TDev &T, const Handles &H, int32_t max_steps) {
   __shared__ int32_t nact;
-  const int32_t tau = __ldcg(d.ctl + CTL_TAU), cur = tau & 1, nxt = cur ^ 1;
+  const int32_t tau = __ldcg(T.ctl + CTL_TAU), cur = tau & 1, nxt = cur ^ 1;
   int32_t *cnt_cur = T.qcnt + (size_t)cur * T.NP;
   int32_t *cnt_next = T.qcnt + (size_t)nxt * T.NP;
   if (threadIdx.x == 0) nact = 0;
@@ -400,17 +400,17 @@ __device__ __forceinline__ void tepilogue_phase(const Dev &d, const TDev &T, con
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    d.ctl[CTL_TACTIVE] = nact;
+    T.ctl[CTL_TACTIVE] = nact;
     T.nf[cur] = 0;
-    d.ctl[CTL_TAU] = tau + 1;
-    if (H.use && (nact == 0 || tau >= d.ctl[CTL_TLIMIT])) cudaGraphSetConditional(H.loop, 0u);
+    T.ctl[CTL_TAU] = tau + 1;
+    if (H.use && (nact == 0 || tau >= T.ctl[CTL_TLIMIT])) cudaGraphSetConditional(H.loop, 0u);
   }
 }
 
 // The next frontier of every pass, then (epi = 1) the step's epilogue in the last block to finish.
 __global__ void __launch_bounds__(256) k_tfrontier(Dev d, TDev T, Handles H, int32_t max_steps, int32_t epi) {
   tfrontier_phase(d, T);
-  if (epi && last_block(d.ctl + CTL_DONE_TFRONT)) tepilogue_phase(d, T, H, max_steps);
+  if (epi && last_block(T.ctl + CTL_DONE_TFRONT)) tepilogue_phase(d, T, H, max_steps);
 }
 
 // one thread per pass: greedy descent on (arrival, id), then closure along the loop
@@ -499,21 +499,23 @@ void configure_tunnel(Batch &b) {
   b.cfg[KK_TFRONTIER] = row_cfg(b, k_tfrontier, KK_TFRONTIER, 256);
 }
 
-// Runs all passes of b.td (already laid out by the host): init, F_1, then one graph launch
-// WHILE(passes running) { update; apply; next frontier; epilogue }, then the traces.
-cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out) {
+// Runs the passes of T (laid out by the host) on stream st: init, F_1, then one graph launch
+// WHILE(passes running) { update; apply; next frontier; epilogue }, then the traces.  The step
+// counter after the loop is copied to *tau_dst (host memory, pinned: the copy is asynchronous).  In
+// the graph mode the instantiated graph goes to *ge_out; destroy it once st has run it.  With
+// host-driven steps (b.host_loop) the call waits for the passes.
+cudaError_t run_tunnels(Batch &b, const TDev &T, cudaStream_t st, int32_t *tau_dst, cudaGraphExec_t *ge_out) {
   Dev &d = b.d;
-  TDev &T = b.td;
-  cudaStream_t st = b.st;
+  *ge_out = nullptr;
   k_tinit<<<T.NP, 256, 0, st>>>(d, T, T.fv[0], T.fq[0], T.nf + 0); VLS_LAUNCH(b);
-  k_tctl_set<<<1, 1, 0, st>>>(d.ctl, CTL_TAU, 0); VLS_LAUNCH(b);
+  k_tctl_set<<<1, 1, 0, st>>>(T.ctl, CTL_TAU, 0); VLS_LAUNCH(b);
   {
     Handles H0{};
     H0.use = 0;
     k_tfrontier<<<b.cfg[KK_TFRONTIER].grid, b.cfg[KK_TFRONTIER].threads, 0, st>>>(d, T, H0, b.opt.max_pass_steps, 0); VLS_LAUNCH(b);
   }
   cudaMemsetAsync(T.nf + 0, 0, sizeof(int32_t), st);
-  k_tctl_set<<<1, 1, 0, st>>>(d.ctl, CTL_TAU, 1); VLS_LAUNCH(b);
+  k_tctl_set<<<1, 1, 0, st>>>(T.ctl, CTL_TAU, 1); VLS_LAUNCH(b);
   cudaError_t e = cudaSuccess;
   if (b.host_loop) {
     Handles H{};
@@ -534,7 +536,7 @@ cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out) {
       b.prof.end(st, ps);
       if (tau % sync_every == 0) {
         int32_t act = 0;
-        e = cudaMemcpyAsync(&act, d.ctl + CTL_TACTIVE, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(&act, T.ctl + CTL_TACTIVE, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
         b.d2h += (int64_t)sizeof(int32_t);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return e;
@@ -556,17 +558,13 @@ cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out) {
     cudaGraphExec_t ge = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
     if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (ge) cudaGraphExecDestroy(ge);
     if (g) cudaGraphDestroy(g);
+    *ge_out = ge;
     if (e != cudaSuccess) return e;
   }
   k_ttrace<<<(T.NP + 127) / 128, 128, 0, st>>>(d, T); VLS_LAUNCH(b);
-  int32_t tau_end = 0;
-  e = cudaMemcpyAsync(&tau_end, d.ctl + CTL_TAU, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  e = cudaMemcpyAsync(tau_dst, T.ctl + CTL_TAU, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   b.d2h += (int64_t)sizeof(int32_t);
-  *h_steps_out = tau_end - 1;
   return e == cudaSuccess ? cudaGetLastError() : e;
 }
 

@@ -54,6 +54,8 @@ struct TDev {
   unsigned long long *qunc; // [NP] uncertified decisions of the pass (see Params::drift)
   long long *qupd;     // [NP]
   int32_t *active;
+  int32_t *ctl;        // [CTL_SIZE] the passes' own control block (step, passes running, step bound):
+                       // chunks of passes in flight on different streams run independently
   // output: tunnel vertex cycles
   int32_t *tvoff, *tvn;  // [NP]
   int32_t *tverts;       // pool
@@ -205,12 +207,12 @@ cudaError_t add_split_nodes(Batch &b, cudaGraph_t body);
 cudaError_t merge_phase_host(Batch &b);
 cudaError_t split_phase_host(Batch &b);
 // tunnel.cu
-cudaError_t run_tunnels(Batch &b, int32_t *h_steps_out);
+cudaError_t run_tunnels(Batch &b, const TDev &T, cudaStream_t st, int32_t *tau_dst, cudaGraphExec_t *ge_out);
 // refine.cu: vertex normals and mean edge lengths, loop classification, refinement set-up
 cudaError_t launch_vnormals(Batch &b, double *vn, double *elen, double *pmedge);
 cudaError_t launch_classify_handles(Batch &b, const double *vn, const double *pmedge, double *hdl, int32_t nh);
-cudaError_t launch_classify_passes(Batch &b, const double *vn, const double *pmedge);
-cudaError_t launch_refine_prep(Batch &b, int32_t *cyc_pool, const int32_t *coff, const int32_t *clen, int32_t *xedge,
-                               const int32_t *xcap, int32_t *hen, int32_t *pcn);
+cudaError_t launch_classify_passes(Batch &b, const TDev &T, cudaStream_t st, const double *vn, const double *pmedge);
+cudaError_t launch_refine_prep(Batch &b, const TDev &T, cudaStream_t st, int32_t *cyc_pool, const int32_t *coff,
+                               const int32_t *clen, int32_t *xedge, const int32_t *xcap, int32_t *hen, int32_t *pcn);
 
 }  // namespace vls

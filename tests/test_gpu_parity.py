@@ -227,3 +227,22 @@ def test_merge_phase_in_rounds(vls, host_loop):
     assert len(out) == 80
     for g in out:
         assert_parity(g, o)
+
+
+def test_passes_overlapping_the_initial_pass(vls, monkeypatch):
+    """The passes can also start while the initial pass runs (VLS_OVERLAP_PASSES=1: tunnel passes of
+    the handles found by each 256-step segment, refinements once a problem's initial pass ended);
+    every result is the same as in the default order (tunnel and refinement passes afterwards) and
+    the oracle's."""
+    meshes = [meshgen.tube_chain(3, 80), meshgen.torus(48, 20)]
+    probs = [(m, [meshgen.seed_vertex(2 * i + k, m.nv) for k in range(2)]) for i, m in enumerate(meshes)]
+    base = run_gpu(vls, probs)
+    monkeypatch.setenv("VLS_OVERLAP_PASSES", "1")
+    over = run_gpu(vls, probs)
+    i = 0
+    for m, seeds in probs:
+        for s in seeds:
+            o = run_orc(m, s)
+            assert_parity(base[i], o)
+            assert_parity(over[i], o)
+            i += 1
