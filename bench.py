@@ -564,7 +564,16 @@ def main():
     cout = vls.read_result(res)
     vls.vls_result_free(res)
     vls.vls_destroy(cctx)
-    check = {"problems_checked": len(orc_results),
+    # loop classification (Sec. 3.5) of every problem's loops: offset length change > 0 reads as a handle
+    dls = [np.asarray(p.offset_change) for p in cout if len(p.handles)]
+    nloops = sum(len(x) for x in dls)
+    classes = {"loops": nloops,
+               "handle_loops_read_as_handles": sum(int((x[:, 0] > 0).sum()) for x in dls),
+               "refined_loops_read_as_handles": sum(int((x[:, 2] > 0).sum()) for x in dls),
+               "tunnel_loops_read_as_tunnels": sum(int((x[:, 1] < 0).sum()) for x in dls)}
+    check = {"problems_checked": len(orc_results), "classification": classes,
+             "phase_ms": {k: round(cout[0].stats[k], 2) for k in ("ms_operator", "ms_initial", "ms_tunnel",
+                                                                  "ms_refine", "ms_download")},
              "uncertified_decisions": [[int(p.stats["uncertified"]), int(p.stats["pass_uncertified"]),
                                         int(p.stats["refine_uncertified"])] for p in cout],
              "mass_check_max_resid": max(p.stats["mass_resid"] for p in cout),
@@ -574,8 +583,9 @@ def main():
     if orc_results:
         cmp = [compare_with_oracle(g, o) for g, o in zip(cout, orc_results)]
         check["events_and_handle_loops_identical"] = all(c["identical"] for c in cmp)
-        for key in ("record_steps_differing", "cover_steps_differing", "final_layers_differing",
-                    "tunnel_loops_differing"):
+        for key in ("record_steps_differing", "first_differing_step", "uncertified_at_first_differing_step",
+                    "cover_steps_differing", "final_layers_differing", "tunnel_loops_differing",
+                    "refined_loops_differing"):
             check[key] = [c[key] for c in cmp]
         # values mid-run (front in flight; at the end every value is 0 or 1): the max error against
         # the FP64 oracle at a few steps
