@@ -83,8 +83,14 @@ def _load():
                              ("orc_loop_offset_change", P(dbl))]:
                 getattr(L, name).restype = rt
                 getattr(L, name).argtypes = [vp, i32]
+            L.orc_tunnel_arrival_time.restype = P(dbl)
+            L.orc_tunnel_arrival_time.argtypes = [vp, i32]
             L.orc_mean_edge.restype = dbl
             L.orc_mean_edge.argtypes = [vp]
+            L.orc_trace_streamline.restype = i32
+            L.orc_trace_streamline.argtypes = [vp, i64, vp, i64, vp, vp, i64, i32, vp, i64, P(i64), P(i32)]
+            L.orc_streamline.restype = i32
+            L.orc_streamline.argtypes = [vp, i32, i32, P(i64), P(dbl), P(P(dbl))]
             _lib = L
     return _lib
 
@@ -128,6 +134,10 @@ class Tunnel:
     bstar: int
     verts: np.ndarray
     arrival: np.ndarray | None = None
+    arrival_time: np.ndarray | None = None   # with the step's fraction (record_steps only)
+    stream_status: int = -1            # PL streamline (Sec. 3.2): status, -1 not run
+    stream: np.ndarray | None = None   # [n, 3] points of the closed polyline
+    stream_length: float = 0.0
 
 
 @dataclass
@@ -159,6 +169,22 @@ class Result:
     def reeb_cycle_rank(self) -> int:
         # arcs = layers (birth -> death); the graph is connected through the seed
         return int(len(self.layers) - len(self.nodes) + 1)
+
+
+def trace_streamline(mesh, tf, start: int, cut_edges=None, cap: int = 16384):
+    """The PL streamline trace alone (Sec. 3.2) on the arrival field tf (sources 0, unreached -1),
+    the given (a, b) edges cut: (status, [n, 3] points, source reached)."""
+    L = _load()
+    X = np.ascontiguousarray(mesh.X, dtype=np.float64)
+    F = np.ascontiguousarray(mesh.F, dtype=np.int32)
+    t = np.ascontiguousarray(tf, dtype=np.float64)
+    ce = np.ascontiguousarray(np.zeros((0, 2)) if cut_edges is None else cut_edges, dtype=np.int32).reshape(-1, 2)
+    pts = np.zeros((cap, 3))
+    n, end = ctypes.c_int64(), ctypes.c_int32()
+    st = L.orc_trace_streamline(X.ctypes.data, X.shape[0], F.ctypes.data, F.shape[0], t.ctypes.data,
+                                ce.ctypes.data, ce.shape[0], int(start), pts.ctypes.data, cap,
+                                ctypes.byref(n), ctypes.byref(end))
+    return int(st), pts[:min(n.value, cap)].copy(), int(end.value)
 
 
 def detect(mesh, seed: int, opts: Options | None = None, **kw) -> Result:
@@ -197,14 +223,23 @@ def detect(mesh, seed: int, opts: Options | None = None, **kw) -> Result:
                 verts=_arr(L.orc_handle_verts(h, i), nvs, np.int32),
                 points=_arr(L.orc_handle_points(h, i), 3 * m, np.float64).reshape(-1, 3),
                 length=float(L.orc_handle_length(h, i))))
+            sl = []
+            for kind in (0, 1):
+                n, ln, pp = ctypes.c_int64(), ctypes.c_double(), ctypes.POINTER(ctypes.c_double)()
+                sst = L.orc_streamline(h, i, kind, ctypes.byref(n), ctypes.byref(ln), ctypes.byref(pp))
+                sl.append(dict(stream_status=int(sst), stream_length=float(ln.value),
+                               stream=_arr(pp, 3 * n.value, np.float64).reshape(-1, 3)))
             ti = _arr(L.orc_tunnel_info(h, i), 4, np.int32)
             arr = L.orc_tunnel_arrival(h, i)
+            atf = L.orc_tunnel_arrival_time(h, i)
             res.tunnels.append(Tunnel(status=int(ti[0]), stop_step=int(ti[1]), bstar=int(ti[2]),
                                       verts=_arr(L.orc_tunnel_verts(h, i), max(int(ti[3]), 0), np.int32),
-                                      arrival=_arr(arr, nv, np.int32) if arr else None))
+                                      arrival=_arr(arr, nv, np.int32) if arr else None,
+                                      arrival_time=_arr(atf, nv, np.float64) if atf else None, **sl[0]))
             ri = _arr(L.orc_refined_info(h, i), 4, np.int32)
             res.refined.append(Tunnel(status=int(ri[0]), stop_step=int(ri[1]), bstar=int(ri[2]),
-                                      verts=_arr(L.orc_refined_verts(h, i), max(int(ri[3]), 0), np.int32)))
+                                      verts=_arr(L.orc_refined_verts(h, i), max(int(ri[3]), 0), np.int32),
+                                      **sl[1]))
         res.offset_change = np.array([_arr(L.orc_loop_offset_change(h, i), 3, np.float64) for i in range(nh)]
                                      ).reshape(-1, 3)
         res.mean_edge = float(L.orc_mean_edge(h))

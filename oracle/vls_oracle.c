@@ -81,6 +81,13 @@ typedef struct {
   int32_t rinfo[4];   /* refined handle (Sec. 3.3): status, stop step, first vertex reached, n verts */
   int32_t *rverts;
   double dlen[3];     /* length change under the normal offset (Sec. 3.5): handle, tunnel, refined */
+  /* PL streamlines (Sec. 3.2) of the tunnel pass [0] and the refinement pass [1]: status (-1 not run),
+     points of the closed polyline, its length */
+  int32_t sst[2];
+  int64_t sn[2];
+  double *spts[2];
+  double slen[2];
+  double *tfa;        /* fractional arrival times of the tunnel pass, kept when record_steps is set */
 } handle_t;
 
 struct orc_run {
@@ -570,6 +577,7 @@ static void emit_handle(orc_run *R, int32_t step, int32_t l, int32_t node, const
   H->info[3] = (int32_t)m;
   H->info[4] = (int32_t)nvs;
   H->tinfo[0] = -1;
+  H->sst[0] = H->sst[1] = -1;
 }
 
 /* mean position of the vertices v in list (or all vertices when list == NULL) with pred */
@@ -891,6 +899,181 @@ static int initial_pass(orc_run *R, int32_t seed) {
   return st;
 }
 
+/* ------------------------------------------------- PL streamline (Sec. 3.2) */
+/* The tunnel pass's streamline: steepest descent of the arrival time interpolated linearly over the
+   faces of the cut, restricted domain, from the first far-side vertex reached back to a source.
+   Arrival time: the step at which theta is crossed, with the fraction of that step found by linear
+   interpolation of the value in time; sources 0, unreached -1.  A face is usable when its three
+   vertices are reached and none of its edges is cut.  In a face with corners (p0, p1, p2), the
+   gradient is g = al e1 + be e2 (e1 = p1 - p0, e2 = p2 - p0), from the Gram system of e1, e2.
+   At a vertex: among the usable faces around it (CSR order) whose descent direction -g points into
+   the face's corner there, the steepest (largest |g|, the first on ties); the path crosses that face
+   to its opposite edge.  With none, it follows the steepest descending kept edge.  On an edge: into
+   the face beyond it if -g enters that face (and the face is usable), to the edge where the ray
+   leaves it; else along the edge to its lower end (smaller arrival, then smaller id).  It ends at a
+   source; a vertex with no descent left fails.  Points: the start vertex, every edge crossing, every
+   vertex passed.  At most SL_MAX points, the closure included. */
+#define SL_MAX 16384
+static int face_usable(const orc_run *R, const double *tf, const char *cut, int32_t f) {
+  const int32_t *t = R->F + 3 * f;
+  for (int q = 0; q < 3; ++q) {
+    if (tf[t[q]] < 0.0) return 0;
+    int64_t k = slot_of(R, t[q], t[(q + 1) % 3]);
+    if (k < 0 || cut[k]) return 0;
+  }
+  return 1;
+}
+static int32_t third_vertex(const orc_run *R, int32_t f, int32_t a, int32_t b) {
+  const int32_t *t = R->F + 3 * f;
+  for (int q = 0; q < 3; ++q)
+    if (t[q] != a && t[q] != b) return t[q];
+  return -1;
+}
+/* gradient coefficients (al, be) and |g|^2 of the arrival time on the face (p0, p1, p2); 0 if degenerate */
+static int grad_face(const orc_run *R, const double *tf, int32_t p0, int32_t p1, int32_t p2, double *al, double *be,
+                     double *n2) {
+  const double *x0 = R->X + 3 * p0, *x1 = R->X + 3 * p1, *x2 = R->X + 3 * p2;
+  double e1[3], e2[3];
+  for (int d = 0; d < 3; ++d) { e1[d] = x1[d] - x0[d]; e2[d] = x2[d] - x0[d]; }
+  double g11 = (e1[0] * e1[0] + e1[1] * e1[1]) + e1[2] * e1[2];
+  double g12 = (e1[0] * e2[0] + e1[1] * e2[1]) + e1[2] * e2[2];
+  double g22 = (e2[0] * e2[0] + e2[1] * e2[1]) + e2[2] * e2[2];
+  double det = g11 * g22 - g12 * g12;
+  if (!(det > 0.0)) return 0;
+  double d1 = tf[p1] - tf[p0], d2 = tf[p2] - tf[p0];
+  double a = (g22 * d1 - g12 * d2) / det, b = (g11 * d2 - g12 * d1) / det;
+  *al = a;
+  *be = b;
+  *n2 = ((a * a) * g11 + ((a + a) * b) * g12) + (b * b) * g22;
+  return 1;
+}
+static int sl_push(double **pts, int64_t *n, int64_t *cap, const double *p) {
+  if (*n >= SL_MAX) return 0;
+  if (*n == *cap) { *cap *= 2; *pts = (double *)realloc(*pts, sizeof(double) * 3 * *cap); }
+  for (int d = 0; d < 3; ++d) (*pts)[3 * *n + d] = p[d];
+  ++*n;
+  return 1;
+}
+static int streamline(const orc_run *R, const double *tf, const char *cut, int32_t start, double **pts_out,
+                      int64_t *n_out, int32_t *end_vertex) {
+  int64_t cap = 256, n = 0;
+  double *pts = (double *)malloc(sizeof(double) * 3 * cap);
+  int32_t v = start, ex = -1, ey = -1;
+  double mu = 0.0;
+  int at_vertex = 1, st = ST_ELOOPFAIL;
+  sl_push(&pts, &n, &cap, R->X + 3 * v);
+  for (int64_t it = 0; it < 4 * SL_MAX; ++it) {
+    if (at_vertex) {
+      if (tf[v] == 0.0) { st = ST_OK; *end_vertex = v; break; }
+      double best = -1.0, bal = 0.0, bbe = 0.0;
+      int32_t bu = -1, bw = -1;
+      for (int64_t k = R->rp[v]; k < R->rp[v + 1]; ++k) {
+        int32_t u = R->col[k], f = R->hface[k], w = third_vertex(R, f, v, u);
+        double al, be, n2;
+        if (!face_usable(R, tf, cut, f) || !grad_face(R, tf, v, u, w, &al, &be, &n2)) continue;
+        if (!(al <= 0.0 && be <= 0.0 && (al < 0.0 || be < 0.0))) continue; /* -g not into this corner */
+        if (n2 > best) { best = n2; bal = al; bbe = be; bu = u; bw = w; }
+      }
+      if (bu >= 0) {
+        double lam = bbe / (bal + bbe); /* where the ray meets edge u -> w, from u */
+        if (lam <= 0.0) { v = bu; if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break; continue; }
+        if (lam >= 1.0) { v = bw; if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break; continue; }
+        double p[3];
+        for (int d = 0; d < 3; ++d) p[d] = R->X[3 * bu + d] + lam * (R->X[3 * bw + d] - R->X[3 * bu + d]);
+        if (!sl_push(&pts, &n, &cap, p)) break;
+        ex = bw; ey = bu; mu = 1.0 - lam; /* into the face left of w -> u */
+        at_vertex = 0;
+        continue;
+      }
+      double bs = 0.0;
+      int32_t bn = -1;
+      for (int64_t k = R->rp[v]; k < R->rp[v + 1]; ++k) {
+        int32_t u = R->col[k];
+        if (cut[k] || tf[u] < 0.0) continue;
+        const double *a = R->X + 3 * v, *b = R->X + 3 * u;
+        double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+        double sl = (tf[v] - tf[u]) / sqrt((dx * dx + dy * dy) + dz * dz);
+        if (sl > bs) { bs = sl; bn = u; }
+      }
+      if (bn < 0) break; /* no descent left */
+      v = bn;
+      if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break;
+      continue;
+    }
+    /* on edge ex -> ey at mu from ex, entering the face left of it */
+    int64_t k = slot_of(R, ex, ey);
+    int32_t f = k >= 0 ? R->hface[k] : -1, z = f >= 0 ? third_vertex(R, f, ex, ey) : -1;
+    double al = 0.0, be = 0.0, n2 = 0.0;
+    if (f < 0 || !face_usable(R, tf, cut, f) || !grad_face(R, tf, ex, ey, z, &al, &be, &n2) || !(be < 0.0)) {
+      v = (tf[ex] < tf[ey] || (tf[ex] == tf[ey] && ex < ey)) ? ex : ey; /* along the edge to its lower end */
+      at_vertex = 1;
+      if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break;
+      continue;
+    }
+    /* ray (u, w) = (mu - s al, -s be) in the frame (e1, e2) of the face (ex, ey, z) */
+    double su = al > 0.0 ? mu / al : INFINITY;
+    double suw = (al + be) < 0.0 ? (mu - 1.0) / (al + be) : INFINITY;
+    double p[3];
+    if (su <= suw) { /* leaves through the edge from ex to z (u = 0) */
+      double w = -(su * be);
+      if (w >= 1.0) { v = z; at_vertex = 1; if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break; continue; }
+      if (w <= 0.0) { v = ex; at_vertex = 1; if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break; continue; }
+      for (int d = 0; d < 3; ++d) p[d] = R->X[3 * ex + d] + w * (R->X[3 * z + d] - R->X[3 * ex + d]);
+      ey = z; mu = w; /* into the face left of ex -> z */
+    } else { /* leaves through the edge from ey to z (u + w = 1) */
+      double w = -(suw * be);
+      if (w >= 1.0) { v = z; at_vertex = 1; if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break; continue; }
+      if (w <= 0.0) { v = ey; at_vertex = 1; if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break; continue; }
+      for (int d = 0; d < 3; ++d) p[d] = R->X[3 * ey + d] + w * (R->X[3 * z + d] - R->X[3 * ey + d]);
+      ex = z; mu = 1.0 - w; /* into the face left of z -> ey */
+    }
+    if (!sl_push(&pts, &n, &cap, p)) break;
+  }
+  *pts_out = pts;
+  *n_out = n;
+  return st;
+}
+/* close the streamline along the loop, as the vertex trace is closed: from the source reached, the
+   shorter way along the loop to a crossing edge ending at the start */
+static int close_streamline(const orc_run *R, const handle_t *H, int64_t m, int32_t bstar, int32_t xs, double **pts,
+                            int64_t *n) {
+  int64_t bd = -1, bj = -1;
+  int dir = 1;
+  for (int64_t i = 0; i < m; ++i) {
+    if (H->edges[2 * i + 1] != bstar) continue;
+    for (int64_t j = 0; j < m; ++j) {
+      if (H->edges[2 * j] != xs) continue;
+      int64_t fwd = ((i - j) % m + m) % m, bwd = ((j - i) % m + m) % m;
+      int64_t d = fwd <= bwd ? fwd : bwd;
+      if (bd < 0 || d < bd) { bd = d; bj = j; dir = fwd <= bwd ? 1 : -1; }
+    }
+  }
+  if (bd < 0) return ST_ELOOPFAIL;
+  int64_t cap = *n > 0 ? *n : 1;
+  int32_t last = xs;
+  for (int64_t s = 1; s <= bd; ++s) {
+    int64_t idx = ((bj + dir * s) % m + m) % m;
+    int32_t a = H->edges[2 * idx];
+    if (a == last) continue;
+    if (*n >= SL_MAX) return ST_ELAYERS;
+    *pts = (double *)realloc(*pts, sizeof(double) * 3 * (*n + 1));
+    for (int d = 0; d < 3; ++d) (*pts)[3 * *n + d] = R->X[3 * a + d];
+    ++*n;
+    last = a;
+  }
+  (void)cap;
+  return ST_OK;
+}
+static double polyline_length(const double *p, int64_t n) {
+  double len = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double *a = p + 3 * i, *b = p + 3 * ((i + 1) % n);
+    double dx = b[0] - a[0], dy = b[1] - a[1], dz = b[2] - a[2];
+    len = len + sqrt((dx * dx + dy * dy) + dz * dz);
+  }
+  return len;
+}
+
 /* --------------------------------------------------------- tunnel pass */
 static int tunnel_pass(orc_run *R, handle_t *H, int32_t th_step) {
   int64_t nv = R->nv;
@@ -929,7 +1112,12 @@ static int tunnel_pass(orc_run *R, handle_t *H, int32_t th_step) {
   }
   double *phi = (double *)calloc(nv, sizeof(double));
   int32_t *T = (int32_t *)malloc(sizeof(int32_t) * nv);
-  for (int64_t v = 0; v < nv; ++v) { T[v] = -1; if (src[v]) { phi[v] = 1.0; T[v] = 0; } }
+  double *tf = (double *)malloc(sizeof(double) * nv); /* arrival step with its fraction (-1 unreached) */
+  for (int64_t v = 0; v < nv; ++v) {
+    T[v] = -1;
+    tf[v] = -1.0;
+    if (src[v]) { phi[v] = 1.0; T[v] = 0; tf[v] = 0.0; }
+  }
   int64_t *cand = (int64_t *)malloc(sizeof(int64_t) * (nv + 1));
   int64_t *Fl = (int64_t *)malloc(sizeof(int64_t) * (nv + 1));
   double *nphi = (double *)malloc(sizeof(double) * (nv + 1));
@@ -978,8 +1166,13 @@ static int tunnel_pass(orc_run *R, handle_t *H, int32_t th_step) {
     }
     for (int64_t i = 0; i < nF; ++i) {
       int64_t v = Fl[i];
+      double old = phi[v];
       phi[v] = nphi[i];
-      if (T[v] < 0 && phi[v] >= th) T[v] = tau;
+      if (T[v] < 0 && phi[v] >= th) {
+        T[v] = tau;
+        /* theta crossed between the step's old and new value: linear in time within the step */
+        tf[v] = (double)(tau - 1) + (th - old) / (phi[v] - old);
+      }
     }
     for (int64_t i = 0; i < nF; ++i) {
       int64_t v = Fl[i];
@@ -1059,12 +1252,23 @@ static int tunnel_pass(orc_run *R, handle_t *H, int32_t th_step) {
       H->tinfo[3] = (int32_t)nc;
     }
     free(path);
+    if (st == ST_OK) {
+      int32_t xs = -1;
+      double *sp = NULL;
+      int64_t sn = 0;
+      int sst = streamline(R, tf, cut, bstar, &sp, &sn, &xs);
+      if (sst == ST_OK) sst = close_streamline(R, H, m, bstar, xs, &sp, &sn);
+      H->sst[0] = sst;
+      H->spts[0] = sp;
+      H->sn[0] = sst == ST_OK ? sn : 0;
+      H->slen[0] = sst == ST_OK ? polyline_length(sp, sn) : 0.0;
+    }
   }
   H->tinfo[0] = st;
-  if (R->opt.record_steps) H->arrival = T;
+  if (R->opt.record_steps) { H->arrival = T; H->tfa = tf; tf = NULL; }
   else free(T);
   free(dom); free(cut); free(src); free(tgt); free(hp); free(hc); free(hv); free(hd);
-  free(phi); free(cand); free(Fl); free(nphi);
+  free(phi); free(tf); free(cand); free(Fl); free(nphi);
   return st;
 }
 
@@ -1130,13 +1334,19 @@ static int refine_pass(orc_run *R, handle_t *H) {
   if (m == 0) { free(xe); return ST_ELOOPFAIL; }
   handle_t T;
   memset(&T, 0, sizeof(T));
+  T.sst[0] = -1;
   T.edges = xe;
   T.info[3] = (int32_t)m;
   int st = tunnel_pass(R, &T, INT32_MAX);
   for (int q = 0; q < 4; ++q) H->rinfo[q] = T.tinfo[q];
   H->rinfo[0] = st;
   H->rverts = T.tverts;
+  H->sst[1] = T.sst[0];
+  H->spts[1] = T.spts[0];
+  H->sn[1] = T.sn[0];
+  H->slen[1] = T.slen[0];
   free(T.arrival);
+  free(T.tfa);
   free(xe);
   return st;
 }
@@ -1245,7 +1455,9 @@ orc_run *orc_detect(const double *X, int64_t nv, const int32_t *F, int64_t nf, i
       int st = tunnel_pass(R, H, H->info[0]);
       if (st == ST_ELOOPFAIL && H->info[3] > 0 && H->tinfo[2] < 0) {
         free(H->arrival);
+        free(H->tfa);
         H->arrival = NULL;
+        H->tfa = NULL;
         st = tunnel_pass(R, H, INT32_MAX);
       }
       if (st != ST_OK && R->status == ST_OK) R->status = st;
@@ -1289,7 +1501,8 @@ void orc_free(orc_run *R) {
   free(R->lst); free(R->lbirth); free(R->ldeath); free(R->nodes); free(R->npos);
   for (int32_t i = 0; i < R->nh; ++i) {
     free(R->h[i].edges); free(R->h[i].verts); free(R->h[i].pts); free(R->h[i].tverts); free(R->h[i].arrival);
-    free(R->h[i].rverts);
+    free(R->h[i].rverts); free(R->h[i].spts[0]); free(R->h[i].spts[1]);
+    free(R->h[i].tfa);
   }
   free(R->vn);
   free(R->h); free(R->out_layer); free(R->out_phi); free(R->rec); free(R->layers_out); free(R->stamp);
@@ -1318,7 +1531,45 @@ double orc_handle_length(const orc_run *r, int32_t h) { return r->h[h].len; }
 const int32_t *orc_tunnel_info(const orc_run *r, int32_t h) { return r->h[h].tinfo; }
 const int32_t *orc_tunnel_verts(const orc_run *r, int32_t h) { return r->h[h].tverts; }
 const int32_t *orc_tunnel_arrival(const orc_run *r, int32_t h) { return r->h[h].arrival; }
+const double *orc_tunnel_arrival_time(const orc_run *r, int32_t h) { return r->h[h].tfa; }
 const int32_t *orc_refined_info(const orc_run *r, int32_t h) { return r->h[h].rinfo; }
 const int32_t *orc_refined_verts(const orc_run *r, int32_t h) { return r->h[h].rverts; }
 const double *orc_loop_offset_change(const orc_run *r, int32_t h) { return r->h[h].dlen; }
+int32_t orc_trace_streamline(const double *X, int64_t nv, const int32_t *F, int64_t nf, const double *tf,
+                             const int32_t *cut_edges, int64_t ncut, int32_t start, double *pts, int64_t cap,
+                             int64_t *n_out, int32_t *end_vertex) {
+  orc_run *R = (orc_run *)calloc(1, sizeof(orc_run));
+  R->nv = nv;
+  R->nf = nf;
+  int st = build_mesh(R, X, F);
+  *n_out = 0;
+  *end_vertex = -1;
+  if (st == ST_OK && (start < 0 || start >= nv)) st = ST_EINVAL;
+  char *cut = st == ST_OK ? (char *)calloc(R->nnz + 1, 1) : NULL;
+  for (int64_t i = 0; st == ST_OK && i < ncut; ++i) {
+    int64_t a = slot_of(R, cut_edges[2 * i], cut_edges[2 * i + 1]), b = slot_of(R, cut_edges[2 * i + 1], cut_edges[2 * i]);
+    if (a < 0 || b < 0) { st = ST_EINVAL; break; }
+    cut[a] = cut[b] = 1;
+  }
+  if (st == ST_OK) {
+    double *sp = NULL;
+    int64_t sn = 0;
+    st = streamline(R, tf, cut, start, &sp, &sn, end_vertex);
+    for (int64_t i = 0; i < sn && i < cap; ++i)
+      for (int d = 0; d < 3; ++d) pts[3 * i + d] = sp[3 * i + d];
+    *n_out = sn;
+    free(sp);
+  }
+  free(cut);
+  free(R->X); free(R->F); free(R->rp); free(R->col); free(R->hface); free(R->Lv); free(R->Ld);
+  free(R);
+  return st;
+}
+int32_t orc_streamline(const orc_run *r, int32_t h, int32_t kind, int64_t *n, double *len, const double **pts) {
+  const handle_t *H = &r->h[h];
+  *n = H->sn[kind];
+  *len = H->slen[kind];
+  *pts = H->spts[kind];
+  return H->sst[kind];
+}
 double orc_mean_edge(const orc_run *r) { return r->mean_edge; }

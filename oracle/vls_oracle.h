@@ -81,6 +81,9 @@ const int32_t *orc_tunnel_info(const orc_run *r, int32_t h);
 const int32_t *orc_tunnel_verts(const orc_run *r, int32_t h);
 /* arrival steps of pass h (-1 unreached), kept only when record_steps is set */
 const int32_t *orc_tunnel_arrival(const orc_run *r, int32_t h);
+/* arrival times of pass h with the fraction of the step at which theta was crossed (linear in time
+ * within the step; sources 0, unreached -1), kept only when record_steps is set */
+const double *orc_tunnel_arrival_time(const orc_run *r, int32_t h);
 
 /* refined handle loops (Sec. 3.3), one per handle: info [0] status (-1: not run), [1] stop step,
  * [2] first vertex reached, [3] n verts; verts = the vertex cycle */
@@ -91,6 +94,14 @@ const int32_t *orc_refined_verts(const orc_run *r, int32_t h);
  * (NaN where the loop does not exist); > 0 reads as a handle, < 0 as a tunnel */
 const double *orc_loop_offset_change(const orc_run *r, int32_t h);
 double orc_mean_edge(const orc_run *r);
+/* PL streamlines (Sec. 3.2) of the tunnel pass (kind 0) and the refinement pass (kind 1) of handle h:
+ * returns the status (-1: not run); n points [n][3] of the closed polyline, its length */
+int32_t orc_streamline(const orc_run *r, int32_t h, int32_t kind, int64_t *n, double *len, const double **pts);
+/* the streamline trace alone, on a given arrival field tf (sources 0, unreached -1) with the given
+ * edges cut: writes up to cap points, returns the status, *n_out points, the source reached */
+int32_t orc_trace_streamline(const double *X, int64_t nv, const int32_t *F, int64_t nf, const double *tf,
+                             const int32_t *cut_edges, int64_t ncut, int32_t start, double *pts, int64_t cap,
+                             int64_t *n_out, int32_t *end_vertex);
 
 #ifdef __cplusplus
 }
