@@ -338,6 +338,17 @@ def compare_with_oracle(g, o) -> dict:
     rec = int((g.records != o.records).any(axis=1).sum()) if len(g.records) == len(o.records) else -1
     bad = np.nonzero((g.records != o.records).any(axis=1))[0] if rec > 0 else []
     first = int(bad[0]) if len(bad) else None
+    # PL streamlines (Sec. 3.2): status agreement, and the length difference where the pass's vertex
+    # loop is the oracle's (the FP32 arrival times drift, so the points move slightly)
+    sl_n = sl_same = 0
+    sl_rel = 0.0
+    for tg, to in list(zip(g.tunnels, o.tunnels)) + list(zip(g.refined, o.refined)):
+        if tg.stream_status < 0 and to.stream_status < 0:
+            continue
+        sl_n += 1
+        sl_same += tg.stream_status == to.stream_status
+        if tg.stream_status == to.stream_status == 0 and np.array_equal(tg.verts, to.verts):
+            sl_rel = max(sl_rel, abs(tg.stream_length - to.stream_length) / to.stream_length)
     # loop classification (Sec. 3.5): offset length change > 0 reads as a handle, < 0 as a tunnel
     dl = np.asarray(g.offset_change)
     return {"identical": bool(same), "record_steps_differing": rec,
@@ -348,6 +359,7 @@ def compare_with_oracle(g, o) -> dict:
             "cover_steps_differing": int((g.cover != o.cover).sum()),
             "final_layers_differing": int((g.layer != o.layer).sum()), "tunnel_loops_differing": int(tun),
             "refined_loops_differing": int(ref),
+            "streamlines": [sl_n, sl_same, sl_rel],
             "classified_as_handle": [int((dl[:, 0] > 0).sum()), int((dl[:, 2] > 0).sum())] if dl.size else [0, 0],
             "classified_as_tunnel": int((dl[:, 1] < 0).sum()) if dl.size else 0, "loops": int(len(dl))}
 
@@ -587,6 +599,9 @@ def main():
                     "cover_steps_differing", "final_layers_differing", "tunnel_loops_differing",
                     "refined_loops_differing"):
             check[key] = [c[key] for c in cmp]
+        check["streamlines"] = {"traced": sum(c["streamlines"][0] for c in cmp),
+                                "status_as_oracle": sum(c["streamlines"][1] for c in cmp),
+                                "max_rel_length_diff_same_vertex_loop": max(c["streamlines"][2] for c in cmp)}
         # values mid-run (front in flight; at the end every value is 0 or 1): the max error against
         # the FP64 oracle at a few steps
         nchk = len(orc_results)

@@ -123,6 +123,8 @@ typedef struct {
                                may have drifted from the FP64 one by this much, so the decision could
                                go the other way there.  0 selects 1e-6 (FP32) or 2e-2 (BF16), above
                                the largest drift measured on the workloads */
+  int32_t streamlines;      /* 1: trace the PL streamline of every tunnel and refinement pass
+                               (vls_result_streamline); 0: only the vertex cycles */
 } vls_options;
 
 /* A closed, oriented triangle mesh: X[nv][3] positions, F[nf][3] vertex ids (CCW). */
@@ -239,6 +241,21 @@ VLS_API vls_status vls_result_refined(const vls_result *r, int32_t p, int32_t i,
  * offset x mean edge length, minus its length (NaN where the loop does not exist).  Tunnel loops
  * tend to shrink (< 0), handle loops to grow (> 0). */
 VLS_API vls_status vls_result_offset_change(const vls_result *r, int32_t p, int32_t i, double out[3]);
+/* PL streamline (Sec. 3.2: the loop traced back from the first point reached, against the
+ * gradient of the arrival time) of handle i's tunnel pass (kind 0) or refinement pass (kind 1).
+ * Arrival time: the step at which theta_iso was crossed, with the fraction of that step from a
+ * linear interpolation of the value in time; it is interpolated linearly over the faces of the
+ * pass's cut, restricted domain.  The path runs from the first far-side vertex reached down the
+ * steepest descent, face by face (through a vertex into the steepest face whose corner holds the
+ * descent direction, else along the steepest descending edge; along an edge where the descent
+ * leaves no face), to a source, and is closed along the border as the vertex cycle is.
+ * *status: VLS_OK, VLS_ELOOPFAIL (no descent left), VLS_ELAYERS (more than 16384 points, or the
+ * pass chunk's point pool overflowed), -1 (not traced: the pass did not run or failed, or
+ * streamlines = 0).  *pts = [n][3] positions of the closed polyline's points (the start vertex,
+ * edge crossings, vertices passed), library-owned; *length = its length, closing segment
+ * included.  VLS_EINVAL for a bad index or kind. */
+VLS_API vls_status vls_result_streamline(const vls_result *r, int32_t p, int32_t i, int32_t kind, int32_t *status,
+                                         const double **pts, int64_t *n, double *length);
 
 /* Reeb graph (Sec. 5): nodes [n][2] = (kind 0 SEED / 1 SPLIT / 2 MERGE / 3 END, step),
  * positions [n][3] (mean of the narrow band); arcs = layers [L][3] = (birth node, death

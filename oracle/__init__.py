@@ -32,7 +32,7 @@ class Options(ctypes.Structure):
                 ("max_steps", ctypes.c_int32), ("max_pass_steps", ctypes.c_int32),
                 ("seed_ring", ctypes.c_int32), ("naive", ctypes.c_int32), ("tunnels", ctypes.c_int32),
                 ("record_steps", ctypes.c_int32), ("refine", ctypes.c_int32), ("offset", ctypes.c_double),
-                ("max_passes", ctypes.c_int32)]
+                ("max_passes", ctypes.c_int32), ("streamlines", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:

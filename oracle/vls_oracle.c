@@ -150,6 +150,7 @@ void orc_default_options(orc_options *o) {
   o->refine = 1;
   o->offset = 0.5;
   o->max_passes = 0;
+  o->streamlines = 1;
 }
 
 void orc_constants(const orc_options *o, double out[4]) {
@@ -1252,7 +1253,7 @@ static int tunnel_pass(orc_run *R, handle_t *H, int32_t th_step) {
       H->tinfo[3] = (int32_t)nc;
     }
     free(path);
-    if (st == ST_OK) {
+    if (st == ST_OK && R->opt.streamlines) {
       int32_t xs = -1;
       double *sp = NULL;
       int64_t sn = 0;

@@ -33,6 +33,7 @@ typedef struct {
   int32_t refine;         /* 1: run the handle-refinement pass after each tunnel pass (Sec. 3.3) */
   double offset;          /* loop classification: normal offset in mean edge lengths (Sec. 3.5) */
   int32_t max_passes;     /* tunnel (and refinement) passes run: the first max_passes handles; 0: all */
+  int32_t streamlines;    /* 1: trace the PL streamline of every successful pass (Sec. 3.2) */
 } orc_options;
 
 typedef struct orc_run orc_run;

@@ -40,6 +40,9 @@ struct ProbResult {
   struct Tunnel {
     int32_t info[3];
     std::vector<int32_t> verts;
+    int32_t sst = -1;          // PL streamline (Sec. 3.2): status, -1 not traced
+    std::vector<double> spts;  // [n][3] closed polyline
+    double slen = 0.0;
   };
   std::vector<Tunnel> tunnels;
   std::vector<Tunnel> refined;             // refined handle loops (Sec. 3.3), one per handle
@@ -141,6 +144,7 @@ extern "C" void vls_default_options(vls_options *o) {
   o->max_passes = 0;
   o->autotune = 1;
   o->drift_bound = 0.0;
+  o->streamlines = 1;
 }
 
 extern "C" void vls_constants(const vls_options *o, double out[4]) {
@@ -186,7 +190,8 @@ extern "C" vls_status vls_create(vls_ctx **ctx, const vls_options *o, void *stre
       (c->opt.rows_per_warp != 0 && c->opt.rows_per_warp != 8 && c->opt.rows_per_warp != 16 &&
        c->opt.rows_per_warp != 32) ||
       (c->opt.K != 0 && c->opt.K != KMAX) || c->opt.laplacian != 0 || !(c->opt.offset > 0.0) ||
-      c->opt.max_passes < 0 || (c->opt.autotune != 0 && c->opt.autotune != 1) || c->opt.drift_bound < 0.0) {
+      c->opt.max_passes < 0 || (c->opt.autotune != 0 && c->opt.autotune != 1) || c->opt.drift_bound < 0.0 ||
+      (c->opt.streamlines != 0 && c->opt.streamlines != 1)) {
     delete c;
     return VLS_EINVAL;
   }
@@ -411,6 +416,19 @@ void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut, i
   T.path = L.take<int32_t>(PV);
   T.qdl = L.take<double>(NP);
   T.ctl = L.take<int32_t>(CTL_SIZE);
+  T.tfa = nullptr;
+  if (b.opt.streamlines) {
+    // streamline point pool shared by the chunk's passes: a quarter point per pass vertex plus 64
+    // per pass (measured: about two points per vertex of the loop, a few hundredths of the mesh)
+    T.scap = PV / 4 + 64 * (int64_t)NP;
+    T.tfa = L.take<double>(PV);
+    T.sst = L.take<int32_t>(NP);
+    T.sn = L.take<int32_t>(NP);
+    T.soff = L.take<int32_t>(NP);
+    T.slen = L.take<double>(NP);
+    T.spts = L.take<double>(3 * T.scap);
+    T.nspts = L.take<int32_t>(1);
+  }
   if (nx > 0) {
     T.xedge = L.take<int32_t>(2 * nx);
     b.r_cyc = L.take<int32_t>(ncyc);
@@ -465,9 +483,13 @@ struct PassOut {
   std::vector<int64_t> upd, unc;
   std::vector<double> mres, dl;
   std::vector<int32_t> verts; // vertex cycles (local ids), pool
+  std::vector<int32_t> sst;   // streamlines: status (-1 not traced), offset in spts (points), points
+  std::vector<int64_t> soff;
+  std::vector<int32_t> sn;
+  std::vector<double> slen, spts;
   explicit PassOut(int32_t nh)
       : status(nh, -1), steps(nh, 0), bstar(nh, 0), voff(nh, 0), vn(nh, 0), upd(nh, 0), unc(nh, 0), mres(nh, 0.0),
-        dl(nh, std::nan("")) {}
+        dl(nh, std::nan("")), sst(nh, -1), soff(nh, 0), sn(nh, 0), slen(nh, 0.0) {}
 };
 enum PassKind : int { PASS_TUNNEL = 0, PASS_REFINE = 1 };
 
@@ -486,6 +508,8 @@ struct PassBatch {
   int32_t *pin_i = nullptr;     // [7 NP + 2]: status, steps, first vertex, cycle offset, length, border edges; ntv, tau
   long long *pin_l = nullptr;   // [2 NP]: rows updated, uncertified decisions
   double *pin_d = nullptr;      // [2 NP]: mass-check residual, offset length change
+  int32_t *pin_s = nullptr;     // streamlines [3 NP + 1]: status, points, pool offset; points stored
+  double *pin_sl = nullptr;     // streamlines [NP]: length
 };
 
 // Enqueue one chunk of passes on stream st (no host wait): tunnel passes (Sec. 3.2) take handle h's
@@ -510,6 +534,13 @@ cudaError_t enqueue_chunk(vls_ctx *ctx, Batch &b, int kind, const std::vector<in
   pb.pin_l = static_cast<long long *>(ctx->pinned.take(sizeof(long long) * (size_t)(2 * NP)));
   pb.pin_d = static_cast<double *>(ctx->pinned.take(sizeof(double) * (size_t)(2 * NP)));
   if (!ht || !pb.pin_i || !pb.pin_l || !pb.pin_d) return cudaErrorMemoryAllocation;
+  pb.pin_s = nullptr;
+  pb.pin_sl = nullptr;
+  if (b.opt.streamlines) {
+    pb.pin_s = static_cast<int32_t *>(ctx->pinned.take(sizeof(int32_t) * (size_t)(3 * NP + 1)));
+    pb.pin_sl = static_cast<double *>(ctx->pinned.take(sizeof(double) * (size_t)NP));
+    if (!pb.pin_s || !pb.pin_sl) return cudaErrorMemoryAllocation;
+  }
   int32_t *pbase = ht, *pprob = ht + NP + 1, *pstep = pprob + NP, *pcoff = pstep + NP, *pcn = pcoff + NP;
   int32_t *heoff = pcn + NP, *hen = heoff + NP, *rcoff = hen + NP, *rclen = rcoff + NP, *xcap = rclen + NP;
   int32_t *rcyc = xcap + NP;
@@ -619,6 +650,13 @@ cudaError_t enqueue_chunk(vls_ctx *ctx, Batch &b, int kind, const std::vector<in
   CKR(dn(pb.pin_l + NP, T.qunc, sizeof(long long) * NP));
   CKR(dn(pb.pin_d, T.qmres, sizeof(double) * NP));
   CKR(dn(pb.pin_d + NP, T.qdl, sizeof(double) * NP));
+  if (T.tfa) {
+    CKR(dn(pb.pin_s, T.sst, sizeof(int32_t) * NP));
+    CKR(dn(pb.pin_s + NP, T.sn, sizeof(int32_t) * NP));
+    CKR(dn(pb.pin_s + 2 * NP, T.soff, sizeof(int32_t) * NP));
+    CKR(dn(pb.pin_s + 3 * NP, T.nspts, sizeof(int32_t)));
+    CKR(dn(pb.pin_sl, T.slen, sizeof(double) * NP));
+  }
   CKR(cudaEventRecord(pb.ev1, st));
   return cudaSuccess;
 }
@@ -640,6 +678,13 @@ cudaError_t finish_chunk(vls_ctx *ctx, Batch &b, PassBatch &pb, PassOut &out, in
     CKR(cudaMemcpyAsync(out.verts.data() + tv0, pb.T.tverts, sizeof(int32_t) * ntv, cudaMemcpyDeviceToHost, ctx->st3));
     b.d2h += (int64_t)sizeof(int32_t) * ntv;
   }
+  const int64_t ns = pb.pin_s ? std::min<int64_t>(pb.pin_s[3 * NP], pb.T.scap) : 0;
+  const size_t sp0 = out.spts.size() / 3;
+  if (ns > 0) {
+    out.spts.resize(3 * (sp0 + (size_t)ns));
+    CKR(cudaMemcpyAsync(out.spts.data() + 3 * sp0, pb.T.spts, sizeof(double) * 3 * ns, cudaMemcpyDeviceToHost, ctx->st3));
+    b.d2h += (int64_t)sizeof(double) * 3 * ns;
+  }
   CKR(cudaFreeAsync(pb.mem, ctx->st3));
   CKR(cudaStreamSynchronize(ctx->st3));
   pb.mem = nullptr;
@@ -654,6 +699,14 @@ cudaError_t finish_chunk(vls_ctx *ctx, Batch &b, PassBatch &pb, PassOut &out, in
     out.unc[h] = pb.pin_l[NP + q];
     out.mres[h] = pb.pin_d[q];
     out.dl[h] = pb.pin_d[NP + q];
+    if (pb.pin_s) {
+      const int32_t *ps = pb.pin_s;
+      const bool ok = ps[q] == VLS_OK && (int64_t)ps[2 * NP + q] + ps[NP + q] <= ns;
+      out.sst[h] = ps[q] == VLS_OK && !ok ? VLS_ELAYERS : ps[q];
+      out.sn[h] = ok ? ps[NP + q] : 0;
+      out.soff[h] = (int64_t)sp0 + (ok ? ps[2 * NP + q] : 0);
+      out.slen[h] = ok ? pb.pin_sl[q] : 0.0;
+    }
     if (pb.kind == PASS_REFINE && pi[5 * NP + q] == 0) { // no border: a degenerate tunnel cycle
       out.status[h] = VLS_ELOOPFAIL;
       out.steps[h] = 0;
@@ -1478,6 +1531,11 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
         T.info[1] = o.steps[h];
         T.info[2] = o.bstar[h];
         if (o.status[h] == VLS_OK) T.verts.assign(o.verts.begin() + o.voff[h], o.verts.begin() + o.voff[h] + o.vn[h]);
+        if (o.status[h] == VLS_OK && o.sst[h] >= 0) {
+          T.sst = o.sst[h];
+          T.slen = o.slen[h];
+          T.spts.assign(o.spts.begin() + 3 * o.soff[h], o.spts.begin() + 3 * (o.soff[h] + o.sn[h]));
+        }
         (kind == 0 ? r.tunnels : r.refined).push_back(std::move(T));
       }
       r.dlen.push_back({h_hdl[h], tun.dl[h], ref.dl[h]});
@@ -1584,6 +1642,18 @@ extern "C" vls_status vls_result_refined(const vls_result *r, int32_t p, int32_t
   GETP(r, p);
   if (i < 0 || i >= (int32_t)P_.refined.size() || !info) return VLS_EINVAL;
   std::memcpy(info, P_.refined[i].info, sizeof(int32_t) * 3);
+  return VLS_OK;
+}
+extern "C" vls_status vls_result_streamline(const vls_result *r, int32_t p, int32_t i, int32_t kind, int32_t *status,
+                                            const double **pts, int64_t *n, double *length) {
+  GETP(r, p);
+  if (kind != 0 && kind != 1) return VLS_EINVAL;
+  const auto &v = kind == 0 ? P_.tunnels : P_.refined;
+  if (i < 0 || i >= (int32_t)v.size() || !status || !pts || !n || !length) return VLS_EINVAL;
+  *status = v[i].sst;
+  *pts = v[i].spts.data();
+  *n = (int64_t)(v[i].spts.size() / 3);
+  *length = v[i].slen;
   return VLS_OK;
 }
 extern "C" vls_status vls_result_offset_change(const vls_result *r, int32_t p, int32_t i, double out[3]) {

@@ -12,8 +12,12 @@
 //   trace    from b*, repeatedly the unvisited kept neighbour with the least (arrival, id)
 //            whose arrival step is not larger, down to a source; the cycle is closed along
 //            the handle loop by the shorter way to a crossing edge ending at b*.
+//   stream   (streamlines on) the PL steepest-descent path of the arrival time from b* to a
+//            source, closed the same way (k_tstream below).
 // Only rows whose closed neighbourhood holds both phases change, so each step updates the
 // frontier rows only (exact).
+#include <math_constants.h>
+
 #include <type_traits>
 
 #include "vls_batch.cuh"
@@ -104,6 +108,7 @@ __global__ void __launch_bounds__(256) k_tinit(Dev d, TDev T, int32_t *fv0, int3
     T.flag[base + (b - voff)] = F_TGT;
     tph_st(T, base + (a - voff), 1.0);
     T.T[base + (a - voff)] = 0;
+    if (T.tfa) T.tfa[base + (a - voff)] = 0.0;
     cut[2 * i] = slot_of(d.rp, d.col, a, b);
     cut[2 * i + 1] = slot_of(d.rp, d.col, b, a);
     const int32_t s = atomicAdd(nF0, 1);
@@ -307,11 +312,17 @@ __device__ __forceinline__ void tapply_phase(const Dev &d, const TDev &T, double
     const int32_t idx = T.pbase[q] + (v - d.voff[p]);
     if (!VCHK(T.err, idx, T.PV, 320)) continue;
     const double x = T.onew[i];
-    tph_st(T, idx, x);
     if (T.T[idx] < 0 && x >= theta) {
+      // arrival time: theta is crossed within this step, linearly in time between the old value
+      // and the new one
+      if (T.tfa) {
+        const double old = tph_ld(T, idx);
+        T.tfa[idx] = dadd((double)(tau - 1), ddiv(dsub(theta, old), dsub(x, old)));
+      }
       T.T[idx] = tau;
       if (T.flag[idx] & F_TGT) atomicMin(&T.qbstar[q], v - d.voff[p]);
     }
+    tph_st(T, idx, x);
   }
 }
 __global__ void k_tapply(Dev d, TDev T, double theta) { tapply_phase(d, T, theta); }
@@ -487,6 +498,306 @@ __global__ void k_ttrace(Dev d, TDev T) {
   }
 }
 
+// ---- PL streamline (Sec. 3.2: the loop is traced back from the first point reached against the
+// gradient of the arrival time).  The arrival time tfa is the step at which theta was crossed, with
+// the fraction of that step found by linear interpolation in time (sources 0; unreached vertices
+// have T < 0), interpolated linearly over the faces of the cut, restricted domain.  A face is
+// usable when its three vertices are reached and none of its edges is cut.  In a face with corners
+// (p0, p1, p2) the gradient is g = al e1 + be e2 (e1 = p1 - p0, e2 = p2 - p0), from the Gram
+// system of e1, e2.  At a vertex the path enters the steepest (largest |g|, first in CSR order on
+// ties) usable face around it whose corner there holds -g, and crosses it to the opposite edge;
+// with none it follows the steepest descending kept edge.  On an edge it enters the face beyond if
+// that face is usable and -g points into it, and leaves it where the ray meets its boundary; else
+// it runs along the edge to its lower end (smaller arrival, then smaller id).  It ends at a source;
+// a vertex with no descent left fails.  Points: the start, every edge crossing, every vertex
+// passed; at most SL_MAX with the closure.  Every product, sum and quotient is rounded on its own.
+constexpr int32_t SL_MAX = 16384;
+
+struct SlPass {
+  const Dev &d;
+  const TDev &T;
+  int32_t q, base, voff;
+  __device__ bool reached(int32_t v) const { return T.T[base + (v - voff)] >= 0; }
+  __device__ double tf(int32_t v) const { return T.tfa[base + (v - voff)]; }
+  __device__ bool cut(int32_t a, int32_t b, int32_t k) const {
+    const int8_t fa = T.flag[base + (a - voff)], fb = T.flag[base + (b - voff)];
+    if (((fa & F_SRC) && (fb & F_TGT)) || ((fa & F_TGT) && (fb & F_SRC))) return is_cut(T, q, k);
+    return false;
+  }
+  __device__ bool usable(int32_t f) const {
+    const int32_t *t = d.F + 3 * (int64_t)f;
+    for (int j = 0; j < 3; ++j)
+      if (!reached(t[j])) return false;
+    for (int j = 0; j < 3; ++j) {
+      const int32_t a = t[j], b = t[j == 2 ? 0 : j + 1];
+      const int32_t k = slot_of(d.rp, d.col, a, b);
+      if (k < 0 || cut(a, b, k)) return false;
+    }
+    return true;
+  }
+  __device__ int32_t third(int32_t f, int32_t a, int32_t b) const {
+    const int32_t *t = d.F + 3 * (int64_t)f;
+    return (t[0] != a && t[0] != b) ? t[0] : (t[1] != a && t[1] != b) ? t[1] : t[2];
+  }
+  // gradient coefficients and |g|^2 of the arrival time on the face (p0, p1, p2)
+  __device__ bool grad(int32_t p0, int32_t p1, int32_t p2, double &al, double &be, double &n2) const {
+    const double *x0 = d.X + 3 * (int64_t)p0, *x1 = d.X + 3 * (int64_t)p1, *x2 = d.X + 3 * (int64_t)p2;
+    double e1[3], e2[3];
+    for (int j = 0; j < 3; ++j) {
+      e1[j] = dsub(x1[j], x0[j]);
+      e2[j] = dsub(x2[j], x0[j]);
+    }
+    const double g11 = dadd(dadd(dmul(e1[0], e1[0]), dmul(e1[1], e1[1])), dmul(e1[2], e1[2]));
+    const double g12 = dadd(dadd(dmul(e1[0], e2[0]), dmul(e1[1], e2[1])), dmul(e1[2], e2[2]));
+    const double g22 = dadd(dadd(dmul(e2[0], e2[0]), dmul(e2[1], e2[1])), dmul(e2[2], e2[2]));
+    const double det = dsub(dmul(g11, g22), dmul(g12, g12));
+    if (!(det > 0.0)) return false;
+    const double t0 = tf(p0), d1 = dsub(tf(p1), t0), d2 = dsub(tf(p2), t0);
+    al = ddiv(dsub(dmul(g22, d1), dmul(g12, d2)), det);
+    be = ddiv(dsub(dmul(g11, d2), dmul(g12, d1)), det);
+    n2 = dadd(dadd(dmul(dmul(al, al), g11), dmul(dmul(dadd(al, al), be), g12)), dmul(dmul(be, be), g22));
+    return true;
+  }
+};
+
+// point writer: counts, and stores when out is non-null; at most lim points
+struct SlOut {
+  double *out;
+  int32_t n, lim;
+  __device__ bool push(const double p[3]) {
+    if (n >= lim) return false;
+    if (out) {
+      out[3 * (int64_t)n] = p[0];
+      out[3 * (int64_t)n + 1] = p[1];
+      out[3 * (int64_t)n + 2] = p[2];
+    }
+    ++n;
+    return true;
+  }
+  __device__ bool push_v(const Dev &d, int32_t v) { return push(d.X + 3 * (int64_t)v); }
+};
+
+// the trace from start; returns VLS_OK with the source reached in xs, or VLS_ELOOPFAIL
+__device__ int32_t sl_trace(const SlPass &S, int32_t start, SlOut &o, int32_t &xs) {
+  const Dev &d = S.d;
+  int32_t v = start, ex = -1, ey = -1;
+  double mu = 0.0;
+  bool at_vertex = true;
+  o.push_v(d, v);
+  for (int32_t it = 0; it < 4 * SL_MAX; ++it) {
+    if (at_vertex) {
+      if (S.T.T[S.base + (v - S.voff)] == 0) {
+        xs = v;
+        return VLS_OK;
+      }
+      double best = -1.0, bal = 0.0, bbe = 0.0;
+      int32_t bu = -1, bw = -1;
+      for (int32_t k = d.rp[v]; k < d.rp[v + 1]; ++k) {
+        const int32_t u = d.col[k], f = d.hface[k], w = S.third(f, v, u);
+        double al, be, n2;
+        if (!S.usable(f) || !S.grad(v, u, w, al, be, n2)) continue;
+        if (!(al <= 0.0 && be <= 0.0 && (al < 0.0 || be < 0.0))) continue; // -g not into this corner
+        if (n2 > best) {
+          best = n2;
+          bal = al;
+          bbe = be;
+          bu = u;
+          bw = w;
+        }
+      }
+      if (bu >= 0) {
+        const double lam = ddiv(bbe, dadd(bal, bbe)); // where the ray meets edge u -> w, from u
+        if (lam <= 0.0) {
+          v = bu;
+          if (!o.push_v(d, v)) break;
+          continue;
+        }
+        if (lam >= 1.0) {
+          v = bw;
+          if (!o.push_v(d, v)) break;
+          continue;
+        }
+        double p[3];
+        const double *xu = d.X + 3 * (int64_t)bu, *xw = d.X + 3 * (int64_t)bw;
+        for (int j = 0; j < 3; ++j) p[j] = dadd(xu[j], dmul(lam, dsub(xw[j], xu[j])));
+        if (!o.push(p)) break;
+        ex = bw;
+        ey = bu;
+        mu = dsub(1.0, lam); // into the face left of w -> u
+        at_vertex = false;
+        continue;
+      }
+      double bs = 0.0;
+      int32_t bn = -1;
+      const double *xv = d.X + 3 * (int64_t)v;
+      for (int32_t k = d.rp[v]; k < d.rp[v + 1]; ++k) {
+        const int32_t u = d.col[k];
+        if (S.cut(v, u, k) || !S.reached(u)) continue;
+        const double *xu = d.X + 3 * (int64_t)u;
+        const double dx = dsub(xu[0], xv[0]), dy = dsub(xu[1], xv[1]), dz = dsub(xu[2], xv[2]);
+        const double sl = ddiv(dsub(S.tf(v), S.tf(u)), dsqrt(dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz))));
+        if (sl > bs) {
+          bs = sl;
+          bn = u;
+        }
+      }
+      if (bn < 0) break; // no descent left
+      v = bn;
+      if (!o.push_v(d, v)) break;
+      continue;
+    }
+    // on edge ex -> ey at mu from ex, entering the face left of it
+    const int32_t k = slot_of(d.rp, d.col, ex, ey);
+    const int32_t f = k >= 0 ? d.hface[k] : -1, z = f >= 0 ? S.third(f, ex, ey) : -1;
+    double al = 0.0, be = 0.0, n2 = 0.0;
+    if (f < 0 || !S.usable(f) || !S.grad(ex, ey, z, al, be, n2) || !(be < 0.0)) {
+      const double ta = S.tf(ex), tb = S.tf(ey);
+      v = (ta < tb || (ta == tb && ex < ey)) ? ex : ey; // along the edge to its lower end
+      at_vertex = true;
+      if (!o.push_v(d, v)) break;
+      continue;
+    }
+    // ray (u, w) = (mu - s al, -s be) in the frame (e1, e2) of the face (ex, ey, z)
+    const double su = al > 0.0 ? ddiv(mu, al) : CUDART_INF;
+    const double suw = dadd(al, be) < 0.0 ? ddiv(dsub(mu, 1.0), dadd(al, be)) : CUDART_INF;
+    double p[3];
+    if (su <= suw) { // leaves through the edge from ex to z
+      const double w = -dmul(su, be);
+      if (w >= 1.0) {
+        v = z;
+        at_vertex = true;
+        if (!o.push_v(d, v)) break;
+        continue;
+      }
+      if (w <= 0.0) {
+        v = ex;
+        at_vertex = true;
+        if (!o.push_v(d, v)) break;
+        continue;
+      }
+      const double *xa = d.X + 3 * (int64_t)ex, *xz = d.X + 3 * (int64_t)z;
+      for (int j = 0; j < 3; ++j) p[j] = dadd(xa[j], dmul(w, dsub(xz[j], xa[j])));
+      ey = z;
+      mu = w; // into the face left of ex -> z
+    } else { // leaves through the edge from ey to z
+      const double w = -dmul(suw, be);
+      if (w >= 1.0) {
+        v = z;
+        at_vertex = true;
+        if (!o.push_v(d, v)) break;
+        continue;
+      }
+      if (w <= 0.0) {
+        v = ey;
+        at_vertex = true;
+        if (!o.push_v(d, v)) break;
+        continue;
+      }
+      const double *xb = d.X + 3 * (int64_t)ey, *xz = d.X + 3 * (int64_t)z;
+      for (int j = 0; j < 3; ++j) p[j] = dadd(xb[j], dmul(w, dsub(xz[j], xb[j])));
+      ex = z;
+      mu = dsub(1.0, w); // into the face left of z -> ey
+    }
+    if (!o.push(p)) break;
+  }
+  return VLS_ELOOPFAIL;
+}
+
+// closure along the border, as the vertex trace is closed: from the source reached, the shorter
+// way along the border edges to one ending at the start
+__device__ int32_t sl_close(const Dev &d, const TDev &T, int32_t q, int32_t bstar, int32_t xs, SlOut &o) {
+  const int32_t eo = T.heoff[q], m = T.hen[q];
+  int64_t bd = -1, bj = -1;
+  int dir = 1;
+  for (int32_t i = 0; i < m; ++i) {
+    if (T.xedge[2 * (int64_t)(eo + i) + 1] != bstar) continue;
+    for (int32_t j = 0; j < m; ++j) {
+      if (T.xedge[2 * (int64_t)(eo + j)] != xs) continue;
+      const int64_t fwd = ((int64_t)(i - j) % m + m) % m, bwd = ((int64_t)(j - i) % m + m) % m;
+      const int64_t dd = fwd <= bwd ? fwd : bwd;
+      if (bd < 0 || dd < bd) {
+        bd = dd;
+        bj = j;
+        dir = fwd <= bwd ? 1 : -1;
+      }
+    }
+  }
+  if (bd < 0) return VLS_ELOOPFAIL;
+  int32_t last = xs;
+  for (int64_t s = 1; s <= bd; ++s) {
+    const int64_t ix = ((bj + dir * s) % m + m) % m;
+    const int32_t a = T.xedge[2 * (int64_t)(eo + ix)];
+    if (a == last) continue;
+    if (!o.push_v(d, a)) return VLS_ELAYERS;
+    last = a;
+  }
+  return VLS_OK;
+}
+
+// one thread per pass whose vertex trace succeeded.  Count pass (write false): status and point
+// count.  Write pass: the points at the pass's pool offset and the polyline's length.
+__global__ void __launch_bounds__(32) k_tstream(Dev d, TDev T, bool write) {
+  const int32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= T.NP) return;
+  if (!write) T.sst[q] = -1;
+  if (T.qstatus[q] != VLS_OK || (write && T.sst[q] != VLS_OK)) return;
+  const int32_t p = T.pprob[q];
+  const SlPass S{d, T, q, T.pbase[q], d.voff[p]};
+  const int32_t start = S.voff + T.qbstar[q];
+  // the write pass stores no more points than the count pass found room for
+  SlOut o{write ? T.spts + 3 * (int64_t)T.soff[q] : nullptr, 0, write ? T.sn[q] : SL_MAX};
+  int32_t xs = -1;
+  int32_t st = sl_trace(S, start, o, xs);
+  if (st == VLS_OK) st = sl_close(d, T, q, start, xs, o);
+  if (!write) {
+    T.sst[q] = st;
+    T.sn[q] = st == VLS_OK ? o.n : 0;
+    return;
+  }
+  if (st != VLS_OK || o.n != T.sn[q]) { // the write pass retraces the count pass's path
+    T.sst[q] = VLS_ELOOPFAIL;
+    return;
+  }
+  const double *P = T.spts + 3 * (int64_t)T.soff[q];
+  double len = 0.0;
+  for (int32_t i = 0; i < o.n; ++i) {
+    const double *a = P + 3 * (int64_t)i, *b = P + 3 * (int64_t)(i + 1 == o.n ? 0 : i + 1);
+    const double dx = dsub(b[0], a[0]), dy = dsub(b[1], a[1]), dz = dsub(b[2], a[2]);
+    len = dadd(len, dsqrt(dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz))));
+  }
+  T.slen[q] = len;
+}
+
+// one warp: pool offsets of the traced streamlines in pass order; a streamline past the pool's end
+// fails with VLS_ELAYERS.  *nspts = points stored.
+__global__ void k_tstream_scan(TDev T) {
+  const int32_t lane = threadIdx.x;
+  int64_t run = 0, kept_end = 0;
+  for (int32_t b0 = 0; b0 < T.NP; b0 += 32) {
+    const int32_t q = b0 + lane;
+    const bool ok = q < T.NP && T.sst[q] == VLS_OK;
+    const int64_t c = ok ? T.sn[q] : 0;
+    int64_t inc = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const int64_t beg = run + inc - c;
+    int64_t end = 0;
+    if (ok) {
+      if (beg + c > T.scap) T.sst[q] = VLS_ELAYERS;
+      else {
+        T.soff[q] = (int32_t)beg;
+        end = beg + c;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) end = max(end, __shfl_xor_sync(0xffffffffu, end, o));
+    kept_end = max(kept_end, end);
+    run += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  if (lane == 0) *T.nspts = (int32_t)kept_end;
+}
+
 __global__ void k_tctl_set(int32_t *ctl, int32_t idx, int32_t v) { ctl[idx] = v; }
 
 }  // namespace
@@ -563,6 +874,12 @@ cudaError_t run_tunnels(Batch &b, const TDev &T, cudaStream_t st, int32_t *tau_d
     if (e != cudaSuccess) return e;
   }
   k_ttrace<<<(T.NP + 127) / 128, 128, 0, st>>>(d, T); VLS_LAUNCH(b);
+  if (T.tfa) {
+    const int32_t g = (T.NP + 31) / 32;
+    k_tstream<<<g, 32, 0, st>>>(d, T, false); VLS_LAUNCH(b);
+    k_tstream_scan<<<1, 32, 0, st>>>(T); VLS_LAUNCH(b);
+    k_tstream<<<g, 32, 0, st>>>(d, T, true); VLS_LAUNCH(b);
+  }
   e = cudaMemcpyAsync(tau_dst, T.ctl + CTL_TAU, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   b.d2h += (int64_t)sizeof(int32_t);
   return e == cudaSuccess ? cudaGetLastError() : e;

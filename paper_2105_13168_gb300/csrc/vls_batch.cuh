@@ -62,6 +62,13 @@ struct TDev {
   int32_t *ntverts;
   int32_t tvcap;
   int32_t *path;         // scratch [pass-vertex] for traces
+  // PL streamlines (Sec. 3.2), when on (tfa non-null)
+  double *tfa;           // [pass-vertex] arrival time with the step's fraction (read where T >= 0)
+  int32_t *sst, *sn, *soff; // [NP] status (-1 not traced), points, offset in the pool
+  double *slen;          // [NP] length of the closed polyline
+  double *spts;          // [scap][3] point pool
+  int32_t *nspts;        // points stored
+  int64_t scap;
 };
 
 // Kernel kinds timed in profile mode.

@@ -31,7 +31,7 @@ class vls_options(ctypes.Structure):
                 ("hook_variant", ctypes.c_int32), ("rows_per_warp", ctypes.c_int32),
                 ("refine", ctypes.c_int32), ("offset", ctypes.c_double), ("K", ctypes.c_int32),
                 ("laplacian", ctypes.c_int32), ("max_passes", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("drift_bound", ctypes.c_double)]
+                ("drift_bound", ctypes.c_double), ("streamlines", ctypes.c_int32)]
 
 
 class vls_mesh(ctypes.Structure):
@@ -57,7 +57,7 @@ class vls_stats(ctypes.Structure):
 EXPORTS = ["vls_default_options", "vls_constants", "vls_create", "vls_destroy", "vls_detect", "vls_detect_batch",
            "vls_result_count", "vls_result_status", "vls_result_genus", "vls_result_stats", "vls_result_num_loops",
            "vls_result_loop", "vls_result_handle", "vls_result_tunnel", "vls_result_refined",
-           "vls_result_offset_change", "vls_result_reeb", "vls_result_state",
+           "vls_result_offset_change", "vls_result_streamline", "vls_result_reeb", "vls_result_state",
            "vls_result_records", "vls_result_kernel_times", "vls_result_free", "vls_status_string",
            "vls_tunnel_pass_noalloc"]
 
@@ -106,6 +106,8 @@ def load(path: str = LIB_PATH):
     L.vls_result_refined.restype = i32
     L.vls_result_offset_change.argtypes = [vp, i32, i32, P(dbl)]
     L.vls_result_offset_change.restype = i32
+    L.vls_result_streamline.argtypes = [vp, i32, i32, i32, P(i32), P(P(dbl)), P(i64), P(dbl)]
+    L.vls_result_streamline.restype = i32
     L.vls_result_reeb.argtypes = [vp, i32, P(P(i32)), P(P(dbl)), P(i32), P(P(i32)), P(i32)]
     L.vls_result_reeb.restype = i32
     L.vls_result_state.argtypes = [vp, i32, P(P(i32)), P(P(dbl)), P(P(i32)), P(i64)]
@@ -237,6 +239,9 @@ class Tunnel:
     stop_step: int
     bstar: int
     verts: np.ndarray
+    stream_status: int = -1             # PL streamline (Sec. 3.2): status, -1 not traced
+    stream: np.ndarray | None = None    # [n, 3] points of the closed polyline
+    stream_length: float = 0.0
 
 
 @dataclass
@@ -284,6 +289,13 @@ def vls_result_kernel_times(res) -> dict:
     return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(n.value)}
 
 
+def _streamline(L, res, p: int, i: int, kind: int) -> dict:
+    st, pts, n, ln = ctypes.c_int32(), ctypes.POINTER(ctypes.c_double)(), ctypes.c_int64(), ctypes.c_double()
+    L.vls_result_streamline(res, p, i, kind, ctypes.byref(st), ctypes.byref(pts), ctypes.byref(n), ctypes.byref(ln))
+    return dict(stream_status=int(st.value), stream=_np(pts, 3 * n.value, np.float64).reshape(-1, 3),
+                stream_length=float(ln.value))
+
+
 def read_result(res) -> list:
     """Copy every problem of a result handle into Python objects."""
     L = load()
@@ -318,13 +330,15 @@ def read_result(res) -> list:
             L.vls_result_tunnel(res, p, i, info)
             v, nv_ = P(ctypes.c_int32)(), ctypes.c_int64()
             L.vls_result_loop(res, p, 1, i, ctypes.byref(v), ctypes.byref(nv_), None, None)
-            pr.tunnels.append(Tunnel(status=info[0], stop_step=info[1], bstar=info[2], verts=_np(v, nv_.value, np.int32)))
+            pr.tunnels.append(Tunnel(status=info[0], stop_step=info[1], bstar=info[2], verts=_np(v, nv_.value, np.int32),
+                                     **_streamline(L, res, p, i, 0)))
         for i in range(max(0, L.vls_result_num_loops(res, p, 2))):
             info = (ctypes.c_int32 * 3)()
             L.vls_result_refined(res, p, i, info)
             v, nv_ = P(ctypes.c_int32)(), ctypes.c_int64()
             L.vls_result_loop(res, p, 2, i, ctypes.byref(v), ctypes.byref(nv_), None, None)
-            pr.refined.append(Tunnel(status=info[0], stop_step=info[1], bstar=info[2], verts=_np(v, nv_.value, np.int32)))
+            pr.refined.append(Tunnel(status=info[0], stop_step=info[1], bstar=info[2], verts=_np(v, nv_.value, np.int32),
+                                     **_streamline(L, res, p, i, 1)))
         dl = []
         for i in range(len(pr.handles)):
             out3 = (ctypes.c_double * 3)()
