@@ -249,9 +249,9 @@ VLS_API vls_status vls_result_offset_change(const vls_result *r, int32_t p, int3
  * steepest descent, face by face (through a vertex into the steepest face whose corner holds the
  * descent direction, else along the steepest descending edge; along an edge where the descent
  * leaves no face), to a source, and is closed along the border as the vertex cycle is.
- * *status: VLS_OK, VLS_ELOOPFAIL (no descent left), VLS_ELAYERS (more than 16384 points, or the
- * pass chunk's point pool overflowed), -1 (not traced: the pass did not run or failed, or
- * streamlines = 0).  *pts = [n][3] positions of the closed polyline's points (the start vertex,
+ * *status: VLS_OK, VLS_ELOOPFAIL (no descent left), VLS_ELAYERS (more points than the budget
+ * min(16384, nv / 4 + 64) for a mesh of nv vertices), -1 (not traced: the pass did not run or
+ * failed, or streamlines = 0).  *pts = [n][3] positions of the closed polyline's points (the start vertex,
  * edge crossings, vertices passed), library-owned; *length = its length, closing segment
  * included.  VLS_EINVAL for a bad index or kind. */
 VLS_API vls_status vls_result_streamline(const vls_result *r, int32_t p, int32_t i, int32_t kind, int32_t *status,

@@ -913,8 +913,10 @@ static int initial_pass(orc_run *R, int32_t seed) {
    the face beyond it if -g enters that face (and the face is usable), to the edge where the ray
    leaves it; else along the edge to its lower end (smaller arrival, then smaller id).  It ends at a
    source; a vertex with no descent left fails.  Points: the start vertex, every edge crossing, every
-   vertex passed.  At most SL_MAX points, the closure included. */
+   vertex passed.  Point budget, the closure included: min(SL_MAX, nv / 4 + 64) for a mesh of nv
+   vertices (the loops seen take a few hundredths of nv); a trace past it fails with ST_ELAYERS. */
 #define SL_MAX 16384
+static int64_t sl_budget(const orc_run *R) { return R->nv / 4 + 64 < SL_MAX ? R->nv / 4 + 64 : SL_MAX; }
 static int face_usable(const orc_run *R, const double *tf, const char *cut, int32_t f) {
   const int32_t *t = R->F + 3 * f;
   for (int q = 0; q < 3; ++q) {
@@ -948,8 +950,8 @@ static int grad_face(const orc_run *R, const double *tf, int32_t p0, int32_t p1,
   *n2 = ((a * a) * g11 + ((a + a) * b) * g12) + (b * b) * g22;
   return 1;
 }
-static int sl_push(double **pts, int64_t *n, int64_t *cap, const double *p) {
-  if (*n >= SL_MAX) return 0;
+static int sl_push(double **pts, int64_t *n, int64_t *cap, const double *p, int64_t budget) {
+  if (*n >= budget) return 0;
   if (*n == *cap) { *cap *= 2; *pts = (double *)realloc(*pts, sizeof(double) * 3 * *cap); }
   for (int d = 0; d < 3; ++d) (*pts)[3 * *n + d] = p[d];
   ++*n;
@@ -962,7 +964,8 @@ static int streamline(const orc_run *R, const double *tf, const char *cut, int32
   int32_t v = start, ex = -1, ey = -1;
   double mu = 0.0;
   int at_vertex = 1, st = ST_ELOOPFAIL;
-  sl_push(&pts, &n, &cap, R->X + 3 * v);
+  const int64_t budget = sl_budget(R);
+  sl_push(&pts, &n, &cap, R->X + 3 * v, budget);
   for (int64_t it = 0; it < 4 * SL_MAX; ++it) {
     if (at_vertex) {
       if (tf[v] == 0.0) { st = ST_OK; *end_vertex = v; break; }
@@ -977,11 +980,11 @@ static int streamline(const orc_run *R, const double *tf, const char *cut, int32
       }
       if (bu >= 0) {
         double lam = bbe / (bal + bbe); /* where the ray meets edge u -> w, from u */
-        if (lam <= 0.0) { v = bu; if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break; continue; }
-        if (lam >= 1.0) { v = bw; if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break; continue; }
+        if (lam <= 0.0) { v = bu; if (!sl_push(&pts, &n, &cap, R->X + 3 * v, budget)) break; continue; }
+        if (lam >= 1.0) { v = bw; if (!sl_push(&pts, &n, &cap, R->X + 3 * v, budget)) break; continue; }
         double p[3];
         for (int d = 0; d < 3; ++d) p[d] = R->X[3 * bu + d] + lam * (R->X[3 * bw + d] - R->X[3 * bu + d]);
-        if (!sl_push(&pts, &n, &cap, p)) break;
+        if (!sl_push(&pts, &n, &cap, p, budget)) break;
         ex = bw; ey = bu; mu = 1.0 - lam; /* into the face left of w -> u */
         at_vertex = 0;
         continue;
@@ -998,7 +1001,7 @@ static int streamline(const orc_run *R, const double *tf, const char *cut, int32
       }
       if (bn < 0) break; /* no descent left */
       v = bn;
-      if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break;
+      if (!sl_push(&pts, &n, &cap, R->X + 3 * v, budget)) break;
       continue;
     }
     /* on edge ex -> ey at mu from ex, entering the face left of it */
@@ -1008,7 +1011,7 @@ static int streamline(const orc_run *R, const double *tf, const char *cut, int32
     if (f < 0 || !face_usable(R, tf, cut, f) || !grad_face(R, tf, ex, ey, z, &al, &be, &n2) || !(be < 0.0)) {
       v = (tf[ex] < tf[ey] || (tf[ex] == tf[ey] && ex < ey)) ? ex : ey; /* along the edge to its lower end */
       at_vertex = 1;
-      if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break;
+      if (!sl_push(&pts, &n, &cap, R->X + 3 * v, budget)) break;
       continue;
     }
     /* ray (u, w) = (mu - s al, -s be) in the frame (e1, e2) of the face (ex, ey, z) */
@@ -1017,18 +1020,18 @@ static int streamline(const orc_run *R, const double *tf, const char *cut, int32
     double p[3];
     if (su <= suw) { /* leaves through the edge from ex to z (u = 0) */
       double w = -(su * be);
-      if (w >= 1.0) { v = z; at_vertex = 1; if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break; continue; }
-      if (w <= 0.0) { v = ex; at_vertex = 1; if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break; continue; }
+      if (w >= 1.0) { v = z; at_vertex = 1; if (!sl_push(&pts, &n, &cap, R->X + 3 * v, budget)) break; continue; }
+      if (w <= 0.0) { v = ex; at_vertex = 1; if (!sl_push(&pts, &n, &cap, R->X + 3 * v, budget)) break; continue; }
       for (int d = 0; d < 3; ++d) p[d] = R->X[3 * ex + d] + w * (R->X[3 * z + d] - R->X[3 * ex + d]);
       ey = z; mu = w; /* into the face left of ex -> z */
     } else { /* leaves through the edge from ey to z (u + w = 1) */
       double w = -(suw * be);
-      if (w >= 1.0) { v = z; at_vertex = 1; if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break; continue; }
-      if (w <= 0.0) { v = ey; at_vertex = 1; if (!sl_push(&pts, &n, &cap, R->X + 3 * v)) break; continue; }
+      if (w >= 1.0) { v = z; at_vertex = 1; if (!sl_push(&pts, &n, &cap, R->X + 3 * v, budget)) break; continue; }
+      if (w <= 0.0) { v = ey; at_vertex = 1; if (!sl_push(&pts, &n, &cap, R->X + 3 * v, budget)) break; continue; }
       for (int d = 0; d < 3; ++d) p[d] = R->X[3 * ey + d] + w * (R->X[3 * z + d] - R->X[3 * ey + d]);
       ex = z; mu = 1.0 - w; /* into the face left of z -> ey */
     }
-    if (!sl_push(&pts, &n, &cap, p)) break;
+    if (!sl_push(&pts, &n, &cap, p, budget)) break;
   }
   *pts_out = pts;
   *n_out = n;
@@ -1056,7 +1059,7 @@ static int close_streamline(const orc_run *R, const handle_t *H, int64_t m, int3
     int64_t idx = ((bj + dir * s) % m + m) % m;
     int32_t a = H->edges[2 * idx];
     if (a == last) continue;
-    if (*n >= SL_MAX) return ST_ELAYERS;
+    if (*n >= sl_budget(R)) return ST_ELAYERS;
     *pts = (double *)realloc(*pts, sizeof(double) * 3 * (*n + 1));
     for (int d = 0; d < 3; ++d) (*pts)[3 * *n + d] = R->X[3 * a + d];
     ++*n;

@@ -372,7 +372,7 @@ void layout_batch(Layout &L, Batch &b) {
 
 // nx > 0: a refinement chunk -- its own border-edge pool (nx edges) and the tunnel cycles it starts
 // from (ncyc vertex ids)
-void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut, int64_t nx, int64_t ncyc) {
+void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut, int64_t nx, int64_t ncyc, int64_t scap) {
   TDev &T = b.td;
   T.NP = NP;
   T.PV = (int32_t)PV;
@@ -418,10 +418,12 @@ void layout_tunnels(Layout &L, Batch &b, int32_t NP, int64_t PV, int64_t ncut, i
   T.ctl = L.take<int32_t>(CTL_SIZE);
   T.tfa = nullptr;
   if (b.opt.streamlines) {
-    // streamline point pool shared by the chunk's passes: a quarter point per pass vertex plus 64
-    // per pass (measured: about two points per vertex of the loop, a few hundredths of the mesh)
-    T.scap = PV / 4 + 64 * (int64_t)NP;
+    // streamline points: each pass's region of its point budget (see sl_budget), and a compact pool
+    // of the same total that is downloaded
+    T.scap = scap;
     T.tfa = L.take<double>(PV);
+    T.sroff = L.take<int32_t>(NP + 1);
+    T.sreg = L.take<double>(3 * scap);
     T.sst = L.take<int32_t>(NP);
     T.sn = L.take<int32_t>(NP);
     T.soff = L.take<int32_t>(NP);
@@ -492,6 +494,9 @@ struct PassOut {
         dl(nh, std::nan("")), sst(nh, -1), soff(nh, 0), sn(nh, 0), slen(nh, 0.0) {}
 };
 enum PassKind : int { PASS_TUNNEL = 0, PASS_REFINE = 1 };
+// a pass's streamline point budget (the closure included) on a mesh of nv vertices: min(16384, nv / 4
+// + 64); the loops seen take a few hundredths of nv
+int64_t sl_budget(int64_t nv) { return std::min<int64_t>(16384, nv / 4 + 64); }
 
 // A chunk of single-layer passes in flight on one stream: its own device block (from the context's
 // stream-ordered pool) and control block, so that chunks on different streams run independently of
@@ -529,7 +534,7 @@ cudaError_t enqueue_chunk(vls_ctx *ctx, Batch &b, int kind, const std::vector<in
   int32_t ncyc_total = 0;
   if (kind == PASS_REFINE)
     for (int32_t h : chunk) ncyc_total += tun->vn[h];
-  int32_t *ht = static_cast<int32_t *>(ctx->pinned.take(sizeof(int32_t) * (size_t)(10 * NP + 1 + ncyc_total)));
+  int32_t *ht = static_cast<int32_t *>(ctx->pinned.take(sizeof(int32_t) * (size_t)(11 * NP + 2 + ncyc_total)));
   pb.pin_i = static_cast<int32_t *>(ctx->pinned.take(sizeof(int32_t) * (size_t)(7 * NP + 2)));
   pb.pin_l = static_cast<long long *>(ctx->pinned.take(sizeof(long long) * (size_t)(2 * NP)));
   pb.pin_d = static_cast<double *>(ctx->pinned.take(sizeof(double) * (size_t)(2 * NP)));
@@ -543,8 +548,9 @@ cudaError_t enqueue_chunk(vls_ctx *ctx, Batch &b, int kind, const std::vector<in
   }
   int32_t *pbase = ht, *pprob = ht + NP + 1, *pstep = pprob + NP, *pcoff = pstep + NP, *pcn = pcoff + NP;
   int32_t *heoff = pcn + NP, *hen = heoff + NP, *rcoff = hen + NP, *rclen = rcoff + NP, *xcap = rclen + NP;
-  int32_t *rcyc = xcap + NP;
-  int64_t PV = 0, ncut = 0, nx = 0;
+  int32_t *sroff = xcap + NP; // [NP + 1]
+  int32_t *rcyc = sroff + NP + 1;
+  int64_t PV = 0, ncut = 0, nx = 0, stot = 0;
   int32_t nc = 0;
   for (int32_t q = 0; q < NP; ++q) {
     const int32_t h = chunk[q], p = h_hprob[h];
@@ -569,15 +575,19 @@ cudaError_t enqueue_chunk(vls_ctx *ctx, Batch &b, int kind, const std::vector<in
       pcoff[q] = (int32_t)ncut;
       ncut += 2 * (int64_t)xcap[q];
     }
+    sroff[q] = (int32_t)stot;
+    stot += sl_budget(b.voff[p + 1] - b.voff[p]);
     PV += b.voff[p + 1] - b.voff[p];
   }
   pbase[NP] = (int32_t)PV;
-  if (PV >= INT32_MAX / 2 || ncut >= INT32_MAX / 2) {
+  sroff[NP] = (int32_t)stot;
+  if (!b.opt.streamlines) stot = 0;
+  if (PV >= INT32_MAX / 2 || ncut >= INT32_MAX / 2 || stot >= INT32_MAX / 4) {
     if (debug_on()) std::fprintf(stderr, "vls: pass chunk of %lld pass-vertices\n", (long long)PV);
     return cudaErrorMemoryAllocation;
   }
   Layout L{nullptr, true};
-  layout_tunnels(L, b, NP, PV, ncut, nx, nc);
+  layout_tunnels(L, b, NP, PV, ncut, nx, nc, stot);
   CKR(cudaEventCreateWithFlags(&pb.ev0, cudaEventDefault));
   CKR(cudaEventCreateWithFlags(&pb.ev1, cudaEventDefault));
   CKR(cudaEventRecord(pb.ev0, st));
@@ -586,7 +596,7 @@ cudaError_t enqueue_chunk(vls_ctx *ctx, Batch &b, int kind, const std::vector<in
   a.base = pb.mem;
   a.cap = L.bytes + 256;
   Layout L2{&a, false};
-  layout_tunnels(L2, b, NP, PV, ncut, nx, nc);
+  layout_tunnels(L2, b, NP, PV, ncut, nx, nc, stot);
   pb.T = b.td;
   TDev &T = pb.T;
   T.err = d.err;
@@ -600,6 +610,7 @@ cudaError_t enqueue_chunk(vls_ctx *ctx, Batch &b, int kind, const std::vector<in
   CKR(up(T.pstep, pstep, NP));
   CKR(up(T.pcoff, pcoff, NP));
   CKR(up(T.heoff, heoff, NP));
+  if (T.tfa) CKR(up(T.sroff, sroff, NP + 1));
   if (kind == PASS_TUNNEL) {
     CKR(up(T.pcn, pcn, NP));
     CKR(up(T.hen, hen, NP));

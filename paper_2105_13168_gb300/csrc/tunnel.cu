@@ -510,8 +510,22 @@ __global__ void k_ttrace(Dev d, TDev T) {
 // that face is usable and -g points into it, and leaves it where the ray meets its boundary; else
 // it runs along the edge to its lower end (smaller arrival, then smaller id).  It ends at a source;
 // a vertex with no descent left fails.  Points: the start, every edge crossing, every vertex
-// passed; at most SL_MAX with the closure.  Every product, sum and quotient is rounded on its own.
+// passed; at most min(SL_MAX, nv / 4 + 64) with the closure for a mesh of nv vertices (the host lays
+// out one region of that many points per pass).  Every product, sum and quotient is rounded on its
+// own.
 constexpr int32_t SL_MAX = 16384;
+
+// CSR slot of u -> w: the row's columns compared all at once (one memory level for rows of up to 16)
+__device__ __forceinline__ int32_t slot_scan(const int32_t *__restrict__ rp, const int32_t *__restrict__ col, int32_t u,
+                                             int32_t w) {
+  const int32_t b = rp[u], e = rp[u + 1];
+  if (e - b > 16) return slot_of(rp, col, u, w);
+  int32_t k = -1;
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if (b + j < e && col[b + j] == w) k = b + j;
+  return k;
+}
 
 struct SlPass {
   const Dev &d;
@@ -524,14 +538,23 @@ struct SlPass {
     if (((fa & F_SRC) && (fb & F_TGT)) || ((fa & F_TGT) && (fb & F_SRC))) return is_cut(T, q, k);
     return false;
   }
+  // every vertex reached and no edge cut; only an edge between a source and a target can be cut,
+  // so its slot is looked up only then (edges of a face always have slots in a validated mesh)
   __device__ bool usable(int32_t f) const {
     const int32_t *t = d.F + 3 * (int64_t)f;
-    for (int j = 0; j < 3; ++j)
-      if (!reached(t[j])) return false;
+    const int32_t a0 = t[0], a1 = t[1], a2 = t[2];
+    const int32_t i0 = base + (a0 - voff), i1 = base + (a1 - voff), i2 = base + (a2 - voff);
+    if (T.T[i0] < 0 || T.T[i1] < 0 || T.T[i2] < 0) return false;
+    const int8_t f0 = T.flag[i0], f1 = T.flag[i1], f2 = T.flag[i2];
+    if (((f0 | f1 | f2) & (F_SRC | F_TGT)) == 0) return true;
+    const int32_t vv[3] = {a0, a1, a2};
+    const int8_t ff[3] = {f0, f1, f2};
     for (int j = 0; j < 3; ++j) {
-      const int32_t a = t[j], b = t[j == 2 ? 0 : j + 1];
-      const int32_t k = slot_of(d.rp, d.col, a, b);
-      if (k < 0 || cut(a, b, k)) return false;
+      const int jn = j == 2 ? 0 : j + 1;
+      if (((ff[j] & F_SRC) && (ff[jn] & F_TGT)) || ((ff[j] & F_TGT) && (ff[jn] & F_SRC))) {
+        const int32_t k = slot_scan(d.rp, d.col, vv[j], vv[jn]);
+        if (k < 0 || is_cut(T, q, k)) return false;
+      }
     }
     return true;
   }
@@ -560,13 +583,15 @@ struct SlPass {
   }
 };
 
-// point writer: counts, and stores when out is non-null; at most lim points
+// point writer of a warp that traces in lock-step: every lane counts, lane 0 stores; at most lim
+// points
 struct SlOut {
   double *out;
   int32_t n, lim;
+  bool writer;
   __device__ bool push(const double p[3]) {
     if (n >= lim) return false;
-    if (out) {
+    if (writer) {
       out[3 * (int64_t)n] = p[0];
       out[3 * (int64_t)n + 1] = p[1];
       out[3 * (int64_t)n + 2] = p[2];
@@ -578,7 +603,8 @@ struct SlOut {
 };
 
 // the trace from start; returns VLS_OK with the source reached in xs, or VLS_ELOOPFAIL
-__device__ int32_t sl_trace(const SlPass &S, int32_t start, SlOut &o, int32_t &xs) {
+// (all lanes of a warp, in lock-step; lane = the caller's lane)
+__device__ int32_t sl_trace(const SlPass &S, int32_t start, SlOut &o, int32_t &xs, int32_t lane) {
   const Dev &d = S.d;
   int32_t v = start, ex = -1, ey = -1;
   double mu = 0.0;
@@ -590,9 +616,14 @@ __device__ int32_t sl_trace(const SlPass &S, int32_t start, SlOut &o, int32_t &x
         xs = v;
         return VLS_OK;
       }
+      // the faces around v, one half-edge per lane: each lane keeps its first steepest face, then the
+      // warp takes the steepest, the smallest slot on ties (the first in CSR order)
       double best = -1.0, bal = 0.0, bbe = 0.0;
-      int32_t bu = -1, bw = -1;
-      for (int32_t k = d.rp[v]; k < d.rp[v + 1]; ++k) {
+      int32_t bu = -1, bw = -1, bk = INT32_MAX;
+      const int32_t kb = d.rp[v], ke = d.rp[v + 1];
+      for (int32_t k0 = kb; k0 < ke; k0 += 32) {
+        const int32_t k = k0 + lane;
+        if (k >= ke) continue;
         const int32_t u = d.col[k], f = d.hface[k], w = S.third(f, v, u);
         double al, be, n2;
         if (!S.usable(f) || !S.grad(v, u, w, al, be, n2)) continue;
@@ -603,7 +634,26 @@ __device__ int32_t sl_trace(const SlPass &S, int32_t start, SlOut &o, int32_t &x
           bbe = be;
           bu = u;
           bw = w;
+          bk = k;
         }
+      }
+      {
+        double wb = best;
+        int32_t wk = bk;
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+          const double ob = __shfl_xor_sync(0xffffffffu, wb, o2);
+          const int32_t ok = __shfl_xor_sync(0xffffffffu, wk, o2);
+          if (ob > wb || (ob == wb && ok < wk)) {
+            wb = ob;
+            wk = ok;
+          }
+        }
+        const int owner = wk == INT32_MAX ? 0 : (wk - kb) & 31;
+        bal = __shfl_sync(0xffffffffu, bal, owner);
+        bbe = __shfl_sync(0xffffffffu, bbe, owner);
+        bu = __shfl_sync(0xffffffffu, bu, owner);
+        bw = __shfl_sync(0xffffffffu, bw, owner);
+        if (wk == INT32_MAX) bu = -1;
       }
       if (bu >= 0) {
         const double lam = ddiv(bbe, dadd(bal, bbe)); // where the ray meets edge u -> w, from u
@@ -627,10 +677,13 @@ __device__ int32_t sl_trace(const SlPass &S, int32_t start, SlOut &o, int32_t &x
         at_vertex = false;
         continue;
       }
+      // the steepest descending kept edge, one half-edge per lane as above (ties: the first)
       double bs = 0.0;
-      int32_t bn = -1;
+      int32_t bn = -1, bk2 = INT32_MAX;
       const double *xv = d.X + 3 * (int64_t)v;
-      for (int32_t k = d.rp[v]; k < d.rp[v + 1]; ++k) {
+      for (int32_t k0 = kb; k0 < ke; k0 += 32) {
+        const int32_t k = k0 + lane;
+        if (k >= ke) continue;
         const int32_t u = d.col[k];
         if (S.cut(v, u, k) || !S.reached(u)) continue;
         const double *xu = d.X + 3 * (int64_t)u;
@@ -639,15 +692,25 @@ __device__ int32_t sl_trace(const SlPass &S, int32_t start, SlOut &o, int32_t &x
         if (sl > bs) {
           bs = sl;
           bn = u;
+          bk2 = k;
         }
       }
+      for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, bs, o2);
+        const int32_t ok = __shfl_xor_sync(0xffffffffu, bk2, o2);
+        if (ob > bs || (ob == bs && ok < bk2)) {
+          bs = ob;
+          bk2 = ok;
+        }
+      }
+      bn = bk2 == INT32_MAX ? -1 : d.col[bk2];
       if (bn < 0) break; // no descent left
       v = bn;
       if (!o.push_v(d, v)) break;
       continue;
     }
     // on edge ex -> ey at mu from ex, entering the face left of it
-    const int32_t k = slot_of(d.rp, d.col, ex, ey);
+    const int32_t k = slot_scan(d.rp, d.col, ex, ey);
     const int32_t f = k >= 0 ? d.hface[k] : -1, z = f >= 0 ? S.third(f, ex, ey) : -1;
     double al = 0.0, be = 0.0, n2 = 0.0;
     if (f < 0 || !S.usable(f) || !S.grad(ex, ey, z, al, be, n2) || !(be < 0.0)) {
@@ -734,31 +797,33 @@ __device__ int32_t sl_close(const Dev &d, const TDev &T, int32_t q, int32_t bsta
   return VLS_OK;
 }
 
-// one thread per pass whose vertex trace succeeded.  Count pass (write false): status and point
-// count.  Write pass: the points at the pass's pool offset and the polyline's length.
-__global__ void __launch_bounds__(32) k_tstream(Dev d, TDev T, bool write) {
-  const int32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+// one warp per pass whose vertex trace succeeded (the lanes share the vertex steps): the trace into
+// the pass's region of the point pool (sroff), its status, point count and the closed polyline's
+// length
+constexpr int STREAM_WARPS = 4;
+__global__ void __launch_bounds__(32 * STREAM_WARPS) k_tstream(Dev d, TDev T) {
+  const int32_t q = blockIdx.x * STREAM_WARPS + (int32_t)(threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (q >= T.NP) return;
-  if (!write) T.sst[q] = -1;
-  if (T.qstatus[q] != VLS_OK || (write && T.sst[q] != VLS_OK)) return;
+  if (T.qstatus[q] != VLS_OK) {
+    if (lane == 0) {
+      T.sst[q] = -1;
+      T.sn[q] = 0;
+    }
+    return;
+  }
   const int32_t p = T.pprob[q];
   const SlPass S{d, T, q, T.pbase[q], d.voff[p]};
   const int32_t start = S.voff + T.qbstar[q];
-  // the write pass stores no more points than the count pass found room for
-  SlOut o{write ? T.spts + 3 * (int64_t)T.soff[q] : nullptr, 0, write ? T.sn[q] : SL_MAX};
+  double *P = T.sreg + 3 * (int64_t)T.sroff[q];
+  SlOut o{P, 0, T.sroff[q + 1] - T.sroff[q], lane == 0};
   int32_t xs = -1;
-  int32_t st = sl_trace(S, start, o, xs);
+  int32_t st = sl_trace(S, start, o, xs, lane);
   if (st == VLS_OK) st = sl_close(d, T, q, start, xs, o);
-  if (!write) {
-    T.sst[q] = st;
-    T.sn[q] = st == VLS_OK ? o.n : 0;
-    return;
-  }
-  if (st != VLS_OK || o.n != T.sn[q]) { // the write pass retraces the count pass's path
-    T.sst[q] = VLS_ELOOPFAIL;
-    return;
-  }
-  const double *P = T.spts + 3 * (int64_t)T.soff[q];
+  __syncwarp();
+  if (lane != 0) return;
+  T.sst[q] = st;
+  T.sn[q] = st == VLS_OK ? o.n : 0;
+  if (st != VLS_OK) return;
   double len = 0.0;
   for (int32_t i = 0; i < o.n; ++i) {
     const double *a = P + 3 * (int64_t)i, *b = P + 3 * (int64_t)(i + 1 == o.n ? 0 : i + 1);
@@ -768,34 +833,33 @@ __global__ void __launch_bounds__(32) k_tstream(Dev d, TDev T, bool write) {
   T.slen[q] = len;
 }
 
-// one warp: pool offsets of the traced streamlines in pass order; a streamline past the pool's end
-// fails with VLS_ELAYERS.  *nspts = points stored.
+// one warp: offsets of the traced streamlines in the compact pool, in pass order; *nspts = points
 __global__ void k_tstream_scan(TDev T) {
   const int32_t lane = threadIdx.x;
-  int64_t run = 0, kept_end = 0;
+  int64_t run = 0;
   for (int32_t b0 = 0; b0 < T.NP; b0 += 32) {
     const int32_t q = b0 + lane;
-    const bool ok = q < T.NP && T.sst[q] == VLS_OK;
-    const int64_t c = ok ? T.sn[q] : 0;
+    const int64_t c = q < T.NP && T.sst[q] == VLS_OK ? T.sn[q] : 0;
     int64_t inc = c;
     for (int o = 1; o < 32; o <<= 1) {
       const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
       if (lane >= o) inc += y;
     }
-    const int64_t beg = run + inc - c;
-    int64_t end = 0;
-    if (ok) {
-      if (beg + c > T.scap) T.sst[q] = VLS_ELAYERS;
-      else {
-        T.soff[q] = (int32_t)beg;
-        end = beg + c;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) end = max(end, __shfl_xor_sync(0xffffffffu, end, o));
-    kept_end = max(kept_end, end);
+    if (q < T.NP) T.soff[q] = (int32_t)(run + inc - c);
     run += __shfl_sync(0xffffffffu, inc, 31);
   }
-  if (lane == 0) *T.nspts = (int32_t)kept_end;
+  if (lane == 0) *T.nspts = (int32_t)run;
+}
+
+// one block per pass: its points from its region into the compact pool (whose capacity is the
+// regions' total, so every traced streamline fits)
+__global__ void k_tstream_compact(TDev T) {
+  const int32_t q = blockIdx.x;
+  if (q >= T.NP || T.sst[q] != VLS_OK) return;
+  const double *src = T.sreg + 3 * (int64_t)T.sroff[q];
+  double *dst = T.spts + 3 * (int64_t)T.soff[q];
+  const int32_t n3 = 3 * T.sn[q];
+  for (int32_t i = threadIdx.x; i < n3; i += blockDim.x) dst[i] = src[i];
 }
 
 __global__ void k_tctl_set(int32_t *ctl, int32_t idx, int32_t v) { ctl[idx] = v; }
@@ -875,10 +939,9 @@ cudaError_t run_tunnels(Batch &b, const TDev &T, cudaStream_t st, int32_t *tau_d
   }
   k_ttrace<<<(T.NP + 127) / 128, 128, 0, st>>>(d, T); VLS_LAUNCH(b);
   if (T.tfa) {
-    const int32_t g = (T.NP + 31) / 32;
-    k_tstream<<<g, 32, 0, st>>>(d, T, false); VLS_LAUNCH(b);
+    k_tstream<<<(T.NP + STREAM_WARPS - 1) / STREAM_WARPS, 32 * STREAM_WARPS, 0, st>>>(d, T); VLS_LAUNCH(b);
     k_tstream_scan<<<1, 32, 0, st>>>(T); VLS_LAUNCH(b);
-    k_tstream<<<g, 32, 0, st>>>(d, T, true); VLS_LAUNCH(b);
+    k_tstream_compact<<<T.NP, 128, 0, st>>>(T); VLS_LAUNCH(b);
   }
   e = cudaMemcpyAsync(tau_dst, T.ctl + CTL_TAU, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   b.d2h += (int64_t)sizeof(int32_t);

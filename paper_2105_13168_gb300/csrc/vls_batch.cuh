@@ -64,10 +64,12 @@ struct TDev {
   int32_t *path;         // scratch [pass-vertex] for traces
   // PL streamlines (Sec. 3.2), when on (tfa non-null)
   double *tfa;           // [pass-vertex] arrival time with the step's fraction (read where T >= 0)
-  int32_t *sst, *sn, *soff; // [NP] status (-1 not traced), points, offset in the pool
+  const int32_t *sroff;  // [NP+1] the passes' regions in sreg (a pass's point budget each)
+  double *sreg;          // [scap][3] the regions the traces write
+  int32_t *sst, *sn, *soff; // [NP] status (-1 not traced), points, offset in the compact pool
   double *slen;          // [NP] length of the closed polyline
-  double *spts;          // [scap][3] point pool
-  int32_t *nspts;        // points stored
+  double *spts;          // [scap][3] compact pool (what is downloaded)
+  int32_t *nspts;        // points in the compact pool
   int64_t scap;
 };
 
