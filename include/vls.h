@@ -95,17 +95,19 @@ typedef struct {
                                (total vertices rounded up to a power of two) runs the first 600
                                steps of its initial pass under each candidate shape and band
                                union-find variant and keeps the fastest for the life of the
-                               process */
+                               process; the tunnel and refinement pass kernels keep the default
+                               shapes */
   vls_precision precision;
   int32_t profile;          /* 1: time every frontier-update launch with CUDA events (vls_stats) */
   int32_t host_loop;        /* 1: launch each step's kernels from the host instead of running the
                                step loops as device-driven CUDA graphs (same results) */
   int32_t hook_variant;     /* band union-find: 1 one thread per band row, 2 a group of 8 lanes per
                                band row (one neighbour each), 0 autotuned or 2 (same results) */
-  int32_t rows_per_warp;    /* frontier rows a warp of the one-thread-per-row kernels takes per
-                               pass: 32, 16 or 8 (fewer rows per warp spread a small frontier over
-                               more warps and schedulers); 0 autotuned with the launch shape, or
-                               32 when the shape is given (same results) */
+  int32_t rows_per_warp;    /* frontier rows a warp of the initial pass's one-thread-per-row
+                               kernels takes per pass: 32, 16 or 8 (fewer rows per warp spread a
+                               small frontier over more warps and schedulers); 0 autotuned with the
+                               launch shape, or 32 when the shape is given (same results).  The
+                               tunnel and refinement pass kernels take 32 */
   int32_t refine;           /* 1: after each tunnel pass, the handle-refinement pass of its handle
                                (Sec. 3.3; needs tunnels = 1) */
   double offset;            /* loop classification (Sec. 3.5): normal offset as a fraction of the

@@ -368,6 +368,10 @@ void layout_batch(Layout &L, Batch &b) {
   d.ctl = L.take<int32_t>(CTL_SIZE);
   d.nalive = L.take<int32_t>(P);
   d.nbl = L.take<int32_t>(P);
+  d.nlay = L.take<int32_t>(V);
+  d.nph = pr == VLS_FP64 ? static_cast<void *>(L.take<double>(V))
+          : pr == VLS_FP32_RECHECK ? static_cast<void *>(L.take<float>(V))
+                                   : static_cast<void *>(L.take<__nv_bfloat16>(V));
 }
 
 // nx > 0: a refinement chunk -- its own border-edge pool (nx edges) and the tunnel cycles it starts
@@ -879,7 +883,9 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
   // row kernels (one thread per frontier row): small blocks spread a few thousand rows over
   // every SM; lane-group kernels (GL lanes per row): 256-thread blocks
   if (have_tuned) {
-    for (int k = 0; k < KK_COUNT_KINDS; ++k) b.shape[k] = tuned.shape[k];
+    // the tuner times the initial pass only: the pass kernels keep the default shapes
+    for (int k = 0; k < KK_COUNT_KINDS; ++k)
+      if (k != KK_TUPDATE && k != KK_TAPPLY && k != KK_TFRONTIER) b.shape[k] = tuned.shape[k];
     b.hook_variant = tuned.hook_variant;
     b.d.rpw = tuned.rpw;
   } else {
@@ -1059,6 +1065,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     CK(cudaMemsetAsync(d.stamp, 0, sizeof(int32_t) * b.V, st));
     CK(cudaMemsetAsync(d.fmark, 0, sizeof(int32_t) * b.V, st));
     CK(cudaMemsetAsync(d.multi, 0xff, sizeof(int32_t) * b.V, st));
+    CK(cudaMemsetAsync(d.nlay, 0, sizeof(int32_t) * b.V, st)); // layer ids stay in range before the first write
     CK(cudaMemsetAsync(d.lstate, 0, sizeof(int32_t) * b.Lcap, st));
     CK(cudaMemsetAsync(d.lfwd, 0, sizeof(int32_t) * b.Lcap, st));
     CK(cudaMemsetAsync(d.lcnt, 0, sizeof(int32_t) * b.Lcap, st));

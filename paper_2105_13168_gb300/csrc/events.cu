@@ -643,7 +643,7 @@ __global__ void k_mround_start(Handles H) {
 }  // namespace
 
 // IF(merge) body: WHILE(groups left) { groups -> traces (one block each) -> finish -> relabel }
-cudaError_t add_merge_nodes(Batch &b, cudaGraph_t gif) {
+cudaError_t add_merge_nodes(Batch &b, cudaGraph_t gif, const cudaGraphNode_t *dep) {
   Dev &d = b.d;
   int32_t *luf = d.lcnt + b.Lcap;                  // [Lcap] layer union-find scratch (init -1)
   int32_t *touched = d.lcnt + 2 * (size_t)b.Lcap;  // [Lcap]
@@ -652,7 +652,7 @@ cudaError_t add_merge_nodes(Batch &b, cudaGraph_t gif) {
   H.use = 1;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaGraphConditionalHandleCreate(&H.mround, gif, 1u, cudaGraphCondAssignDefault);
-  if (e == cudaSuccess) e = add_kernel(&s0, gif, nullptr, 0, k_mround_start, dim3(1), dim3(32), H);
+  if (e == cudaSuccess) e = add_kernel(&s0, gif, dep, dep ? 1 : 0, k_mround_start, dim3(1), dim3(32), H);
   if (e == cudaSuccess) {
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;

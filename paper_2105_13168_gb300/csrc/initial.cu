@@ -1,8 +1,11 @@
 // initial.cu -- the initial pass (Sec. 3.1): per step
 //   update   Eq. (2) explicit Euler step at every frontier row (Jacobi: reads the old state,
 //            writes a per-row output), clamp, snap, column normalisation;
-//   apply    scatter the rows into the state, collect rows where several layers meet
-//            (merge candidates, Sec. 3.1), record cover steps;
+//   apply    the rows' new states go into the state: by the band count (below) on ordinary
+//            steps, the band phases reading them from the update's vertex-indexed output
+//            (nlay, nph); first of all, in the merge phase's body, on a step where several
+//            layers meet at a row (merge candidates, Sec. 3.1), which also collects those rows;
+//            cover steps are recorded with the scatter;
 //   events   merges, then band labelling and splits / extinctions (events.cu);
 //   frontier next frontier = vertices of the closed neighbourhood of this step's rows whose
 //            own closed neighbourhood holds the base and at least one live layer (only
@@ -188,9 +191,14 @@ __device__ __forceinline__ int update_row(const Dev &d, const Params &P, int32_t
   if (ovf) {
     atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_ESLOTS);
     d.onl[i] = -1;
+    row_new(d, v, lv, (double)xv);
     return ROW_DONE;
   }
-  if (!hb || nl == 0) { d.onl[i] = -1; return ROW_DONE; }
+  if (!hb || nl == 0) {
+    d.onl[i] = -1;
+    row_new(d, v, lv, (double)xv);
+    return ROW_DONE;
+  }
   double out[KMAX];
   int outcome = ROW_DONE;
   bool unc = false;
@@ -222,14 +230,22 @@ __device__ __forceinline__ int update_row(const Dev &d, const Params &P, int32_t
     row_f64<MAXD, TV>(P, nl, ls, lv, o, xv, nlay, nx, deg, out, mass);
   }
   int cnt = 0;
+  int32_t l1 = 0;
+  double x1 = 0.0;
 #pragma unroll
   for (int q = 0; q < KMAX; ++q)
     if (q < nl && out[q] > 0.0) {
       d.olay[(int64_t)i * KMAX + cnt] = ls[q];
       d.ophi[(int64_t)i * KMAX + cnt] = out[q];
+      if (cnt == 0) {
+        l1 = ls[q];
+        x1 = out[q];
+      }
       ++cnt;
     }
   d.onl[i] = cnt;
+  row_new(d, v, l1, x1);
+  if (cnt >= 2) d.ctl[CTL_MERGE] = 1; // several layers at the row: the merge phase runs
   return outcome | (unc ? ROW_UNCERT : 0);
 }
 
@@ -320,9 +336,17 @@ __device__ __forceinline__ int update_row_fast(const Dev &d, const Params &P, in
       }
     }
   if (!one) return ROW_GENERAL;
-  if (l0 == 0) { d.onl[i] = -1; return ROW_DONE; } // the base alone: nothing changes
+  if (l0 == 0) { // the base alone: nothing changes
+    d.onl[i] = -1;
+    row_new(d, v, lv, (double)xv);
+    return ROW_DONE;
+  }
   if (d.lstate[l0] != L_ALIVE) return ROW_GENERAL;
-  if (!hb) { d.onl[i] = -1; return ROW_DONE; }      // no base in the neighbourhood
+  if (!hb) { // no base in the neighbourhood: nothing changes
+    d.onl[i] = -1;
+    row_new(d, v, lv, (double)xv);
+    return ROW_DONE;
+  }
   double out;
   int outcome = ROW_DONE;
   bool unc = false;
@@ -342,8 +366,10 @@ __device__ __forceinline__ int update_row_fast(const Dev &d, const Params &P, in
     d.olay[(int64_t)i * KMAX] = l0;
     d.ophi[(int64_t)i * KMAX] = out;
     d.onl[i] = 1;
+    row_new(d, v, l0, out);
   } else {
     d.onl[i] = 0;
+    row_new(d, v, 0, 0.0);
   }
   return outcome;
 }
@@ -351,9 +377,10 @@ __device__ __forceinline__ int update_row_fast(const Dev &d, const Params &P, in
 template <class TV>
 __device__ __forceinline__ int update_one(const Dev &d, const Params &P, const int32_t *fv, int32_t i, int32_t p,
                                           double2 &mass) {
-  if (__ldcg(d.pdone + p)) { d.onl[i] = -1; return ROW_DONE; }
+  if (__ldcg(d.pdone + p)) { d.onl[i] = -1; return ROW_DONE; } // nothing reads a finished problem's rows
   const int32_t v = fv[i];
   if (!VCHK(d.err, v, d.V, 101)) { d.onl[i] = -1; return ROW_DONE; }
+  d.uf[v] = v; // the band labelling starts from singletons (only band rows are ever united)
   const int32_t b = d.rp[v], e = d.rp[v + 1];
   if (!VCHK(d.err, e, d.nnz + 1, 102) || !VCHK(d.err, b, e + 1, 103)) { d.onl[i] = -1; return ROW_DONE; }
   const int32_t deg = e - b;
@@ -364,6 +391,7 @@ __device__ __forceinline__ int update_one(const Dev &d, const Params &P, const i
   if (deg <= 64) return update_row_wide<TV>(d, P, i, p, v, b, deg, mass);
   atomicCAS(&d.pstatus[p], 0, (int32_t)VLS_EINVAL);
   d.onl[i] = -1;
+  row_new(d, v, d.lay[v], ph_ld(d, v));
   return ROW_DONE;
 }
 
@@ -399,20 +427,32 @@ __device__ __forceinline__ void update_rows(const Dev &d, const Params &P) {
   }
 }
 
-// One instantiation per stored value type, so that each form gets its own register budget.
-template <class TV> __global__ void __launch_bounds__(256, VLS_UPDATE_MINB) k_update(Dev d, Params P) { update_rows<TV>(d, P); }
+// One instantiation per stored value type, so that each form gets its own register budget.  The
+// last block decides whether the merge phase (with the scatter first) runs this step.
+template <class TV>
+__global__ void __launch_bounds__(256, VLS_UPDATE_MINB) k_update(Dev d, Params P, Handles H) {
+  update_rows<TV>(d, P);
+  if (last_block_done(d.ctl + CTL_DONE_APPLY)) {
+    const int32_t m = __ldcg(d.ctl + CTL_MERGE);
+    if (H.use) cudaGraphSetConditional(H.merge, m ? 1u : 0u);
+    if (m) d.ctl[CTL_NMERGE]++;
+    d.ctl[CTL_MERGE] = 0;
+    d.ctl[CTL_APPLIED] = m ? 1 : 0;
+  }
+}
 
 // ------------------------------------------------------------------- apply
-// Also starts the band labelling: every row is its own union-find root (only band rows are
-// ever united), and flags the step for the merge phase when a row holds several layers.
+// A merge step (first node of the merge phase's body): every row into the state, and the rows
+// where several layers meet collected for the merge phase.  On other steps the band count does
+// the scatter (apply returns at once: it is launched every step only in the host-driven loop).
 __device__ __forceinline__ void apply_phase(const Dev &d) {
   const int32_t t = __ldcg(d.ctl + CTL_T), cur = t & 1;
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
   const int32_t nF = __ldcg(d.nfront + cur);
+  if (!__ldcg(d.ctl + CTL_APPLIED)) return;
   FOR_ROWS_R(i, nF, d.rpw) {
     const int32_t v = fv[i];
-    d.uf[v] = v;
     const int32_t c = d.onl[i];
     if (c < 0) continue;
     if (c == 0) {
@@ -428,26 +468,23 @@ __device__ __forceinline__ void apply_phase(const Dev &d) {
       const int32_t s = append(d.ncoll);
       if (VCHK(d.err, s, d.V, 110)) d.coll[s] = i;
       d.pmerge[fp[i]] = 1;
-      d.ctl[CTL_MERGE] = 1;
     }
   }
 }
-// The last block decides whether the merge phase runs this step.
-__global__ void k_apply(Dev d, Handles H) {
-  apply_phase(d);
-  if (last_block_done(d.ctl + CTL_DONE_APPLY)) {
-    const int32_t m = __ldcg(d.ctl + CTL_MERGE);
-    if (H.use) cudaGraphSetConditional(H.merge, m ? 1u : 0u);
-    if (m) d.ctl[CTL_NMERGE]++;
-    d.ctl[CTL_MERGE] = 0;
-  }
-}
+__global__ void k_apply(Dev d) { apply_phase(d); }
 
 // ------------------------------------------------------------------- band labelling
 __device__ __forceinline__ bool is_band(const Dev &d, int32_t v, int32_t &l) {
   l = d.lay[v];
   if (l == 0 || d.lstate[l] != L_ALIVE) return false;
   return ph_band(d, v);
+}
+// the same on this step's new state of a frontier row (before the scatter)
+__device__ __forceinline__ bool is_band_new(const Dev &d, int32_t v, int32_t &l, bool applied) {
+  if (applied) return is_band(d, v, l);
+  l = d.nlay[v];
+  if (l == 0 || d.lstate[l] != L_ALIVE) return false;
+  return nph_band(d, v);
 }
 
 __device__ __forceinline__ void hook_phase(const Dev &d) {
@@ -456,20 +493,21 @@ __device__ __forceinline__ void hook_phase(const Dev &d) {
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
   const int32_t nF = __ldcg(d.nfront + cur);
   const int32_t lane = group_lane();
+  const bool applied = __ldcg(d.ctl + CTL_APPLIED) != 0;
   // GL lanes per band row, one neighbour each: a neighbour joins the row's band component iff
   // it is a frontier row of this step (band vertices are) holding the same live layer strictly
-  // between 0 and 1; the smaller id of each such pair unites
+  // between 0 and 1 in its new state; the smaller id of each such pair unites
   FOR_ROWS_G(i, nF) {
     if (__ldcg(d.pdone + fp[i])) continue;
     const int32_t v = fv[i];
     int32_t l;
-    if (!is_band(d, v, l)) continue;
+    if (!is_band_new(d, v, l, applied)) continue;
     const int32_t b = d.rp[v], e = d.rp[v + 1];
     for (int32_t k = b + lane; k < e; k += GL) {
       const int32_t u = d.col[k];
       if (!VCHK(d.err, u, d.V, 130)) continue;
-      const int32_t fm = d.fmark[u], lu = d.lay[u];
-      const bool bu = ph_band(d, u);
+      const int32_t fm = d.fmark[u], lu = applied ? d.lay[u] : d.nlay[u];
+      const bool bu = applied ? ph_band(d, u) : nph_band(d, u);
       if (u < v && fm == t && lu == l && bu) uf_unite(d.uf, u, v);
     }
   }
@@ -483,11 +521,12 @@ __global__ void k_band_hook_row(Dev d) {
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
   const int32_t nF = __ldcg(d.nfront + cur);
+  const bool applied = __ldcg(d.ctl + CTL_APPLIED) != 0;
   FOR_ROWS_R(i, nF, d.rpw) {
     if (__ldcg(d.pdone + fp[i])) continue;
     const int32_t v = fv[i];
     int32_t l;
-    if (!is_band(d, v, l)) continue;
+    if (!is_band_new(d, v, l, applied)) continue;
     const int32_t b = d.rp[v], deg = d.rp[v + 1] - b;
     if (deg <= 16) {
       int32_t nu[16], nm[16], nl[16];
@@ -498,8 +537,8 @@ __global__ void k_band_hook_row(Dev d) {
       for (int j = 0; j < 16; ++j) {
         const bool ok = j < deg && nu[j] < v;
         nm[j] = ok ? d.fmark[nu[j]] : -1;
-        nl[j] = ok ? d.lay[nu[j]] : 0;
-        nb[j] = ok && ph_band(d, nu[j]);
+        nl[j] = ok ? (applied ? d.lay[nu[j]] : d.nlay[nu[j]]) : 0;
+        nb[j] = ok && (applied ? ph_band(d, nu[j]) : nph_band(d, nu[j]));
       }
 #pragma unroll
       for (int j = 0; j < 16; ++j)
@@ -510,7 +549,7 @@ __global__ void k_band_hook_row(Dev d) {
         if (!VCHK(d.err, u, d.V, 131)) continue;
         if (u >= v || d.fmark[u] != t) continue;
         int32_t lu;
-        if (is_band(d, u, lu) && lu == l) uf_unite(d.uf, u, v);
+        if (is_band_new(d, u, lu, applied) && lu == l) uf_unite(d.uf, u, v);
       }
     }
   }
@@ -518,17 +557,25 @@ __global__ void k_band_hook_row(Dev d) {
 
 // Component roots per layer.  A layer reaching two roots, or a problem with a live layer
 // that has no root (no band left), sends the step through the split phase.
+// Also the scatter of the step's rows into (lay, phi) and their cover steps, unless a merge step
+// did it before the band phases.
 __device__ __forceinline__ void count_phase(const Dev &d) {
-  const int32_t cur = __ldcg(d.ctl + CTL_T) & 1;
+  const int32_t t = __ldcg(d.ctl + CTL_T), cur = t & 1;
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
   const int32_t nF = __ldcg(d.nfront + cur);
+  const bool applied = __ldcg(d.ctl + CTL_APPLIED) != 0;
   FOR_ROWS_R(i, nF, d.rpw) {
     const int32_t p = fp[i];
     if (__ldcg(d.pdone + p)) continue;
     const int32_t v = fv[i];
     int32_t l;
-    if (!is_band(d, v, l)) continue;
+    const bool band = is_band_new(d, v, l, applied);
+    if (!applied) {
+      row_scatter(d, v);
+      if (d.nlay[v] != 0 && d.cover[v] < 0) d.cover[v] = t;
+    }
+    if (!band) continue;
     if (__ldcg(d.uf + v) == v) { // hooking is complete: roots are exactly the self-parents
       const int32_t old = atomicAdd(&d.lcnt[l], 1);
       if (old == 0) atomicAdd(&d.nbl[p], 1);
@@ -673,6 +720,7 @@ __device__ __forceinline__ void epilogue_phase(const Dev &d, const Handles &H, i
     d.ctl[CTL_ACTIVE] = nact;
     d.nfront[cur] = 0; // the list just consumed is reused two steps later
     *d.ncoll = 0;
+    d.ctl[CTL_APPLIED] = 0;
     d.ctl[CTL_T] = t + 1;
     if (H.use && (nact == 0 || t >= d.ctl[CTL_LIMIT])) cudaGraphSetConditional(H.loop, 0u);
   }
@@ -752,8 +800,8 @@ cudaError_t init_state(Batch &b) {
   return cudaGetLastError();
 }
 
-// The initial pass as one graph: WHILE(problems running) { update; apply; IF(merge) {...};
-// band hook; band count; IF(split / extinction) {...}; next frontier; epilogue }.
+// The initial pass as one graph: WHILE(problems running) { update; IF(merge) { apply; ... };
+// band hook; band count (and the scatter); IF(split / extinction) {...}; next frontier; epilogue }.
 cudaError_t build_initial_graph(Batch &b, cudaGraph_t *out) {
   cudaGraph_t g = nullptr, body = nullptr, mbody = nullptr, sbody = nullptr;
   cudaGraphNode_t w, n_upd, n_app, n_if_m, n_hook, n_cnt, n_if_s, n_fr;
@@ -773,17 +821,17 @@ cudaError_t build_initial_graph(Batch &b, cudaGraph_t *out) {
   GK(cudaGraphConditionalHandleCreate(&H.split, body, 0u, cudaGraphCondAssignDefault));
   GK(add_kernel(&n_upd, body, nullptr, 0, b.d.phih ? k_update<__nv_bfloat16> : b.d.phif ? k_update<float> : k_update<double>,
                 G(KK_UPDATE), T(KK_UPDATE),
-                b.d, b.prm));
-  GK(add_kernel(&n_app, body, &n_upd, 1, k_apply, G(KK_APPLY), T(KK_APPLY), b.d, H));
+                b.d, b.prm, H));
   {
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;
     np.conditional.handle = H.merge;
     np.conditional.type = cudaGraphCondTypeIf;
     np.conditional.size = 1;
-    GK(cudaGraphAddNode(&n_if_m, body, &n_app, nullptr, 1, &np));
+    GK(cudaGraphAddNode(&n_if_m, body, &n_upd, nullptr, 1, &np));
     mbody = np.conditional.phGraph_out[0];
-    GK(add_merge_nodes(b, mbody));
+    GK(add_kernel(&n_app, mbody, nullptr, 0, k_apply, G(KK_APPLY), T(KK_APPLY), b.d));
+    GK(add_merge_nodes(b, mbody, &n_app));
   }
   GK(add_kernel(&n_hook, body, &n_if_m, 1, b.hook_variant == 1 ? k_band_hook_row : k_band_hook, G(KK_HOOK), T(KK_HOOK),
                 b.d));
@@ -815,13 +863,13 @@ cudaError_t initial_step_host(Batch &b) {
   Handles H{};
   H.use = 0;
   long ps = b.prof.begin(st, KK_UPDATE);
-  if (d.phih) k_update<__nv_bfloat16><<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm);
-  else if (d.phif) k_update<float><<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm);
-  else k_update<double><<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm);
+  if (d.phih) k_update<__nv_bfloat16><<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm, H);
+  else if (d.phif) k_update<float><<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm, H);
+  else k_update<double><<<b.cfg[KK_UPDATE].grid, b.cfg[KK_UPDATE].threads, 0, st>>>(d, b.prm, H);
   VLS_LAUNCH(b);
   b.prof.end(st, ps);
   ps = b.prof.begin(st, KK_APPLY);
-  k_apply<<<b.cfg[KK_APPLY].grid, b.cfg[KK_APPLY].threads, 0, st>>>(d, H); VLS_LAUNCH(b);
+  k_apply<<<b.cfg[KK_APPLY].grid, b.cfg[KK_APPLY].threads, 0, st>>>(d); VLS_LAUNCH(b);
   b.prof.end(st, ps);
   cudaError_t e = merge_phase_host(b);
   if (e != cudaSuccess) return e;

@@ -211,7 +211,7 @@ cudaError_t build_initial_graph(Batch &b, cudaGraph_t *graph);
 cudaError_t initial_step_host(Batch &b);
 cudaError_t final_checks(Batch &b);
 // events.cu: bodies of the IF nodes (and their host-loop launches)
-cudaError_t add_merge_nodes(Batch &b, cudaGraph_t body);
+cudaError_t add_merge_nodes(Batch &b, cudaGraph_t body, const cudaGraphNode_t *dep);
 cudaError_t add_split_nodes(Batch &b, cudaGraph_t body);
 cudaError_t merge_phase_host(Batch &b);
 cudaError_t split_phase_host(Batch &b);

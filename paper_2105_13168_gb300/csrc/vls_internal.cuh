@@ -100,6 +100,11 @@ struct Dev {
   int32_t *fmark;    // step at which the vertex was last in the frontier
   int32_t *uf;       // union-find parent for band CCL
   int32_t *multi;    // frontier row of a vertex holding several layers this step, else -1
+  // the new state of this step's frontier rows, vertex-indexed, written by the update (one layer or
+  // the base; unchanged rows keep their state): the band phases read it, the band count scatters it
+  // into (lay, phi) -- unless a merge step scattered the rows first (CTL_APPLIED)
+  int32_t *nlay;
+  void *nph;         // stored value type of the form (double, float or bfloat16)
   // layers (global ids)
   int32_t *lstate, *lfwd, *lbirth, *ldeath, *lcnt;
   int32_t *lprob;
@@ -174,6 +179,8 @@ enum Ctl : int {
   CTL_DONE_FRONT = 12, // last-block counter of the initial-pass frontier kernel
   CTL_DONE_TFRONT = 13, // last-block counter of the tunnel-pass frontier kernel
   CTL_MSKIP = 14,     // merge groups of this step already resolved by earlier rounds of the phase
+  CTL_APPLIED = 15,   // 1: this step's rows were scattered into the state before the band phases (a
+                      // merge step); 0: the band phases read the rows' new states from nlay / nph
   CTL_SIZE = 16
 };
 
@@ -331,6 +338,25 @@ __device__ __forceinline__ void ph_st(const Dev &d, int32_t v, double x) {
   if (d.phih) d.phih[v] = __double2bfloat16(x);
   else if (d.phif) d.phif[v] = (float)x;
   else d.phi[v] = x;
+}
+// a row's new state (one layer l or the base, value exactly representable in the stored type)
+__device__ __forceinline__ void row_new(const Dev &d, int32_t v, int32_t l, double x) {
+  d.nlay[v] = l;
+  if (d.phih) static_cast<__nv_bfloat16 *>(d.nph)[v] = __double2bfloat16(x);
+  else if (d.phif) static_cast<float *>(d.nph)[v] = (float)x;
+  else static_cast<double *>(d.nph)[v] = x;
+}
+__device__ __forceinline__ bool nph_band(const Dev &d, int32_t v) {
+  return d.phih ? val_band(static_cast<const __nv_bfloat16 *>(d.nph)[v])
+         : d.phif ? val_band(static_cast<const float *>(d.nph)[v])
+                  : val_band(static_cast<const double *>(d.nph)[v]);
+}
+// the row's new state into (lay, phi)
+__device__ __forceinline__ void row_scatter(const Dev &d, int32_t v) {
+  d.lay[v] = d.nlay[v];
+  if (d.phih) d.phih[v] = static_cast<const __nv_bfloat16 *>(d.nph)[v];
+  else if (d.phif) d.phif[v] = static_cast<const float *>(d.nph)[v];
+  else d.phi[v] = static_cast<const double *>(d.nph)[v];
 }
 // any FP64 value into the state (FP32 / BF16 forms: rounded keeping its side of every threshold)
 __device__ __forceinline__ void ph_st_round(const Dev &d, const Params &P, int32_t v, double x) {
