@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--scale", type=float, default=1.0, help="workload grid scale (1.0 = full size)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=2, help="problems timed for the CPU baseline")
+    ap.add_argument("--cpu-sample", type=int, default=3, help="problems timed for the CPU baseline (about 13 s of one core)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one detection of the workload bounded to --max-steps initial steps (for profilers)")
     ap.add_argument("--shape", default="",
