@@ -159,6 +159,7 @@ struct Dev {
   // device control block (see CTL_*), per-problem live layers and layers holding a band root
   int32_t *ctl;
   int32_t *nalive, *nbl;
+  int32_t *pcomp;    // [P] this step's band components summed over the problem's live layers
 };
 
 // Control block: the step loops run on the device (a CUDA graph WHILE node around the step
@@ -478,15 +479,18 @@ __device__ __forceinline__ int32_t uf_find(int32_t *par, int32_t x) {
   }
   return x;
 }
-__device__ __forceinline__ void uf_unite(int32_t *par, int32_t a, int32_t b) {
+// Returns true when this call linked two components (each link joins two distinct trees: links
+// only point from a larger root to a smaller id).
+__device__ __forceinline__ bool uf_unite(int32_t *par, int32_t a, int32_t b) {
   int32_t ra = uf_find(par, a), rb = uf_find(par, b);
   while (ra != rb) {
     if (ra > rb) { int32_t t = ra; ra = rb; rb = t; }
     int32_t old = atomicCAS(&par[rb], rb, ra);
-    if (old == rb) return;
+    if (old == rb) return true;
     rb = uf_find(par, old);
     ra = uf_find(par, ra);
   }
+  return false;
 }
 
 // Append to a list shared by the whole grid with one atomic per warp (the lanes that reach this
