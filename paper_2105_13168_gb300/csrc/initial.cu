@@ -245,7 +245,10 @@ __device__ __forceinline__ int update_row(const Dev &d, const Params &P, int32_t
     }
   d.onl[i] = cnt;
   row_new(d, v, l1, x1);
-  if (cnt >= 2) d.ctl[CTL_MERGE] = 1; // several layers at the row: the merge phase runs
+  if (cnt >= 2) { // several layers at the row: the merge phase runs (read by the update's last block)
+    d.ctl[CTL_MERGE] = 1;
+    __threadfence();
+  }
   return outcome | (unc ? ROW_UNCERT : 0);
 }
 
@@ -432,7 +435,7 @@ __device__ __forceinline__ void update_rows(const Dev &d, const Params &P) {
 template <class TV>
 __global__ void __launch_bounds__(256, VLS_UPDATE_MINB) k_update(Dev d, Params P, Handles H) {
   update_rows<TV>(d, P);
-  if (last_block_done(d.ctl + CTL_DONE_APPLY)) {
+  if (last_block_done_fenced(d.ctl + CTL_DONE_APPLY)) {
     const int32_t m = __ldcg(d.ctl + CTL_MERGE);
     if (H.use) cudaGraphSetConditional(H.merge, m ? 1u : 0u);
     if (m) d.ctl[CTL_NMERGE]++;
@@ -503,8 +506,16 @@ __device__ __forceinline__ void hook_account(const Dev &d, bool lead, int32_t p,
   const unsigned lp = __match_any_sync(0xffffffffu, lead ? l : -1) & act;
   if (lead) {
     const int32_t sum = __reduce_add_sync(pp, contrib);
-    if (lane == __ffs(pp) - 1 && sum != 0) atomicAdd(&d.pcomp[p], sum);
-    if (lane == __ffs(lp) - 1 && atomicAdd(&d.lcnt[l], __popc(lp)) == 0) atomicAdd(&d.nbl[p], 1);
+    bool wrote = false;
+    if (lane == __ffs(pp) - 1 && sum != 0) {
+      atomicAdd(&d.pcomp[p], sum);
+      wrote = true;
+    }
+    if (lane == __ffs(lp) - 1 && atomicAdd(&d.lcnt[l], __popc(lp)) == 0) {
+      atomicAdd(&d.nbl[p], 1);
+      wrote = true;
+    }
+    if (wrote) __threadfence(); // read by the last block (hook_decide)
   }
 }
 __device__ __forceinline__ void scatter_row(const Dev &d, int32_t v, int32_t t) {
@@ -603,7 +614,7 @@ __device__ __forceinline__ void hook_row_phase(const Dev &d) {
 
 // The last block decides whether the split phase runs this step.
 __device__ __forceinline__ void hook_decide(const Dev &d, const Handles &H) {
-  if (last_block_done(d.ctl + CTL_DONE_COUNT)) {
+  if (last_block_done_fenced(d.ctl + CTL_DONE_COUNT)) {
     int32_t s = 0;
     for (int32_t p = 0; p < d.P && !s; ++p)
       if (!d.pdone[p] && (__ldcg(d.nbl + p) != d.nalive[p] || __ldcg(d.pcomp + p) != d.nalive[p])) s = 1;
@@ -642,7 +653,9 @@ __device__ __forceinline__ uint32_t gives(const Dev &d, int32_t w) {
 // than GL loop); the row itself joins when it qualifies on its own or through any pair.  Also
 // clears the per-layer root counts of this step (each band root resets its layer's counter) and
 // accumulates the step record.
-__device__ __forceinline__ void frontier_phase(const Dev &d) {
+// Returns true in the threads that wrote something the step's epilogue reads (list counts, step
+// records).
+__device__ __forceinline__ bool frontier_phase(const Dev &d) {
   const int32_t t = __ldcg(d.ctl + CTL_T), cur = t & 1, nxt = cur ^ 1, tnext = t + 1;
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
@@ -654,7 +667,9 @@ __device__ __forceinline__ void frontier_phase(const Dev &d) {
   const int32_t lane = group_lane();
   const unsigned grp = group_mask();
   int32_t *__restrict__ seg_out = d.fseg[nxt];
+  bool wrote = false;
   auto add = [&](int32_t u, int32_t p) {
+    wrote = true;
     if (atomicExch(&d.stamp[u], tnext) == tnext) return;
     int32_t ks;
     const int32_t s = warp_append(nN_ptr, pcount_next, p, &ks);
@@ -674,6 +689,7 @@ __device__ __forceinline__ void frontier_phase(const Dev &d) {
       if (is_band(d, v, l)) {
         d.lcnt[l] = 0; // band rows of the layer counted by the next step's band labelling
         if (d.record) {
+          wrote = true;
           atomicAdd(&d.rband[p], 1);
           const uint64_t key = ((uint64_t)(uint32_t)(v - d.voff[p]) << 32) | (uint32_t)(l - d.lbase[p]);
           atomicAdd(&d.rhash[p], (unsigned long long)mix64(key));
@@ -696,6 +712,7 @@ __device__ __forceinline__ void frontier_phase(const Dev &d) {
     join = __any_sync(grp, join) && gv != 0u;
     if (lane == 0 && join) add(v, p);
   }
+  return wrote;
 }
 
 // ------------------------------------------------------------------- epilogue
@@ -753,8 +770,10 @@ __device__ __forceinline__ void epilogue_phase(const Dev &d, const Handles &H, i
 }
 // The next frontier, then (epi = 1) the step's epilogue in the last block to finish.
 __global__ void __launch_bounds__(256) k_frontier(Dev d, Handles H, int32_t max_steps, int32_t epi) {
-  frontier_phase(d);
-  if (epi && last_block(d.ctl + CTL_DONE_FRONT)) epilogue_phase(d, H, max_steps);
+  const bool wrote = frontier_phase(d);
+  if (!epi) return;
+  if (wrote) __threadfence(); // the epilogue reads the list counts and step records
+  if (last_block_fenced(d.ctl + CTL_DONE_FRONT)) epilogue_phase(d, H, max_steps);
 }
 
 // ------------------------------------------------------------------- init

@@ -345,7 +345,8 @@ __device__ __forceinline__ uint32_t tgives_at(const TDev &T, int32_t i) {
 }
 
 // GL-lane groups per row, lane j takes the row's neighbour j (rows longer than GL loop).
-__device__ __forceinline__ void tfrontier_phase(const Dev &d, const TDev &T) {
+// Returns true in the threads that appended to the next frontier (the epilogue reads its counts).
+__device__ __forceinline__ bool tfrontier_phase(const Dev &d, const TDev &T) {
   const int32_t tau = __ldcg(T.ctl + CTL_TAU), cur = tau & 1, nxt = cur ^ 1, tnext = tau + 1;
   const int32_t *__restrict__ fv = T.fv[cur];
   const int32_t *__restrict__ fq = T.fq[cur];
@@ -356,7 +357,9 @@ __device__ __forceinline__ void tfrontier_phase(const Dev &d, const TDev &T) {
   int32_t *qcnt_next = T.qcnt + (size_t)nxt * T.NP;
   const int32_t lane = group_lane();
   const unsigned grp = group_mask();
+  bool wrote = false;
   auto add = [&](int32_t u, int32_t iu, int32_t q) {
+    wrote = true;
     if (atomicExch(&T.stamp[iu], tnext) == tnext) return;
     const int32_t s = warp_append(nN_ptr, qcnt_next, q);
     if (!VCHK(T.err, s, T.PV, 331)) return;
@@ -389,6 +392,7 @@ __device__ __forceinline__ void tfrontier_phase(const Dev &d, const TDev &T) {
     join = __any_sync(grp, join) && !(fl & F_SRC);
     if (lane == 0 && join) add(v, iv, q);
   }
+  return wrote;
 }
 
 
@@ -424,8 +428,10 @@ __device__ __forceinline__ void tepilogue_phase(const Dev &d, const TDev &T, con
 
 // The next frontier of every pass, then (epi = 1) the step's epilogue in the last block to finish.
 __global__ void __launch_bounds__(256) k_tfrontier(Dev d, TDev T, Handles H, int32_t max_steps, int32_t epi) {
-  tfrontier_phase(d, T);
-  if (epi && last_block(T.ctl + CTL_DONE_TFRONT)) tepilogue_phase(d, T, H, max_steps);
+  const bool wrote = tfrontier_phase(d, T);
+  if (!epi) return;
+  if (wrote) __threadfence(); // the epilogue reads the next frontier's counts
+  if (last_block_fenced(T.ctl + CTL_DONE_TFRONT)) tepilogue_phase(d, T, H, max_steps);
 }
 
 // one thread per pass: greedy descent on (arrival, id), then closure along the loop
