@@ -100,7 +100,7 @@ __device__ int32_t new_layer(Dev &d, int32_t p, int32_t birth_local) {
   d.ldeath[l] = -1;
   d.lfwd[l] = 0;
   d.lprob[l] = p;
-  d.lcnt[l] = 0; // band rows counted by the band labelling
+  d.lcnt[l] = 0; // band components counted by the band labelling
   return l;
 }
 
@@ -558,14 +558,9 @@ __global__ void __launch_bounds__(256) k_split(Dev d) {
     const int32_t l = d.lbase[p] + loc;
     if (d.lstate[l] != L_ALIVE) continue; // uniform across the block
     if (threadIdx.x == 0) {
-      s_c = 0;
+      // the layer's band components this step (none when it had no band row)
+      s_c = d.lseen[l] == t ? d.lcnt[l] : 0;
       s_nroot = 0;
-    }
-    __syncthreads();
-    // the layer's band components: the union-find roots among its band rows of this step
-    for (int32_t j = threadIdx.x; j < ns; j += blockDim.x) {
-      const int32_t v = seg[j];
-      if (d.lay[v] == l && ph_band(d, v) && d.uf[v] == v) atomicAdd(&s_c, 1);
     }
     __syncthreads();
     const int32_t c = s_c;

@@ -498,21 +498,26 @@ __device__ __forceinline__ bool is_band_new(const Dev &d, int32_t v, int32_t &l,
 // equal the live layers; otherwise the step goes through the split phase (a split or an
 // extinction).  The row's own state and its band neighbours' are this step's new states: a band
 // neighbour is always a row of this step.
-__device__ __forceinline__ void hook_account(const Dev &d, bool lead, int32_t p, int32_t l, int32_t contrib) {
+// contrib = 1 - (links made by the row): summed over a layer's band rows it is the layer's number of
+// band components (lcnt, read by the split phase), over a problem's the problem's (pcomp)
+__device__ __forceinline__ void hook_account(const Dev &d, bool lead, int32_t p, int32_t l, int32_t contrib,
+                                             int32_t t) {
   const unsigned act = __ballot_sync(0xffffffffu, lead);
   if (!act) return;
   const int32_t lane = (int32_t)(threadIdx.x & 31);
   const unsigned pp = __match_any_sync(0xffffffffu, lead ? p : -1) & act;
   const unsigned lp = __match_any_sync(0xffffffffu, lead ? l : -1) & act;
   if (lead) {
-    const int32_t sum = __reduce_add_sync(pp, contrib);
+    const int32_t psum = __reduce_add_sync(pp, contrib);
+    const int32_t lsum = __reduce_add_sync(lp, contrib);
     bool wrote = false;
-    if (lane == __ffs(pp) - 1 && sum != 0) {
-      atomicAdd(&d.pcomp[p], sum);
+    if (lane == __ffs(pp) - 1 && psum != 0) {
+      atomicAdd(&d.pcomp[p], psum);
       wrote = true;
     }
-    if (lane == __ffs(lp) - 1 && atomicAdd(&d.lcnt[l], __popc(lp)) == 0) {
-      atomicAdd(&d.nbl[p], 1);
+    if (lane == __ffs(lp) - 1) {
+      if (lsum != 0) atomicAdd(&d.lcnt[l], lsum);
+      if (atomicExch(&d.lseen[l], t) != t) atomicAdd(&d.nbl[p], 1); // the layer's first band rows
       wrote = true;
     }
     if (wrote) __threadfence(); // read by the last block (hook_decide)
@@ -558,7 +563,7 @@ __device__ __forceinline__ void hook_phase(const Dev &d) {
     }
     const int32_t rl = __reduce_add_sync(gmask, links);
     const bool lead = band && glane == 0;
-    hook_account(d, lead, p, l, 1 - rl);
+    hook_account(d, lead, p, l, 1 - rl, t);
   }
 }
 
@@ -608,7 +613,7 @@ __device__ __forceinline__ void hook_row_phase(const Dev &d) {
         }
       }
     }
-    hook_account(d, band, p, l, 1 - links);
+    hook_account(d, band, p, l, 1 - links, t);
   }
 }
 
@@ -687,7 +692,7 @@ __device__ __forceinline__ bool frontier_phase(const Dev &d) {
     if (lane == 0) {
       int32_t l;
       if (is_band(d, v, l)) {
-        d.lcnt[l] = 0; // band rows of the layer counted by the next step's band labelling
+        d.lcnt[l] = 0; // components of the layer, counted by the next step's band labelling
         if (d.record) {
           wrote = true;
           atomicAdd(&d.rband[p], 1);

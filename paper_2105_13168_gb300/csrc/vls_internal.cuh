@@ -107,6 +107,7 @@ struct Dev {
   void *nph;         // stored value type of the form (double, float or bfloat16)
   // layers (global ids)
   int32_t *lstate, *lfwd, *lbirth, *ldeath, *lcnt;
+  int32_t *lseen;    // [Lcap] last step at which the layer had band rows
   int32_t *lprob;
   // frontier lists (double buffered) and per-row outputs
   int32_t *front[2];
