@@ -368,8 +368,6 @@ void layout_batch(Layout &L, Batch &b) {
   d.ctl = L.take<int32_t>(CTL_SIZE);
   d.nalive = L.take<int32_t>(P);
   d.nbl = L.take<int32_t>(P);
-  d.pcomp = L.take<int32_t>(P);
-  d.lseen = L.take<int32_t>(Lc);
   d.nlay = L.take<int32_t>(V);
   d.nph = pr == VLS_FP64 ? static_cast<void *>(L.take<double>(V))
           : pr == VLS_FP32_RECHECK ? static_cast<void *>(L.take<float>(V))
@@ -1090,8 +1088,6 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     CK(cudaMemsetAsync(d.err, 0, sizeof(int32_t) * 4, st));
     CK(cudaMemsetAsync(d.nalive, 0, sizeof(int32_t) * b.P, st));
     CK(cudaMemsetAsync(d.nbl, 0, sizeof(int32_t) * b.P, st));
-    CK(cudaMemsetAsync(d.pcomp, 0, sizeof(int32_t) * b.P, st));
-    CK(cudaMemsetAsync(d.lseen, 0, sizeof(int32_t) * b.Lcap, st));
     {
       int32_t ctl[CTL_SIZE] = {};
       ctl[CTL_LIMIT] = ctx->opt.max_steps;

@@ -100,7 +100,6 @@ __device__ int32_t new_layer(Dev &d, int32_t p, int32_t birth_local) {
   d.ldeath[l] = -1;
   d.lfwd[l] = 0;
   d.lprob[l] = p;
-  d.lcnt[l] = 0; // band components counted by the band labelling
   return l;
 }
 
@@ -558,8 +557,8 @@ __global__ void __launch_bounds__(256) k_split(Dev d) {
     const int32_t l = d.lbase[p] + loc;
     if (d.lstate[l] != L_ALIVE) continue; // uniform across the block
     if (threadIdx.x == 0) {
-      // the layer's band components this step (none when it had no band row)
-      s_c = d.lseen[l] == t ? d.lcnt[l] : 0;
+      s_c = d.lcnt[l];
+      d.lcnt[l] = 0;
       s_nroot = 0;
     }
     __syncthreads();

@@ -1,11 +1,11 @@
 // initial.cu -- the initial pass (Sec. 3.1): per step
 //   update   Eq. (2) explicit Euler step at every frontier row (Jacobi: reads the old state,
 //            writes a per-row output), clamp, snap, column normalisation;
-//   apply    the rows' new states go into the state: by the band labelling (below) on
-//            ordinary steps, which reads them from the update's vertex-indexed output (nlay,
-//            nph); first of all, in the merge phase's body, on a step where several layers meet
-//            at a row (merge candidates, Sec. 3.1), which also collects those rows; cover steps
-//            are recorded with the scatter;
+//   apply    the rows' new states go into the state: by the band count (below) on ordinary
+//            steps, the band phases reading them from the update's vertex-indexed output
+//            (nlay, nph); first of all, in the merge phase's body, on a step where several
+//            layers meet at a row (merge candidates, Sec. 3.1), which also collects those rows;
+//            cover steps are recorded with the scatter;
 //   events   merges, then band labelling and splits / extinctions (events.cu);
 //   frontier next frontier = vertices of the closed neighbourhood of this step's rows whose
 //            own closed neighbourhood holds the base and at least one live layer (only
@@ -490,150 +490,113 @@ __device__ __forceinline__ bool is_band_new(const Dev &d, int32_t v, int32_t &l,
   return nph_band(d, v);
 }
 
-// Band components by union-find, with the scatter of the rows' new states into (lay, phi) and
-// their cover steps (unless a merge step did it first) and the component count.  A successful
-// link joins two components of one layer's band, so per problem (band rows) - (links) is the
-// number of band components summed over its live layers; the layers holding band rows are counted
-// at each layer's first band row.  Every live layer has exactly one component iff both numbers
-// equal the live layers; otherwise the step goes through the split phase (a split or an
-// extinction).  The row's own state and its band neighbours' are this step's new states: a band
-// neighbour is always a row of this step.
-// contrib = 1 - (links made by the row): summed over a layer's band rows it is the layer's number of
-// band components (lcnt, read by the split phase), over a problem's the problem's (pcomp)
-__device__ __forceinline__ void hook_account(const Dev &d, bool lead, int32_t p, int32_t l, int32_t contrib,
-                                             int32_t t) {
-  const unsigned act = __ballot_sync(0xffffffffu, lead);
-  if (!act) return;
-  const int32_t lane = (int32_t)(threadIdx.x & 31);
-  const unsigned pp = __match_any_sync(0xffffffffu, lead ? p : -1) & act;
-  const unsigned lp = __match_any_sync(0xffffffffu, lead ? l : -1) & act;
-  if (lead) {
-    const int32_t psum = __reduce_add_sync(pp, contrib);
-    const int32_t lsum = __reduce_add_sync(lp, contrib);
-    bool wrote = false;
-    if (lane == __ffs(pp) - 1 && psum != 0) {
-      atomicAdd(&d.pcomp[p], psum);
-      wrote = true;
-    }
-    if (lane == __ffs(lp) - 1) {
-      if (lsum != 0) atomicAdd(&d.lcnt[l], lsum);
-      if (atomicExch(&d.lseen[l], t) != t) atomicAdd(&d.nbl[p], 1); // the layer's first band rows
-      wrote = true;
-    }
-    if (wrote) __threadfence(); // read by the last block (hook_decide)
-  }
-}
-__device__ __forceinline__ void scatter_row(const Dev &d, int32_t v, int32_t t) {
-  row_scatter(d, v);
-  if (d.nlay[v] != 0 && d.cover[v] < 0) d.cover[v] = t;
-}
-
 __device__ __forceinline__ void hook_phase(const Dev &d) {
   const int32_t t = __ldcg(d.ctl + CTL_T), cur = t & 1;
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
   const int32_t nF = __ldcg(d.nfront + cur);
-  const int32_t glane = group_lane();
-  const unsigned gmask = group_mask();
+  const int32_t lane = group_lane();
   const bool applied = __ldcg(d.ctl + CTL_APPLIED) != 0;
-  // GL lanes per row, one neighbour each: a neighbour joins the row's band component iff it is a
-  // frontier row of this step holding the same live layer strictly between 0 and 1 in its new
-  // state; the smaller id of each such pair unites
-  VLS_WARP_LOOP(w, 32 / GL, nF) {
-    const int32_t i = w * (32 / GL) + (int32_t)((threadIdx.x & 31) / GL);
-    int32_t p = -1, l = 0, links = 0;
-    bool band = false;
-    if (i < nF) {
-      p = fp[i];
-      if (!__ldcg(d.pdone + p)) {
-        const int32_t v = fv[i];
-        if (!applied && glane == 0) scatter_row(d, v, t);
-        band = is_band_new(d, v, l, applied);
-        if (band) {
-          const int32_t b = d.rp[v], e = d.rp[v + 1];
-          for (int32_t k = b + glane; k < e; k += GL) {
-            const int32_t u = d.col[k];
-            if (!VCHK(d.err, u, d.V, 130)) continue;
-            const int32_t fm = d.fmark[u], lu = applied ? d.lay[u] : d.nlay[u];
-            const bool bu = applied ? ph_band(d, u) : nph_band(d, u);
-            if (u < v && fm == t && lu == l && bu && uf_unite(d.uf, u, v)) ++links;
-          }
-        }
-      }
+  // GL lanes per band row, one neighbour each: a neighbour joins the row's band component iff
+  // it is a frontier row of this step (band vertices are) holding the same live layer strictly
+  // between 0 and 1 in its new state; the smaller id of each such pair unites
+  FOR_ROWS_G(i, nF) {
+    if (__ldcg(d.pdone + fp[i])) continue;
+    const int32_t v = fv[i];
+    int32_t l;
+    if (!is_band_new(d, v, l, applied)) continue;
+    const int32_t b = d.rp[v], e = d.rp[v + 1];
+    for (int32_t k = b + lane; k < e; k += GL) {
+      const int32_t u = d.col[k];
+      if (!VCHK(d.err, u, d.V, 130)) continue;
+      const int32_t fm = d.fmark[u], lu = applied ? d.lay[u] : d.nlay[u];
+      const bool bu = applied ? ph_band(d, u) : nph_band(d, u);
+      if (u < v && fm == t && lu == l && bu) uf_unite(d.uf, u, v);
     }
-    const int32_t rl = __reduce_add_sync(gmask, links);
-    const bool lead = band && glane == 0;
-    hook_account(d, lead, p, l, 1 - rl, t);
   }
 }
+__global__ void k_band_hook(Dev d) { hook_phase(d); }
 
 // The other union-find variant: one thread per band row unites the row with each qualifying
 // neighbour in turn (neighbour states gathered first).
-__device__ __forceinline__ void hook_row_phase(const Dev &d) {
+__global__ void k_band_hook_row(Dev d) {
   const int32_t t = __ldcg(d.ctl + CTL_T), cur = t & 1;
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
   const int32_t nF = __ldcg(d.nfront + cur);
   const bool applied = __ldcg(d.ctl + CTL_APPLIED) != 0;
-  const int32_t R = d.rpw, lane = (int32_t)(threadIdx.x & 31);
-  VLS_WARP_LOOP(w, R, nF) {
-    const int32_t i = w * R + lane;
-    int32_t p = -1, l = 0, links = 0;
-    bool band = false;
-    if (lane < R && i < nF) {
-      p = fp[i];
-      if (!__ldcg(d.pdone + p)) {
-        const int32_t v = fv[i];
-        if (!applied) scatter_row(d, v, t);
-        band = is_band_new(d, v, l, applied);
-        const int32_t b = d.rp[v], deg = d.rp[v + 1] - b;
-        if (band && deg <= 16) {
-          int32_t nu[16], nm[16], nl[16];
-          bool nb[16];
+  FOR_ROWS_R(i, nF, d.rpw) {
+    if (__ldcg(d.pdone + fp[i])) continue;
+    const int32_t v = fv[i];
+    int32_t l;
+    if (!is_band_new(d, v, l, applied)) continue;
+    const int32_t b = d.rp[v], deg = d.rp[v + 1] - b;
+    if (deg <= 16) {
+      int32_t nu[16], nm[16], nl[16];
+      bool nb[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) nu[j] = (j < deg) ? d.col[b + j] : v;
+      for (int j = 0; j < 16; ++j) nu[j] = (j < deg) ? d.col[b + j] : v;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const bool ok = j < deg && nu[j] < v;
-            nm[j] = ok ? d.fmark[nu[j]] : -1;
-            nl[j] = ok ? (applied ? d.lay[nu[j]] : d.nlay[nu[j]]) : 0;
-            nb[j] = ok && (applied ? ph_band(d, nu[j]) : nph_band(d, nu[j]));
-          }
+      for (int j = 0; j < 16; ++j) {
+        const bool ok = j < deg && nu[j] < v;
+        nm[j] = ok ? d.fmark[nu[j]] : -1;
+        nl[j] = ok ? (applied ? d.lay[nu[j]] : d.nlay[nu[j]]) : 0;
+        nb[j] = ok && (applied ? ph_band(d, nu[j]) : nph_band(d, nu[j]));
+      }
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (nm[j] == t && nl[j] == l && nb[j] && uf_unite(d.uf, nu[j], v)) ++links;
-        } else if (band) {
-          for (int32_t k = b; k < b + deg; ++k) {
-            const int32_t u = d.col[k];
-            if (!VCHK(d.err, u, d.V, 131)) continue;
-            if (u >= v || d.fmark[u] != t) continue;
-            int32_t lu;
-            if (is_band_new(d, u, lu, applied) && lu == l && uf_unite(d.uf, u, v)) ++links;
-          }
-        }
+      for (int j = 0; j < 16; ++j)
+        if (nm[j] == t && nl[j] == l && nb[j]) uf_unite(d.uf, nu[j], v);
+    } else {
+      for (int32_t k = b; k < b + deg; ++k) {
+        const int32_t u = d.col[k];
+        if (!VCHK(d.err, u, d.V, 131)) continue;
+        if (u >= v || d.fmark[u] != t) continue;
+        int32_t lu;
+        if (is_band_new(d, u, lu, applied) && lu == l) uf_unite(d.uf, u, v);
       }
     }
-    hook_account(d, band, p, l, 1 - links, t);
   }
 }
 
-// The last block decides whether the split phase runs this step.
-__device__ __forceinline__ void hook_decide(const Dev &d, const Handles &H) {
-  if (last_block_done_fenced(d.ctl + CTL_DONE_COUNT)) {
-    int32_t s = 0;
-    for (int32_t p = 0; p < d.P && !s; ++p)
-      if (!d.pdone[p] && (__ldcg(d.nbl + p) != d.nalive[p] || __ldcg(d.pcomp + p) != d.nalive[p])) s = 1;
-    if (H.use) cudaGraphSetConditional(H.split, s ? 1u : 0u);
-    if (s) d.ctl[CTL_NSPLIT]++;
+// Component roots per layer.  A layer reaching two roots, or a problem with a live layer
+// that has no root (no band left), sends the step through the split phase.
+// Also the scatter of the step's rows into (lay, phi) and their cover steps, unless a merge step
+// did it before the band phases.
+__device__ __forceinline__ void count_phase(const Dev &d) {
+  const int32_t t = __ldcg(d.ctl + CTL_T), cur = t & 1;
+  const int32_t *__restrict__ fv = d.front[cur];
+  const int32_t *__restrict__ fp = d.front[cur] + d.V;
+  const int32_t nF = __ldcg(d.nfront + cur);
+  const bool applied = __ldcg(d.ctl + CTL_APPLIED) != 0;
+  FOR_ROWS_R(i, nF, d.rpw) {
+    const int32_t p = fp[i];
+    if (__ldcg(d.pdone + p)) continue;
+    const int32_t v = fv[i];
+    int32_t l;
+    const bool band = is_band_new(d, v, l, applied);
+    if (!applied) {
+      row_scatter(d, v);
+      if (d.nlay[v] != 0 && d.cover[v] < 0) d.cover[v] = t;
+    }
+    if (!band) continue;
+    if (__ldcg(d.uf + v) == v) { // hooking is complete: roots are exactly the self-parents
+      const int32_t old = atomicAdd(&d.lcnt[l], 1);
+      if (old == 0) atomicAdd(&d.nbl[p], 1);
+      else if (old == 1) d.ctl[CTL_SPLIT] = 1;
+      __threadfence(); // read by the last block
+    }
   }
 }
-__global__ void k_band_hook(Dev d, Handles H) {
-  hook_phase(d);
-  hook_decide(d, H);
-}
-__global__ void k_band_hook_row(Dev d, Handles H) {
-  hook_row_phase(d);
-  hook_decide(d, H);
+__global__ void k_band_count(Dev d, Handles H) {
+  count_phase(d);
+  if (last_block_done_fenced(d.ctl + CTL_DONE_COUNT)) {
+    int32_t s = __ldcg(d.ctl + CTL_SPLIT);
+    for (int32_t p = 0; p < d.P && !s; ++p)
+      if (!d.pdone[p] && __ldcg(d.nbl + p) != d.nalive[p]) s = 1;
+    if (H.use) cudaGraphSetConditional(H.split, s ? 1u : 0u);
+    if (s) d.ctl[CTL_NSPLIT]++;
+    d.ctl[CTL_SPLIT] = 0;
+  }
 }
 
 // ------------------------------------------------------------------- next frontier
@@ -692,7 +655,7 @@ __device__ __forceinline__ bool frontier_phase(const Dev &d) {
     if (lane == 0) {
       int32_t l;
       if (is_band(d, v, l)) {
-        d.lcnt[l] = 0; // components of the layer, counted by the next step's band labelling
+        if (d.uf[v] == v) d.lcnt[l] = 0;
         if (d.record) {
           wrote = true;
           atomicAdd(&d.rband[p], 1);
@@ -761,7 +724,6 @@ __device__ __forceinline__ void epilogue_phase(const Dev &d, const Handles &H, i
     pcount_cur[p] = 0;
     d.pmerge[p] = 0;
     d.nbl[p] = 0;
-    d.pcomp[p] = 0;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -851,11 +813,10 @@ cudaError_t init_state(Batch &b) {
 }
 
 // The initial pass as one graph: WHILE(problems running) { update; IF(merge) { apply; ... };
-// band labelling (with the scatter and the component count); IF(split / extinction) {...};
-// next frontier; epilogue }.
+// band hook; band count (and the scatter); IF(split / extinction) {...}; next frontier; epilogue }.
 cudaError_t build_initial_graph(Batch &b, cudaGraph_t *out) {
   cudaGraph_t g = nullptr, body = nullptr, mbody = nullptr, sbody = nullptr;
-  cudaGraphNode_t w, n_upd, n_app, n_if_m, n_hook, n_if_s, n_fr;
+  cudaGraphNode_t w, n_upd, n_app, n_if_m, n_hook, n_cnt, n_if_s, n_fr;
   Handles H{};
   H.use = 1;
   cudaError_t e = cudaGraphCreate(&g, 0);
@@ -885,14 +846,15 @@ cudaError_t build_initial_graph(Batch &b, cudaGraph_t *out) {
     GK(add_merge_nodes(b, mbody, &n_app));
   }
   GK(add_kernel(&n_hook, body, &n_if_m, 1, b.hook_variant == 1 ? k_band_hook_row : k_band_hook, G(KK_HOOK), T(KK_HOOK),
-                b.d, H));
+                b.d));
+  GK(add_kernel(&n_cnt, body, &n_hook, 1, k_band_count, G(KK_COUNT), T(KK_COUNT), b.d, H));
   {
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;
     np.conditional.handle = H.split;
     np.conditional.type = cudaGraphCondTypeIf;
     np.conditional.size = 1;
-    GK(cudaGraphAddNode(&n_if_s, body, &n_hook, nullptr, 1, &np));
+    GK(cudaGraphAddNode(&n_if_s, body, &n_cnt, nullptr, 1, &np));
     sbody = np.conditional.phGraph_out[0];
     GK(add_split_nodes(b, sbody));
   }
@@ -924,9 +886,12 @@ cudaError_t initial_step_host(Batch &b) {
   cudaError_t e = merge_phase_host(b);
   if (e != cudaSuccess) return e;
   ps = b.prof.begin(st, KK_HOOK);
-  if (b.hook_variant == 1) k_band_hook_row<<<b.cfg[KK_HOOK].grid, b.cfg[KK_HOOK].threads, 0, st>>>(d, H);
-  else k_band_hook<<<b.cfg[KK_HOOK].grid, b.cfg[KK_HOOK].threads, 0, st>>>(d, H);
+  if (b.hook_variant == 1) k_band_hook_row<<<b.cfg[KK_HOOK].grid, b.cfg[KK_HOOK].threads, 0, st>>>(d);
+  else k_band_hook<<<b.cfg[KK_HOOK].grid, b.cfg[KK_HOOK].threads, 0, st>>>(d);
   VLS_LAUNCH(b);
+  b.prof.end(st, ps);
+  ps = b.prof.begin(st, KK_COUNT);
+  k_band_count<<<b.cfg[KK_COUNT].grid, b.cfg[KK_COUNT].threads, 0, st>>>(d, H); VLS_LAUNCH(b);
   b.prof.end(st, ps);
   e = split_phase_host(b);
   if (e != cudaSuccess) return e;
@@ -943,6 +908,7 @@ void configure_initial(Batch &b) {
                                                            : row_cfg(b, k_update<double>, KK_UPDATE, 128);
   b.cfg[KK_APPLY] = row_cfg(b, k_apply, KK_APPLY, 128);
   b.cfg[KK_HOOK] = b.hook_variant == 1 ? row_cfg(b, k_band_hook_row, KK_HOOK, 128) : row_cfg(b, k_band_hook, KK_HOOK, 256);
+  b.cfg[KK_COUNT] = row_cfg(b, k_band_count, KK_COUNT, 128);
   b.cfg[KK_FRONTIER] = row_cfg(b, k_frontier, KK_FRONTIER, 256); // GL lanes per row
 }
 

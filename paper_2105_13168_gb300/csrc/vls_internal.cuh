@@ -107,7 +107,6 @@ struct Dev {
   void *nph;         // stored value type of the form (double, float or bfloat16)
   // layers (global ids)
   int32_t *lstate, *lfwd, *lbirth, *ldeath, *lcnt;
-  int32_t *lseen;    // [Lcap] last step at which the layer had band rows
   int32_t *lprob;
   // frontier lists (double buffered) and per-row outputs
   int32_t *front[2];
@@ -160,7 +159,6 @@ struct Dev {
   // device control block (see CTL_*), per-problem live layers and layers holding a band root
   int32_t *ctl;
   int32_t *nalive, *nbl;
-  int32_t *pcomp;    // [P] this step's band components summed over the problem's live layers
 };
 
 // Control block: the step loops run on the device (a CUDA graph WHILE node around the step
