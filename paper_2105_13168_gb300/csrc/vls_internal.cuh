@@ -191,28 +191,11 @@ struct Handles {
   int32_t use;
 };
 
-// True in exactly one thread of the grid: thread 0 of the last block to finish.  Every thread
-// of every block must call it (after its share of the work).
-__device__ __forceinline__ bool last_block_done(int32_t *counter) {
-  __shared__ bool last;
-  __threadfence(); // every thread's flag stores become visible before the block reports done
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(counter, 1) == (int32_t)gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    *counter = 0;
-    return true;
-  }
-  return false;
-}
-
-// The same, for kernels whose last block reads only data that its writers made visible
-// themselves (a __threadfence after the write, in the writing thread): the other threads skip the
-// fence, which otherwise holds every warp of every block until its stores have drained.
+// True in exactly one thread of the grid: thread 0 of the last block to finish.  Every thread of
+// every block must call it (after its share of the work).  The last block may read only data whose
+// writers made it visible themselves (a __threadfence after the write, in the writing thread):
+// the other threads skip the fence, which would hold every warp of every block until its stores
+// have drained.
 __device__ __forceinline__ bool last_block_done_fenced(int32_t *counter) {
   __shared__ bool last;
   __syncthreads();
@@ -233,21 +216,6 @@ __device__ __forceinline__ bool last_block_done_fenced(int32_t *counter) {
 // their own writes (see last_block_done_fenced).
 __device__ __forceinline__ bool last_block_fenced(int32_t *counter) {
   __shared__ bool last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(counter, 1) == (int32_t)gridDim.x - 1;
-    if (last) *counter = 0;
-  }
-  __syncthreads();
-  if (last) __threadfence();
-  return last;
-}
-
-// True in every thread of the last block of the grid to finish (same protocol as above).
-__device__ __forceinline__ bool last_block(int32_t *counter) {
-  __shared__ bool last;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
