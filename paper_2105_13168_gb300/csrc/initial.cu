@@ -515,11 +515,15 @@ __device__ __forceinline__ void hook_phase(const Dev &d) {
     }
   }
 }
-__global__ void k_band_hook(Dev d) { hook_phase(d); }
+__global__ void k_band_hook(Dev d) {
+  pdl_enter();
+  hook_phase(d);
+}
 
 // The other union-find variant: one thread per band row unites the row with each qualifying
 // neighbour in turn (neighbour states gathered first).
 __global__ void k_band_hook_row(Dev d) {
+  pdl_enter();
   const int32_t t = __ldcg(d.ctl + CTL_T), cur = t & 1;
   const int32_t *__restrict__ fv = d.front[cur];
   const int32_t *__restrict__ fp = d.front[cur] + d.V;
@@ -588,6 +592,7 @@ __device__ __forceinline__ void count_phase(const Dev &d) {
   }
 }
 __global__ void k_band_count(Dev d, Handles H) {
+  pdl_enter();
   count_phase(d);
   if (last_block_done_fenced(d.ctl + CTL_DONE_COUNT)) {
     int32_t s = __ldcg(d.ctl + CTL_SPLIT);
@@ -847,7 +852,8 @@ cudaError_t build_initial_graph(Batch &b, cudaGraph_t *out) {
   }
   GK(add_kernel(&n_hook, body, &n_if_m, 1, b.hook_variant == 1 ? k_band_hook_row : k_band_hook, G(KK_HOOK), T(KK_HOOK),
                 b.d));
-  GK(add_kernel(&n_cnt, body, &n_hook, 1, k_band_count, G(KK_COUNT), T(KK_COUNT), b.d, H));
+  GK(add_kernel(&n_cnt, body, nullptr, 0, k_band_count, G(KK_COUNT), T(KK_COUNT), b.d, H));
+  GK(add_programmatic_edge(body, n_hook, n_cnt));
   {
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;

@@ -302,6 +302,7 @@ __device__ __forceinline__ void tupdate_rows(const Dev &d, const TDev &T, const 
 
 // One instantiation per stored value type, so that each form gets its own register budget.
 template <class TV> __global__ void __launch_bounds__(256, VLS_UPDATE_MINB) k_tupdate(Dev d, TDev T, Params P) {
+  pdl_enter();
   tupdate_rows<TV>(d, T, P);
 }
 
@@ -329,7 +330,10 @@ __device__ __forceinline__ void tapply_phase(const Dev &d, const TDev &T, double
     tph_st(T, idx, x);
   }
 }
-__global__ void k_tapply(Dev d, TDev T, double theta) { tapply_phase(d, T, theta); }
+__global__ void k_tapply(Dev d, TDev T, double theta) {
+  pdl_enter();
+  tapply_phase(d, T, theta);
+}
 
 // u joins pass q's frontier iff it is in the domain, not a source, and its kept closed
 // neighbourhood holds both phases (a value > 0 and a value < 1).  tgives(x): bit 0 the layer
@@ -428,6 +432,7 @@ __device__ __forceinline__ void tepilogue_phase(const Dev &d, const TDev &T, con
 
 // The next frontier of every pass, then (epi = 1) the step's epilogue in the last block to finish.
 __global__ void __launch_bounds__(256) k_tfrontier(Dev d, TDev T, Handles H, int32_t max_steps, int32_t epi) {
+  pdl_enter();
   const bool wrote = tfrontier_phase(d, T);
   if (!epi) return;
   if (wrote) __threadfence(); // the epilogue reads the next frontier's counts
@@ -936,10 +941,12 @@ cudaError_t run_tunnels(Batch &b, const TDev &T, cudaStream_t st, int32_t *tau_d
     e = cudaGraphCreate(&g, 0);
     if (e == cudaSuccess) e = add_conditional(&w, g, nullptr, 0, cudaGraphCondTypeWhile, 1u, &H.loop, &body);
     if (e == cudaSuccess) e = add_kernel(&n0, body, nullptr, 0, T.phih ? k_tupdate<__nv_bfloat16> : T.phif ? k_tupdate<float> : k_tupdate<double>, dim3(b.cfg[KK_TUPDATE].grid), dim3(b.cfg[KK_TUPDATE].threads), d, T, b.prm);
-    if (e == cudaSuccess) e = add_kernel(&n1, body, &n0, 1, k_tapply, dim3(b.cfg[KK_TAPPLY].grid), dim3(b.cfg[KK_TAPPLY].threads), d, T, b.prm.theta);
+    if (e == cudaSuccess) e = add_kernel(&n1, body, nullptr, 0, k_tapply, dim3(b.cfg[KK_TAPPLY].grid), dim3(b.cfg[KK_TAPPLY].threads), d, T, b.prm.theta);
+    if (e == cudaSuccess) e = add_programmatic_edge(body, n0, n1);
     if (e == cudaSuccess)
-      e = add_kernel(&n2, body, &n1, 1, k_tfrontier, dim3(b.cfg[KK_TFRONTIER].grid), dim3(b.cfg[KK_TFRONTIER].threads), d, T, H,
+      e = add_kernel(&n2, body, nullptr, 0, k_tfrontier, dim3(b.cfg[KK_TFRONTIER].grid), dim3(b.cfg[KK_TFRONTIER].threads), d, T, H,
                      b.opt.max_pass_steps, 1);
+    if (e == cudaSuccess) e = add_programmatic_edge(body, n1, n2);
     cudaGraphExec_t ge = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
     if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);

@@ -163,6 +163,21 @@ inline cudaError_t add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGr
 
 // Add a conditional node (IF / WHILE) to g after deps; its handle is created on g with the
 // given default (assigned at every launch of the graph).  *body receives the body graph.
+// A programmatic edge from kernel node `from` to kernel node `to` (the kernels call pdl_enter
+// first): `to` may be scheduled while `from` finishes.  Where the driver refuses the edge, an
+// ordinary one.
+inline cudaError_t add_programmatic_edge(cudaGraph_t g, cudaGraphNode_t from, cudaGraphNode_t to) {
+  cudaGraphEdgeData ed = {};
+  ed.from_port = cudaGraphKernelNodePortProgrammatic;
+  ed.type = cudaGraphDependencyTypeProgrammatic;
+  cudaError_t e = cudaGraphAddDependencies(g, &from, &to, &ed, 1);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    e = cudaGraphAddDependencies(g, &from, &to, nullptr, 1);
+  }
+  return e;
+}
+
 inline cudaError_t add_conditional(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps,
                                    cudaGraphConditionalNodeType type, unsigned dflt,
                                    cudaGraphConditionalHandle *h, cudaGraph_t *body) {

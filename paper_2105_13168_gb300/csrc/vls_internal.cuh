@@ -191,6 +191,15 @@ struct Handles {
   int32_t use;
 };
 
+// Programmatic dependent launch between consecutive step kernels of a graph: wait until the grids
+// this one depends on have completed and their memory is visible (returns at once when the launch
+// has no programmatic dependency), then let the next grid's blocks be scheduled -- they wait in
+// their own pdl_enter, so the launch of the next kernel overlaps the tail of this one.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // True in exactly one thread of the grid: thread 0 of the last block to finish.  Every thread of
 // every block must call it (after its share of the work).  The last block may read only data whose
 // writers made it visible themselves (a __threadfence after the write, in the writing thread):
