@@ -1111,18 +1111,19 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     double ms_t = 0.0, ms_r = 0.0;
     int next_sp = 0;
     int64_t inflight_bytes = 0;
-    // passes run in chunks whose dense per-pass state (one entry per vertex of the pass's problem,
-    // about 48 B each) fits a bound set by the free device memory; chunks in flight together stay
-    // within twice that
+    // passes run in chunks whose dense per-pass state (one entry per vertex of the pass's problem:
+    // at most 52 B in the FP64 form, 72 B with the streamlines' arrival times and point regions)
+    // fits a bound set by the free device memory; chunks in flight together stay within twice that
+    const int64_t pv_bytes = ctx->opt.streamlines ? 72 : 52;
     int64_t pv_cap = (int64_t(1) << 30) - (int64_t(1) << 20); // pass-vertex ids stay below INT32_MAX / 2
     {
       size_t fr = 0, tot = 0;
-      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) pv_cap = std::min<int64_t>(pv_cap, (int64_t)(fr / 4 / 48));
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) pv_cap = std::min<int64_t>(pv_cap, (int64_t)(fr / 4 / pv_bytes));
       // VLS_PASS_VERTS overrides the bound (smaller chunks; the results do not change)
       if (const char *ev = std::getenv("VLS_PASS_VERTS")) pv_cap = std::atoll(ev);
       pv_cap = std::max<int64_t>(pv_cap, 1);
     }
-    const int64_t inflight_cap = 2 * pv_cap * 48;
+    const int64_t inflight_cap = 2 * pv_cap * pv_bytes;
     h_hprob.assign(d.hcap, 0);
     h_hstep.assign(d.hcap, 0);
     h_hoff.assign(d.hcap, 0);
@@ -1153,7 +1154,7 @@ extern "C" vls_status vls_detect_batch(vls_ctx *ctx, int32_t n_mesh, const vls_m
     auto chunk_bytes = [&](const std::vector<int32_t> &hs) {
       int64_t pv = 0;
       for (int32_t h : hs) pv += b.voff[h_hprob[h] + 1] - b.voff[h_hprob[h]];
-      return 48 * pv;
+      return pv_bytes * pv;
     };
     // start chunks of the pending handles (in order) while the in-flight bound allows (one chunk always
     // starts when none is in flight); refinements wait for their problem's initial pass to end;
