@@ -246,3 +246,25 @@ def test_passes_overlapping_the_initial_pass(vls, monkeypatch):
             assert_parity(base[i], o)
             assert_parity(over[i], o)
             i += 1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_host_loop_equals_graph(vls, precision):
+    """The host-launched step loop (profiling path: every kernel launched each step, the merge
+    scatter and the event kernels returning at once when nothing happened) gives the results of the
+    device-driven graph, on a batch with splits, merges and extinctions."""
+    meshes = [meshgen.tube_chain(3, 80), meshgen.capsules(5, 60), meshgen.torus(32, 16)]
+    probs = [(m, [meshgen.seed_vertex(3 * i + k, m.nv) for k in range(2)]) for i, m in enumerate(meshes)]
+    a = run_gpu(vls, probs, precision=precision)
+    b = run_gpu(vls, probs, precision=precision, host_loop=1)
+    for ga, gb in zip(a, b):
+        assert ga.status == gb.status == 0
+        assert ga.events() == gb.events()
+        assert np.array_equal(ga.layers, gb.layers) and np.array_equal(ga.records, gb.records)
+        assert np.array_equal(ga.cover, gb.cover) and np.array_equal(ga.layer, gb.layer)
+        assert np.array_equal(ga.phi, gb.phi)
+        for ta, tb in zip(ga.tunnels + ga.refined, gb.tunnels + gb.refined):
+            assert ta.status == tb.status and np.array_equal(ta.verts, tb.verts)
+            assert ta.stream_status == tb.stream_status and np.array_equal(ta.stream, tb.stream)
+    kinds = {k for p in a for k, _ in p.events()}
+    assert {"SPLIT", "MERGE", "END"} <= kinds
